@@ -1,0 +1,349 @@
+"""Benchmark: online rate-distortion estimation + ground truth on GB300.
+
+One step = one pass of the whole hot path over one field: value range; ZFP
+block pass (sampled-block estimate fused with the every-block ground truth);
+bin width from the exact MSE_sp; SZ pass (sampled-point estimate fused with
+the every-point ground truth); entropy, Huffman costs, selection.  Workload:
+a Hurricane-shaped 100x500x500 float32 field (GRF k^-11/3 plus 8 tanh fronts,
+scaled to [0, 300]) at eb_rel 1e-4 (the paper's throughput setting) and
+r_sp = 5% (its default).  The field (100 MB) fits in L2, so L2 is flushed by
+writing a 256 MB buffer before every timed step; the flush is outside the
+timed events.
+
+Under torchrun each rank evaluates its own independent field (weak scaling,
+no collective on the data path); the timed K steps are bracketed by a barrier
+and a synchronize, and the time is the maximum over ranks.
+
+--impl reference times the CPU oracle (the plain restatement of the method)
+on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "R-D estimate GB/s per GB300 (SZ+ZFP) & % HBM peak; batched vs plain; p99 latency"
+WORKLOAD = "hurricane_100x500x500_grf_tanh_f32"
+SHAPE = (100, 500, 500)
+EB_REL = 1e-4
+R_SP = 0.05
+FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="rdsel", choices=["rdsel", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-planes", type=int, default=100,
+                    help="planes of the field in the CPU-baseline sample")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1806_08901_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(fn.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    rec = d.get(WORKLOAD, {}).get(kernel)
+    if not rec or rec.get("source_hash") != kernel_source_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def _query(self, extra=()):
+        return ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                "--format=csv,noheader,nounits", *extra]
+
+    def start(self):
+        try:
+            self.lines += subprocess.run(self._query(), capture_output=True, text=True,
+                                         timeout=20).stdout.splitlines()
+            self.proc = subprocess.Popen(self._query(["-lms", "20"]), stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except (OSError, subprocess.SubprocessError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=10)
+                self.lines += out.splitlines()
+            except subprocess.SubprocessError:
+                self.proc.kill()
+        try:
+            self.lines += subprocess.run(self._query(), capture_output=True, text=True,
+                                         timeout=20).stdout.splitlines()
+        except (OSError, subprocess.SubprocessError):
+            pass
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(x_host, planes: int, steps: int = 1):
+    """Time the oracle (select + ground truth) on the first `planes` planes."""
+    import oracle as O
+
+    s = x_host[:planes].copy()
+    p = O.params(eb=EB_REL, r_sp=R_SP)
+    t = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        O.select(s, p)
+        O.ground_truth(s, p)
+        t.append(time.perf_counter() - t0)
+    sec = statistics.mean(t)
+    return {"value": 4.0 * s.size / sec / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {planes} of {SHAPE[0]} planes ({s.size} points), "
+                      f"select + ground truth, {steps} run(s), {sec:.2f} s each"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+
+    import synth
+
+    x = synth.config2_field()
+    planes = max(1, min(SHAPE[0], 20))
+    for _ in range(args.warmup):
+        cpu_baseline(x, planes, 1)
+    t0 = time.perf_counter()
+    res = cpu_baseline(x, planes, args.steps)
+    total = time.perf_counter() - t0
+    ms = 1e3 * total / max(1, args.steps)
+    line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+i32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "eb_rel": EB_REL, "r_sp": R_SP,
+                       "sample_planes": planes},
+            "cpu_baseline": res,
+            "e2e": {"value": res["value"], "unit": "GB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    del np
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_1806_08901_gb300 import _build, rdsel as R
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    ctx = R.Context(dev.index)
+    stream = torch.cuda.current_stream()
+
+    x = synth.config2_field_torch(seed=synth.seed_for(2, rank), shape=SHAPE, device=dev)
+    n = x.numel()
+    nbytes = 4 * n
+    p = R.params(eb=EB_REL, r_sp=R_SP)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        ctx.evaluate(x, p, stream)
+    est_ref, truth_ref = ctx.evaluate(x, p, stream)
+
+    ctx.set_profiling(True)
+    ctx.reset_profile()
+    launches0 = ctx.launch_count()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(dev.index)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        ctx.evaluate(x, p, stream)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    clocks.stop()
+    launches = ctx.launch_count() - launches0
+    stats = ctx.kernel_stats()
+    ctx.set_profiling(False)
+    dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+
+    t = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev_ms_max = float(t.item())
+    value = world * nbytes * args.steps / (dev_ms_max / 1e3) / 1e9
+
+    # estimate-only throughput (rd_select: range + sampled ZFP + sampled SZ)
+    est_ms = []
+    for _ in range(min(args.steps, 50)):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.select(x, p, stream)
+        b.record(stream)
+        b.synchronize()
+        est_ms.append(a.elapsed_time(b))
+
+    # end to end through the C ABI from pinned host memory (H2D inside)
+    xh = torch.empty(x.shape, dtype=torch.float32, pin_memory=True)
+    xh.copy_(x)
+    e2e_s = []
+    for i in range(min(args.steps, 20) + 2):
+        t0 = time.perf_counter()
+        ctx.evaluate(xh, p, stream)
+        if i >= 2:
+            e2e_s.append(time.perf_counter() - t0)
+    e2e_val = world * nbytes / statistics.mean(e2e_s) / 1e9
+
+    peak, peak_kind = measured_peaks()
+    per_kernel = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": None}
+                  for k, v in stats.items() if v[1]}
+    total_k = sum(v[0] for v in stats.values())
+    for k, v in stats.items():
+        if v[1]:
+            per_kernel[k]["share"] = v[0] / total_k
+    dom = max(per_kernel, key=lambda k: per_kernel[k]["ms_per_launch"] * per_kernel[k]["launches"])
+    # algorithmic bytes per launch: each full pass reads the field once
+    alg_bytes = {"range": nbytes, "zfp_pass": nbytes, "sz_pass": nbytes}
+    ab = alg_bytes.get(dom, 0)
+    achieved = ab / (per_kernel[dom]["ms_per_launch"] / 1e3) / 1e9 if ab else 0.0
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": recorded_traffic(dom),
+                "alg_bytes_per_launch": ab}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+i32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "eb_rel": EB_REL, "r_sp": R_SP,
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": f"independent fields per rank x{world}"},
+        "roofline": roofline,
+        "frac_hbm_step": (3 * nbytes * args.steps / (dev_ms_max / 1e3) / 1e9) / peak,
+        "estimate_only": {"value": nbytes / (statistics.mean(est_ms) / 1e3) / 1e9, "unit": "GB/s",
+                          "ms": statistics.mean(est_ms)},
+        "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": C_RESULT_BYTES},
+        "gpu_launches": launches,
+        "kernels": per_kernel,
+        "wall_s": wall,
+        "clocks": clocks.summary(),
+        "result": {"selection": est_ref["selection"], "best_gt": truth_ref["best_gt"],
+                   "br_sz": est_ref["br_sz"], "br_zfp": est_ref["br_zfp"],
+                   "br_sz_gt": truth_ref["br_sz_gt"], "br_zfp_gt": truth_ref["br_zfp_gt"],
+                   "psnr_zfp": est_ref["psnr_zfp"], "psnr_zfp_gt": truth_ref["psnr_zfp_gt"]},
+    }
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(x.cpu().numpy(), args.cpu_planes, 1)
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# bytes of the result records read back per call (rd_result + rd_truth + status)
+def _result_bytes():
+    import ctypes as C
+
+    from paper_1806_08901_gb300 import rdsel as R
+
+    return C.sizeof(R.rd_result) + C.sizeof(R.rd_truth) + 4
+
+
+C_RESULT_BYTES = None
+
+if __name__ == "__main__":
+    C_RESULT_BYTES = _result_bytes()
+    main()

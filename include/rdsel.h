@@ -1,0 +1,214 @@
+/*
+ * rdsel.h -- C ABI of the GB300 library for online rate-distortion
+ * estimation and SZ-vs-ZFP selection (Tao et al., "Optimizing Lossy
+ * Compression Rate-Distortion from Automatic Online Selection between SZ and
+ * ZFP", arXiv 1806.08901).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Fields are float32, row-major with shape[ndim-1] the fastest axis,
+ *    ndim in {1,2,3}, every extent >= 1 and at most 2^31-1 points.  The
+ *    caller owns the field memory; the library never writes or frees it.
+ *    rd_field.location says whether `data` is a DEVICE pointer (the normal
+ *    case) or a HOST pointer, which the library then copies into a staging
+ *    buffer it owns inside the context.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Work is stream-ordered; every entry point synchronises that
+ *    stream before it returns and writes its result structs to caller-owned
+ *    host memory.
+ *  - Return value: RD_OK (0) or a negative RD_ERR_* code; on error the output
+ *    structs are zeroed except where stated.  Non-fatal conditions are
+ *    reported in the `flags` word of the outputs (RD_F_*).
+ *  - One context per host thread; calls on one context must not overlap.
+ *  - Every numeric output equals the CPU oracle's bit for bit, except the
+ *    float64 sums (PSNR, entropy, SSE) which agree to the tolerances stated
+ *    in the project's design notes (PSNR within 1e-6 relative).
+ */
+#ifndef RDSEL_H
+#define RDSEL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define RD_OK 0
+#define RD_ERR_INVALID_ARG (-1) /* bad pointer, shape, or parameter */
+#define RD_ERR_NONFINITE (-2)   /* the field holds a NaN or an infinity */
+#define RD_ERR_OOM (-3)         /* a device or pinned allocation failed */
+#define RD_ERR_BUDGET (-4)      /* the request exceeds the context's HBM budget */
+#define RD_ERR_CUDA (-5)        /* a CUDA runtime call failed */
+#define RD_ERR_TIMEOUT (-6)     /* a bounded device wait ran out */
+#define RD_ERR_RANGE (-7)       /* bin width not representable, or codes
+                                   would overflow (|x|/bin >= 2^27) */
+
+/* ---- parameter values ------------------------------------------------ */
+#define RD_EB_REL 0   /* eb is relative to the value range (Eq. psnr-sz) */
+#define RD_EB_ABS 1   /* eb is absolute */
+#define RD_EC_PAPER 0 /* 3 / 9 / 16 EC samples per 1D/2D/3D block */
+#define RD_EC_ALL 1   /* every coefficient of a sampled block */
+#define RD_SEL_PAPER 0   /* SZ iff entropy + offset < mean n_sb (Alg. 1 l.10) */
+#define RD_SEL_HUFFMAN 1 /* SZ iff Huffman bits/value < mean n_sb (exact) */
+#define RD_LOC_DEVICE 0
+#define RD_LOC_HOST 1
+
+/* ---- flags ----------------------------------------------------------- */
+#define RD_F_CONSTANT 1u        /* value range 0: nothing estimated, ZFP */
+#define RD_F_DELTA_CLAMPED 2u   /* sqrt(12 MSE_sp) > 2 eb_abs: bin = 2 eb_abs */
+#define RD_F_MSE_ZERO 4u        /* MSE_sp = 0: bin = 2 eb_abs */
+#define RD_F_TIE_BAND 8u        /* |BR_sz - BR_zfp| <= 1e-9: tie, ZFP */
+#define RD_F_PARTIAL_BLOCKS 16u /* some extent is not a multiple of 4 */
+
+#define RD_NSYM 65536 /* code alphabet: 0 = escape, q + 32768 otherwise */
+
+typedef struct rd_context rd_context;
+
+typedef struct {
+  const float* data;  /* field values (see location) */
+  int32_t ndim;       /* 1, 2 or 3 */
+  int32_t location;   /* RD_LOC_DEVICE | RD_LOC_HOST */
+  int64_t shape[3];   /* shape[0] slowest; entries >= ndim are ignored */
+} rd_field;
+
+/* Inputs of Algorithm 1: error bound eb_abs or eb_rel, sampling rates r_sp
+ * and r_sp^ec. */
+typedef struct {
+  double eb;            /* > 0; relative (RD_EB_REL) or absolute */
+  int32_t eb_mode;      /* RD_EB_REL | RD_EB_ABS */
+  int32_t ec_mode;      /* RD_EC_PAPER | RD_EC_ALL */
+  double r_sp;          /* block sampling rate in [1e-6, 1]; paper default 0.05 */
+  int32_t quant_radius; /* R in [1, 32768]: codes with |q| >= R escape */
+  int32_t sel_rule;     /* RD_SEL_PAPER | RD_SEL_HUFFMAN */
+  double sz_offset;     /* bits/value added to the SZ entropy; paper: 0.5 */
+} rd_params;
+
+/* Estimates of Algorithm 1 lines 2-12 for one field. */
+typedef struct {
+  float vmin, vmax;
+  double vr, eb_abs, r_sp_eff;
+  int32_t strides[3];          /* block sampling strides per axis */
+  int32_t minexp;              /* floor(log2 eb_abs) */
+  uint64_t n_blocks, n_sampled_blocks;
+  double br_zfp, psnr_zfp, mse_sp;  /* ZFP: mean n_sb, PSNR_sp, MSE_sp */
+  uint64_t zfp_s2;             /* doubled interpolated n_sb sum */
+  uint64_t zfp_npoints;        /* valid points in sampled blocks */
+  uint64_t zfp_ncoeff;         /* EC-sampled coefficients */
+  double delta;                /* SZ bin width from PSNR_sz = PSNR_zfp */
+  double br_sz, br_sz_huff, psnr_sz, entropy;
+  uint64_t sz_ns, sz_huff_bits, sz_nesc;
+  uint32_t sz_nsym;
+  int32_t selection;           /* s_i of Alg. 1 l.15: 0 = SZ, 1 = ZFP */
+  uint32_t flags;
+} rd_result;
+
+/* Full-field ground truth that judges the estimates. */
+typedef struct {
+  double eb_sz, delta;         /* SZ bound (= delta/2) and bin width */
+  double br_sz_gt, psnr_sz_gt, sse_sz, maxerr_sz;
+  uint64_t sz_bits_gt, sz_huff_gt, sz_nesc_gt;
+  uint32_t sz_nsym_gt;
+  double br_zfp_gt, psnr_zfp_gt, sse_zfp, maxerr_zfp;
+  uint64_t zfp_bits_gt;        /* exact fixed-accuracy bits, all blocks */
+  int32_t best_gt;             /* 0 = SZ, 1 = ZFP (lower measured bit-rate) */
+  uint32_t flags;
+} rd_truth;
+
+/* ---- context --------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  hbm_budget bounds the device
+ * memory the context may hold (0 = no bound); the fixed workspace (about
+ * 2 MB) is allocated here.  Errors: RD_ERR_INVALID_ARG (out NULL or bad
+ * device), RD_ERR_OOM, RD_ERR_BUDGET, RD_ERR_CUDA. */
+int32_t rd_context_create(int32_t device, size_t hbm_budget, rd_context** out);
+int32_t rd_context_destroy(rd_context* ctx);
+
+/* ---- the hot path (Algorithm 1 lines 2-12, and the ground truth) ---- */
+
+/* ZFP estimate, Alg. 1 lines 2-7 (Sections "Estimation Based on Dynamic
+ * Quantization" and "Estimation of compression error"): value range, block
+ * sampling at r_sp, per 4^d block exponent alignment, lifting transform,
+ * sequency order, negabinary bit planes; BR_zfp = mean interpolated n_sb
+ * over r_sp^ec-sampled coefficients; PSNR_zfp from the exact MSE_sp; and the
+ * SZ bin delta = sqrt(12 MSE_sp) from Eq. (psnr-pdf-linear).  Fills the ZFP
+ * fields, delta, vr, eb_abs and the sampling fields of *out. */
+int32_t rd_estimate_zfp(rd_context* ctx, const rd_field* field,
+                        const rd_params* params, rd_result* out, void* stream);
+
+/* SZ estimate, Alg. 1 lines 8-9 (Sections "Prediction-Based
+ * Transformation" and "Estimation Based on Static Quantization"): Lorenzo
+ * residuals of the points of sampled blocks from their original neighbours,
+ * linear quantisation with bin `delta` (<= 0: 2 eb_abs, SZ's own bin),
+ * 65536-symbol histogram, BR_sz = entropy + sz_offset (Eq. bitrate-sz),
+ * Huffman-coded bits, PSNR_sz (Eq. psnr-pdf-linear).  Fills the SZ fields,
+ * vr, eb_abs, delta and the sampling fields of *out. */
+int32_t rd_estimate_sz(rd_context* ctx, const rd_field* field,
+                       const rd_params* params, double delta, rd_result* out,
+                       void* stream);
+
+/* Algorithm 1 lines 2-12: both estimates and the selection s_i (SZ iff its
+ * estimated bit-rate is lower at the matched PSNR; ties go to ZFP). */
+int32_t rd_select(rd_context* ctx, const rd_field* field,
+                  const rd_params* params, rd_result* out, void* stream);
+
+/* Ground truth over every point: ZFP fixed accuracy at eb_abs (exact
+ * embedded-coding bits, reconstruction, SSE, max error) and SZ at the
+ * absolute bound eb_sz (prequantised codes, integer Lorenzo residuals,
+ * escapes, Huffman-coded bits, SSE, max error).  eb_sz <= 0 runs the ZFP
+ * estimate first and uses eb_sz = delta/2 (Alg. 1 l.13, read as delta/2). */
+int32_t rd_ground_truth(rd_context* ctx, const rd_field* field,
+                        const rd_params* params, double eb_sz,
+                        rd_truth* out, void* stream);
+
+/* rd_select followed by rd_ground_truth at delta/2, fused into three passes
+ * over the field (range; ZFP estimate + ZFP truth; SZ estimate + SZ truth).
+ * Either output may be NULL. */
+int32_t rd_evaluate(rd_context* ctx, const rd_field* field,
+                    const rd_params* params, rd_result* est,
+                    rd_truth* truth, void* stream);
+
+/* ---- inspection (same kernels, per-element outputs) ------------------ */
+
+/* Copy the histograms of the last SZ estimate / SZ ground truth run on this
+ * context into host arrays of RD_NSYM counts (either may be NULL). */
+int32_t rd_copy_histograms(rd_context* ctx, uint32_t* est_hist,
+                           uint32_t* gt_hist);
+
+/* Per-block ZFP records for every block (block order, last axis fastest)
+ * at absolute bound eb_abs, written to DEVICE arrays owned by the caller:
+ * emax[nblocks], prec[nblocks], bits[nblocks], and (optional, may be NULL)
+ * the negabinary coefficients in sequency order coeffs[nblocks * 4^ndim]. */
+int32_t rd_zfp_blocks(rd_context* ctx, const rd_field* field, double eb_abs,
+                      int32_t* emax, int32_t* prec, uint64_t* bits,
+                      uint32_t* coeffs, void* stream);
+
+/* Per-point SZ symbols at bin width delta, written to DEVICE arrays of N
+ * entries owned by the caller (each may be NULL): est_sym = estimator symbol
+ * for points of blocks sampled with `strides` (int32[ndim]), -1 elsewhere;
+ * gt_sym = ground-truth symbol; recon = ground-truth reconstruction. */
+int32_t rd_sz_symbols(rd_context* ctx, const rd_field* field, double delta,
+                      int32_t quant_radius, const int32_t* strides,
+                      int32_t* est_sym, int32_t* gt_sym, float* recon,
+                      void* stream);
+
+/* ---- profiling ------------------------------------------------------- */
+
+/* Record CUDA events around every kernel launch of this context (off by
+ * default).  rd_kernel_stat reports, for i = 0, 1, ..., the kernel's name,
+ * its accumulated device time in milliseconds and its launch count since
+ * the last reset; RD_ERR_INVALID_ARG past the last kernel. */
+int32_t rd_set_profiling(rd_context* ctx, int32_t on);
+int32_t rd_reset_profile(rd_context* ctx);
+int32_t rd_kernel_stat(rd_context* ctx, int32_t i, const char** name,
+                       double* total_ms, int64_t* launches);
+/* Kernel launches made by this context since creation. */
+int64_t rd_launch_count(rd_context* ctx);
+
+const char* rd_status_string(int32_t status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RDSEL_H */

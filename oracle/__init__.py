@@ -124,6 +124,7 @@ def lib():
         sig = {
             "rdo_select": [f32p, C.c_int, i64p, P(Params), P(Result), u32p],
             "rdo_ground_truth": [f32p, C.c_int, i64p, P(Params), C.c_double, P(Truth), u32p],
+            "rdo_estimate_sz": [f32p, C.c_int, i64p, P(Params), C.c_double, P(Result), u32p],
             "rdo_zfp_blocks": [f32p, C.c_int, i64p, C.c_double, i32p, i32p, u64p, u32p],
             "rdo_sz_symbols": [f32p, C.c_int, i64p, C.c_double, C.c_int32, i32p, i32p, i32p, f32p],
             "rdo_zfp_block": [f32p, C.c_int, C.c_int32, C.c_int32, P(BlockOut)],
@@ -191,6 +192,21 @@ def select(x: np.ndarray, p: Params, want_hist: bool = False):
                           _ptr(h, C.c_uint32) if h is not None else None)
     if rc:
         raise OracleError(rc, "rdo_select")
+    d = _todict(r)
+    if want_hist:
+        d["hist"] = h
+    return d
+
+
+def estimate_sz(x: np.ndarray, p: Params, delta: float = 0.0, want_hist: bool = False):
+    x, shape = _field(x)
+    r = Result()
+    h = np.zeros(NSYM, dtype=np.uint32) if want_hist else None
+    rc = lib().rdo_estimate_sz(_ptr(x, C.c_float), x.ndim, _ptr(shape, C.c_int64),
+                               C.byref(p), float(delta), C.byref(r),
+                               _ptr(h, C.c_uint32) if h is not None else None)
+    if rc:
+        raise OracleError(rc, "rdo_estimate_sz")
     d = _todict(r)
     if want_hist:
         d["hist"] = h

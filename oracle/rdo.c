@@ -604,6 +604,20 @@ static int check_params(const rdo_params* p) {
   return RDO_OK;
 }
 
+/* Sampled blocks and the valid points inside them, by enumeration. */
+static void sampling_counts(const field_t* f, const int32_t* strides,
+                            uint64_t* nsb, uint64_t* npts) {
+  int64_t b[3] = {0, 0, 0};
+  int nb = 1 << (2 * f->d);
+  *nsb = 0;
+  *npts = 0;
+  do {
+    if (!block_is_sampled(f, b, strides)) continue;
+    (*nsb)++;
+    for (int t = 0; t < nb; t++) *npts += (uint64_t)block_has_valid(f, b, t);
+  } while (next_block(f, b));
+}
+
 int rdo_sampling(int ndim, const int64_t* shape, double r_sp,
                  int32_t* strides, uint64_t* n_sampled_blocks,
                  uint64_t* n_points) {
@@ -614,13 +628,7 @@ int rdo_sampling(int ndim, const int64_t* shape, double r_sp,
   if (!(r_sp >= 1e-6 && r_sp <= 1.0) || !strides) return RDO_ERR_INVALID_ARG;
   sampling_strides(ndim, r_sp, strides);
   uint64_t nsb = 0, npts = 0;
-  int64_t b[3] = {0, 0, 0};
-  int nb = 1 << (2 * ndim);
-  do {
-    if (!block_is_sampled(&f, b, strides)) continue;
-    nsb++;
-    for (int t = 0; t < nb; t++) npts += (uint64_t)block_has_valid(&f, b, t);
-  } while (next_block(&f, b));
+  sampling_counts(&f, strides, &nsb, &npts);
   if (n_sampled_blocks) *n_sampled_blocks = nsb;
   if (n_points) *n_points = npts;
   return RDO_OK;
@@ -734,6 +742,87 @@ static double psnr_of(double vr, double mse) {
 /* Algorithm 1, lines 2-12, for one field.                                  */
 /* ------------------------------------------------------------------------ */
 
+/* Alg. 1 line 8: histogram of quantised Lorenzo residuals of every valid
+ * point of every sampled block (strides in r->strides); line 9: Eq.
+ * (bitrate-sz) = entropy, plus the 0.5-bit offset of the evaluation section,
+ * and the Huffman-coded cost of the same histogram.  h is zeroed by caller. */
+static void sz_estimate(const field_t* f, const rdo_params* p, float inv,
+                        rdo_result* r, uint32_t* h) {
+  int nb = 1 << (2 * f->d);
+  int64_t bb[3] = {0, 0, 0};
+  do {
+    if (!block_is_sampled(f, bb, r->strides)) continue;
+    for (int t = 0; t < nb; t++) {
+      if (!block_has_valid(f, bb, t)) continue;
+      int64_t idx[3];
+      int tt = t;
+      for (int k = f->d - 1; k >= 0; k--) {
+        idx[k] = 4 * bb[k] + (tt & 3);
+        tt >>= 2;
+      }
+      h[est_symbol(est_residual(f, idx), inv, p->quant_radius)]++;
+    }
+  } while (next_block(f, bb));
+  uint64_t ns = 0;
+  for (int s = 0; s < RDO_NSYM; s++) ns += h[s];
+  r->sz_ns = ns;
+  r->entropy = entropy_bits(h, ns);
+  r->br_sz = r->entropy + p->sz_offset;
+  huffman_of_hist(h, &r->sz_huff_bits, &r->sz_nsym);
+  r->sz_nesc = h[0];
+  r->br_sz_huff = (double)(r->sz_huff_bits + 32ull * h[0]) / (double)ns;
+}
+
+/* SZ estimate alone at an explicit bin width (delta <= 0: 2 eb_abs, SZ's own
+ * bin, for which Eq. (psnr-sz) gives the PSNR). */
+int rdo_estimate_sz(const float* x, int ndim, const int64_t* shape,
+                    const rdo_params* p, double delta, rdo_result* r,
+                    uint32_t* hist_est) {
+  field_t f;
+  int rc = field_init(&f, x, ndim, shape);
+  if (rc) return rc;
+  if ((rc = check_params(p))) return rc;
+  if (!r || isnan(delta)) return RDO_ERR_INVALID_ARG;
+  memset(r, 0, sizeof(*r));
+  if (hist_est) memset(hist_est, 0, RDO_NSYM * sizeof(uint32_t));
+  float vmin, vmax;
+  if ((rc = value_range(&f, &vmin, &vmax))) return rc;
+  r->vmin = vmin;
+  r->vmax = vmax;
+  r->vr = (double)vmax - (double)vmin;
+  r->eb_abs = (p->eb_mode == RDO_EB_REL) ? p->eb * r->vr : p->eb;
+  for (int k = 0; k < f.d; k++)
+    if (f.n[k] % 4) r->flags |= RDO_F_PARTIAL_BLOCKS;
+  uint64_t nblocks = 1;
+  for (int k = 0; k < f.d; k++) nblocks *= (uint64_t)blocks_along(f.n[k]);
+  r->n_blocks = nblocks;
+  sampling_strides(f.d, p->r_sp, r->strides);
+  if (r->vr == 0.0) {
+    r->flags |= RDO_F_CONSTANT;
+    r->psnr_zfp = INFINITY;
+    r->psnr_sz = INFINITY;
+    r->selection = 1;
+    return RDO_OK;
+  }
+  if (!(r->eb_abs > 0.0) || !isfinite(r->eb_abs)) return RDO_ERR_INVALID_ARG;
+  r->minexp = floor_log2(r->eb_abs);
+  uint64_t nsb = 0, npts = 0;
+  sampling_counts(&f, r->strides, &nsb, &npts);
+  r->n_sampled_blocks = nsb;
+  r->r_sp_eff = (double)nsb / (double)nblocks;
+  r->zfp_npoints = npts;
+  r->delta = delta > 0.0 ? delta : 2.0 * r->eb_abs;
+  r->psnr_sz = 20.0 * log10(r->vr / r->delta) + 10.0 * log10(12.0);
+  sz_quant_t qz;
+  if ((rc = sz_quant_init(r->delta, &qz))) return rc;
+  uint32_t* h = (uint32_t*)calloc(RDO_NSYM, sizeof(uint32_t));
+  if (!h) return RDO_ERR_INVALID_ARG;
+  sz_estimate(&f, p, qz.inv, r, h);
+  if (hist_est) memcpy(hist_est, h, RDO_NSYM * sizeof(uint32_t));
+  free(h);
+  return RDO_OK;
+}
+
 static uint64_t u128_lt(uint64_t a_hi, uint64_t a_lo, uint64_t b_hi,
                         uint64_t b_lo) {
   return a_hi < b_hi || (a_hi == b_hi && a_lo < b_lo);
@@ -840,34 +929,11 @@ int rdo_select(const float* x, int ndim, const int64_t* shape,
   sz_quant_t qz;
   if ((rc = sz_quant_init(delta, &qz))) return rc;
 
-  /* line 8: histogram of quantised Lorenzo residuals on sampled blocks */
+  /* lines 8-9 */
   uint32_t* h = (uint32_t*)calloc(RDO_NSYM, sizeof(uint32_t));
   if (!h) return RDO_ERR_INVALID_ARG;
-  int64_t bb[3] = {0, 0, 0};
-  do {
-    if (!block_is_sampled(&f, bb, r->strides)) continue;
-    for (int t = 0; t < nb; t++) {
-      if (!block_has_valid(&f, bb, t)) continue;
-      int64_t idx[3];
-      int tt = t;
-      for (int k = f.d - 1; k >= 0; k--) {
-        idx[k] = 4 * bb[k] + (tt & 3);
-        tt >>= 2;
-      }
-      h[est_symbol(est_residual(&f, idx), qz.inv, p->quant_radius)]++;
-    }
-  } while (next_block(&f, bb));
-
-  /* line 9: Eq. (bitrate-sz) = entropy, plus the 0.5-bit offset of the
-   * evaluation section; and the Huffman-coded cost of the same histogram */
-  uint64_t ns = 0;
-  for (int s = 0; s < RDO_NSYM; s++) ns += h[s];
-  r->sz_ns = ns;
-  r->entropy = entropy_bits(h, ns);
-  r->br_sz = r->entropy + p->sz_offset;
-  huffman_of_hist(h, &r->sz_huff_bits, &r->sz_nsym);
-  r->sz_nesc = h[0];
-  r->br_sz_huff = (double)(r->sz_huff_bits + 32ull * h[0]) / (double)ns;
+  sz_estimate(&f, p, qz.inv, r, h);
+  uint64_t ns = r->sz_ns;
 
   /* lines 10-12: SZ iff its estimated bit-rate is lower; equal -> ZFP */
   if (p->sel_rule == RDO_SEL_PAPER) {

@@ -103,6 +103,12 @@ typedef struct {
 int rdo_select(const float* x, int ndim, const int64_t* shape,
                const rdo_params* p, rdo_result* r, uint32_t* hist_est);
 
+/* SZ estimate alone (Alg. 1 lines 8-9) at bin width delta; delta <= 0 uses
+ * 2 eb_abs.  Fills the SZ, range and sampling fields of r. */
+int rdo_estimate_sz(const float* x, int ndim, const int64_t* shape,
+                    const rdo_params* p, double delta, rdo_result* r,
+                    uint32_t* hist_est);
+
 /* Full-field ground truth. eb_sz > 0: SZ runs at that bound; eb_sz <= 0: at
  * delta/2 from rdo_select on the same field and params. */
 int rdo_ground_truth(const float* x, int ndim, const int64_t* shape,

@@ -1,0 +1,210 @@
+// rd_device.cuh -- device helpers of the rate-distortion kernels: the ZFP
+// block transform in 32-bit two's complement, the sequency permutation,
+// negabinary coding, power-of-two float scaling and histogram updates.
+#pragma once
+
+#include <stdint.h>
+
+#include "rd_internal.cuh"
+
+namespace rdk {
+
+// ---------------------------------------------------------------------------
+// 32-bit wrapping integer arithmetic (the transform is defined modulo 2^32).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int wadd(int a, int b) { return (int)((unsigned)a + (unsigned)b); }
+__device__ __forceinline__ int wsub(int a, int b) { return (int)((unsigned)a - (unsigned)b); }
+__device__ __forceinline__ int wdbl(int a) { return (int)((unsigned)a << 1); }
+__device__ __forceinline__ int asr1(int a) { return a >> 1; }  // floor(a / 2)
+
+// ZFP's decorrelating 4-point transform (zfp publication, Lindstrom 2014):
+// forward matrix (1/16)[[4,4,4,4],[5,1,-1,-5],[-4,4,4,-4],[-2,6,-6,2]] as a
+// lifting scheme (Section "Block Orthogonal Transformation" applies it along
+// every axis of a 4^d block).
+__device__ __forceinline__ void fwd_lift(int& a, int& b, int& c, int& d) {
+  a = asr1(wadd(a, d)); d = wsub(d, a);   // outer pair: mean, half-difference
+  c = asr1(wadd(c, b)); b = wsub(b, c);   // inner pair
+  a = asr1(wadd(a, c)); c = wsub(c, a);   // the two means
+  d = asr1(wadd(d, b)); b = wsub(b, d);   // the two differences
+  d = wadd(d, asr1(b)); b = wsub(b, asr1(d));  // rotate the odd terms
+}
+
+// Exact inverse of every lifting step, applied in reverse order.
+__device__ __forceinline__ void inv_lift(int& a, int& b, int& c, int& d) {
+  b = wadd(b, asr1(d)); d = wsub(d, asr1(b));
+  b = wadd(b, d); d = wsub(wdbl(d), b);
+  c = wadd(c, a); a = wsub(wdbl(a), c);
+  b = wadd(b, c); c = wsub(wdbl(c), b);
+  d = wadd(d, a); a = wsub(wdbl(a), d);
+}
+
+// Apply the transform along axis `A` of a 4^D block held in registers
+// (block index t = sum_k t_k 4^(D-1-k), last axis fastest).
+template <int D, int A, bool INV>
+__device__ __forceinline__ void lift_axis(int* c) {
+  constexpr int NB = 1 << (2 * D);
+  constexpr int ST = 1 << (2 * (D - 1 - A));
+#pragma unroll
+  for (int t = 0; t < NB; t++) {
+    if (((t / ST) & 3) == 0) {
+      if (INV)
+        inv_lift(c[t], c[t + ST], c[t + 2 * ST], c[t + 3 * ST]);
+      else
+        fwd_lift(c[t], c[t + ST], c[t + 2 * ST], c[t + 3 * ST]);
+    }
+  }
+}
+
+// Forward: fastest axis first.  Inverse: slowest axis first.
+template <int D>
+__device__ __forceinline__ void fwd_xform(int* c) {
+  lift_axis<D, D - 1, false>(c);
+  if constexpr (D >= 2) lift_axis<D, D - 2, false>(c);
+  if constexpr (D >= 3) lift_axis<D, D - 3, false>(c);
+}
+
+template <int D>
+__device__ __forceinline__ void inv_xform(int* c) {
+  if constexpr (D >= 3) lift_axis<D, D - 3, true>(c);
+  if constexpr (D >= 2) lift_axis<D, D - 2, true>(c);
+  lift_axis<D, D - 1, true>(c);
+}
+
+// ---------------------------------------------------------------------------
+// Sequency order, built at compile time: block indices ordered by the sum of
+// their per-axis indices, then the sum of squares, then lexicographically
+// with the slowest axis first.
+// ---------------------------------------------------------------------------
+template <int D>
+struct Sequency {
+  static constexpr int NB = 1 << (2 * D);
+  int perm[NB];  // perm[p] = block index of the coefficient at sequency p
+
+  static constexpr int digit(int t, int k) { return (t >> (2 * (D - 1 - k))) & 3; }
+  static constexpr bool before(int a, int b) {
+    int sa = 0, sb = 0, qa = 0, qb = 0;
+    for (int k = 0; k < D; k++) {
+      sa += digit(a, k); sb += digit(b, k);
+      qa += digit(a, k) * digit(a, k); qb += digit(b, k) * digit(b, k);
+    }
+    if (sa != sb) return sa < sb;
+    if (qa != qb) return qa < qb;
+    for (int k = 0; k < D; k++)
+      if (digit(a, k) != digit(b, k)) return digit(a, k) < digit(b, k);
+    return false;
+  }
+  constexpr Sequency() : perm() {
+    for (int t = 0; t < NB; t++) perm[t] = t;
+    for (int i = 1; i < NB; i++) {
+      int v = perm[i];
+      int j = i - 1;
+      while (j >= 0 && before(v, perm[j])) {
+        perm[j + 1] = perm[j];
+        j--;
+      }
+      perm[j + 1] = v;
+    }
+  }
+};
+
+// Embedded-coding sample positions: m of the 4^D sequency positions spread
+// evenly, p_j = floor((j (NB-1) + floor((m-1)/2)) / (m-1)); m = 3/9/16.
+template <int D>
+struct EcPositions {
+  static constexpr int NB = 1 << (2 * D);
+  static constexpr int M = D == 1 ? 3 : D == 2 ? 9 : 16;
+  int pos[M];
+  constexpr EcPositions() : pos() {
+    for (int j = 0; j < M; j++) pos[j] = (j * (NB - 1) + (M - 1) / 2) / (M - 1);
+  }
+};
+
+// Negabinary: base -2 digits of a two's complement integer.
+__device__ __forceinline__ unsigned int to_negabinary(int i) {
+  return ((unsigned)i + 0xaaaaaaaau) ^ 0xaaaaaaaau;
+}
+__device__ __forceinline__ int from_negabinary(unsigned int u) {
+  return (int)((u ^ 0xaaaaaaaau) - 0xaaaaaaaau);
+}
+
+// 2^e as a float for -126 <= e <= 127.
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
+
+// x * 2^e rounded once, for -156 <= e <= 127 (a two-step product whose first
+// factor keeps the intermediate in the normal range).
+__device__ __forceinline__ float scale_pow2(float x, int e) {
+  if (e >= -126) return __fmul_rn(x, pow2f(e));
+  return __fmul_rn(__fmul_rn(x, pow2f(e + 64)), pow2f(-64));
+}
+
+// x * 2^k for -252 <= k <= 254 (two products outside the normal range of 2^k).
+__device__ __forceinline__ float mul_pow2(float x, int k) {
+  if (k > 127) return __fmul_rn(__fmul_rn(x, pow2f(127)), pow2f(k - 127));
+  if (k < -126) return __fmul_rn(__fmul_rn(x, pow2f(-126)), pow2f(k + 126));
+  return __fmul_rn(x, pow2f(k));
+}
+
+// trunc(x * 2^e) for the block-floating-point cast, -98 <= e <= 156, where
+// |x * 2^e| < 2^30.  Results below one may round but truncate to zero.
+__device__ __forceinline__ int cast_scaled(float x, int e) {
+  float y = (e <= 127) ? __fmul_rn(x, pow2f(e))
+                       : __fmul_rn(__fmul_rn(x, pow2f(127)), pow2f(e - 127));
+  return __float2int_rz(y);
+}
+
+// Ordered unsigned key of a float: monotone in the float's value.
+__device__ __forceinline__ unsigned int float_key(float v) {
+  unsigned int b = __float_as_uint(v);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float key_float(unsigned int k) {
+  unsigned int b = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+  return __uint_as_float(b);
+}
+
+// Histogram update: bins near the centre go to a per-CTA shared window, the
+// rest straight to global memory.  Lanes of a warp with the same symbol are
+// merged into one atomic.
+__device__ __forceinline__ void hist_add(uint32_t* s_win, uint32_t* g_hist, int sym,
+                                         unsigned mask) {
+  unsigned same = __match_any_sync(mask, sym);
+  int leader = __ffs(same) - 1;
+  if ((int)(threadIdx.x & 31) == leader) {
+    unsigned cnt = __popc(same);
+    int wi = sym - kHistWinLo;
+    if ((unsigned)wi < (unsigned)kHistWin)
+      atomicAdd(&s_win[wi], cnt);
+    else
+      atomicAdd(&g_hist[sym], cnt);
+  }
+}
+
+__device__ __forceinline__ void hist_flush(const uint32_t* s_win, uint32_t* g_hist) {
+  for (int i = threadIdx.x; i < kHistWin; i += blockDim.x) {
+    uint32_t c = s_win[i];
+    if (c) atomicAdd(&g_hist[kHistWinLo + i], c);
+  }
+}
+
+// 128-bit add with carry into a (lo, hi) pair of 64-bit words.
+__device__ __forceinline__ void atomic_add_u128(unsigned long long* lo, unsigned long long* hi,
+                                                unsigned long long vlo, unsigned long long vhi) {
+  unsigned long long old = atomicAdd(lo, vlo);
+  unsigned long long carry = (old + vlo < old) ? 1ull : 0ull;
+  if (vhi + carry) atomicAdd(hi, vhi + carry);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+}  // namespace rdk

@@ -1,0 +1,146 @@
+// rd_internal.cuh -- shared declarations of the rate-distortion estimation
+// library's CUDA translation units (device workspace, field descriptor,
+// kernel launchers).  Not part of the public ABI (include/rdsel.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rdsel.h"
+
+namespace rdk {
+
+constexpr int kNsym = RD_NSYM;
+constexpr int kCenter = 32768;       // symbol of code 0
+constexpr int kMseBins = 272;        // bin index e + 126, e = emax + d in [-126, 131]
+constexpr int kMaxGrid = 4096;       // upper bound of CTAs of a reducing pass
+constexpr int kHistWin = 4096;       // shared-memory window of histogram bins
+constexpr int kHistWinLo = kCenter - kHistWin / 2;
+constexpr int kEntropyCtas = kNsym / 1024;
+constexpr int kHuffSmemKeys = 32768; // sort in shared memory up to this many symbols
+
+// Scalars produced and consumed on the device within one call: nothing
+// data-dependent (value range, bin width, error flags) leaves the device
+// until the final result copy.
+struct Scalars {
+  int32_t status;        // RD_OK or an RD_ERR_* code raised on the device
+  uint32_t flags;        // RD_F_*
+  int32_t constant;      // value range is zero
+  int32_t minexp;        // floor(log2 eb_abs)
+  uint32_t min_key, max_key, nonfinite, pad0;
+  float vmin, vmax, amax;  // amax = max(|vmin|, |vmax|)
+  float w, inv, tau;       // SZ quantiser: bin, 1/bin, escape threshold
+  double vr, eb_abs, delta, mse_sp;
+  unsigned long long s2;         // doubled interpolated n_sb sum
+  unsigned long long zfp_bits;   // exact ZFP fixed-accuracy bits
+  unsigned int zfp_maxerr;       // float bits of max |x - xhat|
+  unsigned int sz_maxerr;
+  unsigned long long mse_lo[kMseBins];  // 128-bit sums of d^2 per exponent
+  unsigned long long mse_hi[kMseBins];
+};
+
+struct HuffOut {
+  unsigned long long ns;    // total count
+  unsigned long long cost;  // Huffman-coded bits (sum of internal weights)
+  uint32_t nsym;            // nonzero symbols
+  uint32_t pad;
+};
+
+struct Workspace {
+  Scalars sc;
+  uint32_t hist[2][kNsym];            // 0 = SZ estimate, 1 = SZ ground truth
+  double ent_part[2][kEntropyCtas];   // partial sums of h log2 h
+  HuffOut huff[2];
+  double zfp_sse[kMaxGrid];           // per-CTA partial sums (fixed order)
+  double sz_sse[kMaxGrid];
+  uint32_t sort_scratch[2][kNsym];    // Huffman sort buffer when K is large
+  rd_result res;
+  rd_truth truth;
+};
+
+// Field geometry, passed by value to every kernel.  Axis 0 is the slowest;
+// only the first d entries are meaningful.
+struct FieldDev {
+  const float* x;
+  int d;
+  int vec_ok;           // rows along the fastest axis are 16-byte aligned
+  int n[3];             // extents
+  int B[3];             // blocks per axis, ceil(n / 4)
+  int s[3];             // block sampling strides
+  int L[3];             // sampled blocks per axis, ceil(B / s)
+  long long N;          // points
+  long long nblocks;    // blocks
+  long long nsampled;   // sampled blocks
+};
+
+struct ParamsDev {
+  double eb;
+  int eb_mode;
+  int ec_mode;
+  int R;
+  int sel_rule;
+  double sz_offset;
+};
+
+// Grid bounds computed once per context from the occupancy calculator.
+struct LaunchCfg {
+  int num_sms;
+  int zfp_ctas;   // resident CTAs of the ZFP pass (all SMs)
+  int sz_ctas;
+  int range_ctas;
+};
+
+enum KernelId {
+  K_RESET = 0,
+  K_RANGE,
+  K_PREPARE,
+  K_ZFP,
+  K_DELTA,
+  K_SZ_EST,
+  K_SZ_GT,
+  K_ENTROPY,
+  K_HUFFMAN,
+  K_FINISH,
+  K_ZFP_INSPECT,
+  K_SZ_INSPECT,
+  K_COUNT
+};
+
+// Passes of one call, as flags.
+enum PassFlags : int {
+  P_ZFP_EST = 1,   // ZFP estimate over sampled blocks
+  P_ZFP_GT = 2,    // ZFP truth over every block
+  P_SZ_EST = 4,    // SZ estimate over points of sampled blocks
+  P_SZ_GT = 8,     // SZ truth over every point
+};
+
+enum DeltaMode { DELTA_FROM_MSE = 0, DELTA_EXPLICIT = 1, DELTA_FROM_EB_SZ = 2 };
+
+// ---- launchers (each returns the cudaError_t of the launch) ----
+cudaError_t launch_reset(Workspace* ws, cudaStream_t s);
+cudaError_t launch_range(const FieldDev& f, Workspace* ws, int ctas, cudaStream_t s);
+cudaError_t launch_prepare(const ParamsDev& p, Workspace* ws, cudaStream_t s);
+cudaError_t launch_zfp(const FieldDev& f, const ParamsDev& p, int passes,
+                       Workspace* ws, int ctas, cudaStream_t s, int* grid_used);
+cudaError_t launch_delta(const ParamsDev& p, Workspace* ws, int mode, double arg,
+                         int need_quant, int need_gt, unsigned long long ncoeff,
+                         unsigned long long npoints, cudaStream_t s);
+cudaError_t launch_sz_est(const FieldDev& f, const ParamsDev& p, Workspace* ws,
+                          int ctas, cudaStream_t s);
+cudaError_t launch_sz_gt(const FieldDev& f, const ParamsDev& p, int with_est,
+                         Workspace* ws, int ctas, cudaStream_t s, int* grid_used);
+cudaError_t launch_entropy(Workspace* ws, int which_mask, cudaStream_t s);
+cudaError_t launch_huffman(Workspace* ws, int which_mask, cudaStream_t s);
+cudaError_t launch_finish(const ParamsDev& p, Workspace* ws, int passes,
+                          int zfp_parts, int sz_parts, long long npoints_all,
+                          unsigned long long zfp_npoints, cudaStream_t s);
+cudaError_t launch_zfp_inspect(const FieldDev& f, double eb_abs, int32_t* emax,
+                               int32_t* prec, uint64_t* bits, uint32_t* coeffs,
+                               cudaStream_t s);
+cudaError_t launch_sz_inspect_q(const FieldDev& f, float w, float inv, float tau, int R,
+                                int32_t* est_sym, int32_t* gt_sym, float* recon,
+                                int use_strides, cudaStream_t s);
+int zfp_occupancy(int d, int num_sms);
+int sz_occupancy(int d, int num_sms);
+
+}  // namespace rdk

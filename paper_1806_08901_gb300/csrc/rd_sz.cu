@@ -1,0 +1,300 @@
+// rd_sz.cu -- SZ passes.
+//   estimator (Alg. 1 line 8; Sections "Prediction-Based Transformation" and
+//     "Estimation Based on Static Quantization"): every valid point of every
+//     sampled block, Lorenzo residual from its ORIGINAL neighbours (zero
+//     outside the domain) evaluated in float32 as nested first differences,
+//     last axis first; code q = rint(r * (1/delta)); symbol q + 32768 when
+//     |q| < R, else the escape symbol 0; 65536-bin histogram.
+//   ground truth (every point, bound delta/2): prequantised code
+//     Q = rint(x * (1/w)), reconstruction float(Q) * w, escape when the float
+//     error exceeds tau or the integer Lorenzo residual of Q reaches R;
+//     histogram of residual symbols, SSE and max error.
+#include <stdint.h>
+
+#include "rd_device.cuh"
+
+namespace rdk {
+
+constexpr int kSzThreads = 256;
+
+struct Nbr {
+  // the 2^D corner values of the Lorenzo cell ending at a point; index bit k
+  // set = one step back along axis D-1-k (bit 0 = fastest axis)
+  float v[8];
+};
+
+template <int D>
+__device__ __forceinline__ Nbr gather_cell(const FieldDev& f, const int* g) {
+  Nbr c;
+  constexpr int NC = 1 << D;
+#pragma unroll
+  for (int m = 0; m < NC; m++) {
+    long long idx = 0;
+    bool inside = true;
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+      int back = (m >> (D - 1 - k)) & 1;
+      int gk = g[k] - back;
+      inside = inside && gk >= 0;
+      idx = idx * f.n[k] + gk;
+    }
+    c.v[m] = inside ? __ldg(f.x + idx) : 0.0f;
+  }
+  return c;
+}
+
+// x - Lorenzo(x) as nested float32 differences, last axis first:
+//   1D: v0 - v1
+//   2D: (v00 - v01) - (v10 - v11)
+//   3D: 2D form on the current plane minus the 2D form on the plane behind.
+template <int D>
+__device__ __forceinline__ float est_residual(const Nbr& c) {
+  if constexpr (D == 1) {
+    return __fsub_rn(c.v[0], c.v[1]);
+  } else if constexpr (D == 2) {
+    return __fsub_rn(__fsub_rn(c.v[0], c.v[1]), __fsub_rn(c.v[2], c.v[3]));
+  } else {
+    float p0 = __fsub_rn(__fsub_rn(c.v[0], c.v[1]), __fsub_rn(c.v[2], c.v[3]));
+    float p1 = __fsub_rn(__fsub_rn(c.v[4], c.v[5]), __fsub_rn(c.v[6], c.v[7]));
+    return __fsub_rn(p0, p1);
+  }
+}
+
+__device__ __forceinline__ int est_symbol(float r, float inv, int R) {
+  float q = rintf(__fmul_rn(r, inv));
+  return fabsf(q) < (float)R ? (int)q + kCenter : 0;
+}
+
+// Integer Lorenzo residual of the prequantised codes: sum over the cell's
+// corners of (-1)^(steps back) Q.
+template <int D>
+__device__ __forceinline__ int gt_residual(const Nbr& c, float inv) {
+  int r = 0;
+#pragma unroll
+  for (int m = 0; m < (1 << D); m++) {
+    int q = __float2int_rn(__fmul_rn(c.v[m], inv));
+    r += (__popc(m) & 1) ? -q : q;
+  }
+  return r;
+}
+
+template <int D>
+__device__ __forceinline__ void point_coords(const FieldDev& f, long long u, int* g) {
+  long long r = u;
+#pragma unroll
+  for (int k = D - 1; k >= 0; k--) {
+    g[k] = (int)(r % f.n[k]);
+    r /= f.n[k];
+  }
+}
+
+template <int D>
+__device__ __forceinline__ bool in_sampled_block(const FieldDev& f, const int* g) {
+  bool s = true;
+#pragma unroll
+  for (int k = 0; k < D; k++) s = s && (((g[k] >> 2) % f.s[k]) == 0);
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// Estimator over the points of sampled blocks only.
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(kSzThreads) k_sz_est(FieldDev f, ParamsDev p, Workspace* ws) {
+  constexpr int NB = 1 << (2 * D);
+  __shared__ uint32_t s_win[kHistWin];
+  const Scalars& sc = ws->sc;
+  if (sc.status != RD_OK || sc.constant) return;
+  for (int i = threadIdx.x; i < kHistWin; i += blockDim.x) s_win[i] = 0u;
+  __syncthreads();
+  const float inv = sc.inv;
+  const long long units = f.nsampled * NB;
+  for (long long u0 = (long long)blockIdx.x * blockDim.x; u0 < units;
+       u0 += (long long)gridDim.x * blockDim.x) {
+    const long long u = u0 + threadIdx.x;
+    bool ok = u < units;
+    int g[3] = {0, 0, 0};
+    if (ok) {
+      long long sb = u / NB;
+      int t = (int)(u % NB);
+      long long r = sb;
+#pragma unroll
+      for (int k = D - 1; k >= 0; k--) {
+        int l = (int)(r % f.L[k]);
+        r /= f.L[k];
+        int tk = (t >> (2 * (D - 1 - k))) & 3;
+        g[k] = 4 * l * f.s[k] + tk;
+        ok = ok && g[k] < f.n[k];
+      }
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, ok);
+    if (ok) {
+      Nbr c = gather_cell<D>(f, g);
+      hist_add(s_win, ws->hist[0], est_symbol(est_residual<D>(c), inv, p.R), mask);
+    }
+  }
+  __syncthreads();
+  hist_flush(s_win, ws->hist[0]);
+}
+
+// ---------------------------------------------------------------------------
+// Ground truth over every point, with the estimator fused for points of
+// sampled blocks when requested.
+// ---------------------------------------------------------------------------
+template <int D, bool EST>
+__global__ void __launch_bounds__(kSzThreads) k_sz_gt(FieldDev f, ParamsDev p, Workspace* ws) {
+  __shared__ uint32_t s_gt[kHistWin];
+  __shared__ uint32_t s_est[EST ? kHistWin : 1];
+  __shared__ double s_sse[kSzThreads / 32];
+  __shared__ float s_max[kSzThreads / 32];
+  const Scalars& sc = ws->sc;
+  if (sc.status != RD_OK || sc.constant) return;
+  for (int i = threadIdx.x; i < kHistWin; i += blockDim.x) {
+    s_gt[i] = 0u;
+    if (EST) s_est[i] = 0u;
+  }
+  __syncthreads();
+  const float w = sc.w, inv = sc.inv, tau = sc.tau;
+  const int R = p.R;
+  double my_sse = 0.0;
+  float my_max = 0.0f;
+  for (long long u0 = (long long)blockIdx.x * blockDim.x; u0 < f.N;
+       u0 += (long long)gridDim.x * blockDim.x) {
+    const long long u = u0 + threadIdx.x;
+    const bool ok = u < f.N;
+    const unsigned mask = __ballot_sync(0xffffffffu, ok);
+    if (!ok) continue;
+    int g[3] = {0, 0, 0};
+    point_coords<D>(f, u, g);
+    Nbr c = gather_cell<D>(f, g);
+    const float x = c.v[0];
+    const int q = __float2int_rn(__fmul_rn(x, inv));
+    const float xh = __fmul_rn(__int2float_rn(q), w);
+    const float e = __fsub_rn(x, xh);
+    const int r = gt_residual<D>(c, inv);
+    const bool esc = fabsf(e) > tau || r >= R || r <= -R;
+    hist_add(s_gt, ws->hist[1], esc ? 0 : r + kCenter, mask);
+    if (!esc) {
+      const double de = (double)e;  // squares of subnormal errors need float64
+      my_sse += de * de;
+      my_max = fmaxf(my_max, fabsf(e));
+    }
+    if (EST) {
+      const bool smp = in_sampled_block<D>(f, g);
+      const unsigned m2 = __ballot_sync(mask, smp);
+      if (smp) hist_add(s_est, ws->hist[0], est_symbol(est_residual<D>(c), inv, R), m2);
+    }
+  }
+  // per-CTA partials
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double ss = warp_sum(my_sse);
+  float mm = warp_max(my_max);
+  if (lane == 0) {
+    s_sse[wid] = ss;
+    s_max[wid] = mm;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    float m = 0.0f;
+    for (int i = 0; i < kSzThreads / 32; i++) {
+      t += s_sse[i];
+      m = fmaxf(m, s_max[i]);
+    }
+    ws->sz_sse[blockIdx.x] = t;
+    atomicMax(&ws->sc.sz_maxerr, __float_as_uint(m));
+  }
+  hist_flush(s_gt, ws->hist[1]);
+  if (EST) hist_flush(s_est, ws->hist[0]);
+}
+
+template <int D>
+static cudaError_t launch_est_d(const FieldDev& f, const ParamsDev& p, Workspace* ws, int ctas,
+                                cudaStream_t s) {
+  constexpr int NB = 1 << (2 * D);
+  long long want = (f.nsampled * NB + kSzThreads - 1) / kSzThreads;
+  int g = (int)(want < ctas ? (want < 1 ? 1 : want) : ctas);
+  k_sz_est<D><<<g, kSzThreads, 0, s>>>(f, p, ws);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sz_est(const FieldDev& f, const ParamsDev& p, Workspace* ws, int ctas,
+                          cudaStream_t s) {
+  switch (f.d) {
+    case 1: return launch_est_d<1>(f, p, ws, ctas, s);
+    case 2: return launch_est_d<2>(f, p, ws, ctas, s);
+    default: return launch_est_d<3>(f, p, ws, ctas, s);
+  }
+}
+
+template <int D>
+static cudaError_t launch_gt_d(const FieldDev& f, const ParamsDev& p, int with_est, Workspace* ws,
+                               int ctas, cudaStream_t s, int* grid_used) {
+  long long want = (f.N + kSzThreads - 1) / kSzThreads;
+  int g = (int)(want < ctas ? (want < 1 ? 1 : want) : ctas);
+  if (grid_used) *grid_used = g;
+  if (with_est)
+    k_sz_gt<D, true><<<g, kSzThreads, 0, s>>>(f, p, ws);
+  else
+    k_sz_gt<D, false><<<g, kSzThreads, 0, s>>>(f, p, ws);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sz_gt(const FieldDev& f, const ParamsDev& p, int with_est, Workspace* ws,
+                         int ctas, cudaStream_t s, int* grid_used) {
+  switch (f.d) {
+    case 1: return launch_gt_d<1>(f, p, with_est, ws, ctas, s, grid_used);
+    case 2: return launch_gt_d<2>(f, p, with_est, ws, ctas, s, grid_used);
+    default: return launch_gt_d<3>(f, p, with_est, ws, ctas, s, grid_used);
+  }
+}
+
+int sz_occupancy(int d, int num_sms) {
+  int per = 0;
+  const void* fn = d == 1 ? (const void*)k_sz_gt<1, true>
+                 : d == 2 ? (const void*)k_sz_gt<2, true> : (const void*)k_sz_gt<3, true>;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kSzThreads, 0) != cudaSuccess || per < 1)
+    per = 1;
+  long long g = (long long)per * num_sms;
+  return (int)(g > kMaxGrid ? kMaxGrid : g);
+}
+
+// ---------------------------------------------------------------------------
+// Inspector: per-point symbols and reconstruction through the same helpers.
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void k_sz_inspect(FieldDev f, float w, float inv, float tau, int R, int use_strides,
+                             int32_t* est_sym, int32_t* gt_sym, float* recon) {
+  for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < f.N;
+       u += (long long)gridDim.x * blockDim.x) {
+    int g[3] = {0, 0, 0};
+    point_coords<D>(f, u, g);
+    Nbr c = gather_cell<D>(f, g);
+    const float x = c.v[0];
+    if (est_sym) est_sym[u] = (use_strides && in_sampled_block<D>(f, g))
+                                  ? est_symbol(est_residual<D>(c), inv, R) : -1;
+    const int q = __float2int_rn(__fmul_rn(x, inv));
+    const float xh = __fmul_rn(__int2float_rn(q), w);
+    const float e = __fsub_rn(x, xh);
+    const int r = gt_residual<D>(c, inv);
+    const bool esc = fabsf(e) > tau || r >= R || r <= -R;
+    if (gt_sym) gt_sym[u] = esc ? 0 : r + kCenter;
+    if (recon) recon[u] = esc ? x : xh;
+  }
+}
+
+cudaError_t launch_sz_inspect_q(const FieldDev& f, float w, float inv, float tau, int R,
+                                int32_t* est_sym, int32_t* gt_sym, float* recon, int use_strides,
+                                cudaStream_t s) {
+  long long g = (f.N + 255) / 256;
+  if (g > 65535) g = 65535;
+  if (g < 1) g = 1;
+  switch (f.d) {
+    case 1: k_sz_inspect<1><<<(int)g, 256, 0, s>>>(f, w, inv, tau, R, use_strides, est_sym, gt_sym, recon); break;
+    case 2: k_sz_inspect<2><<<(int)g, 256, 0, s>>>(f, w, inv, tau, R, use_strides, est_sym, gt_sym, recon); break;
+    default: k_sz_inspect<3><<<(int)g, 256, 0, s>>>(f, w, inv, tau, R, use_strides, est_sym, gt_sym, recon); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace rdk

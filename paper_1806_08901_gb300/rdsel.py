@@ -1,0 +1,381 @@
+"""ctypes binding of ``librdsel.so`` (include/rdsel.h): argument marshalling
+only.  Every step of the rate-distortion path runs in the library's CUDA
+kernels; this module turns tensors into rd_field records, calls the C entry
+point of the same name and turns the result records into dicts.
+
+There is no fallback: if the library is missing or cannot load, every call
+raises ``RdselUnavailable``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "librdsel.so")
+
+RD_OK = 0
+RD_ERR_INVALID_ARG, RD_ERR_NONFINITE, RD_ERR_OOM = -1, -2, -3
+RD_ERR_BUDGET, RD_ERR_CUDA, RD_ERR_TIMEOUT, RD_ERR_RANGE = -4, -5, -6, -7
+RD_EB_REL, RD_EB_ABS = 0, 1
+RD_EC_PAPER, RD_EC_ALL = 0, 1
+RD_SEL_PAPER, RD_SEL_HUFFMAN = 0, 1
+RD_LOC_DEVICE, RD_LOC_HOST = 0, 1
+RD_F_CONSTANT, RD_F_DELTA_CLAMPED, RD_F_MSE_ZERO = 1, 2, 4
+RD_F_TIE_BAND, RD_F_PARTIAL_BLOCKS = 8, 16
+RD_NSYM = 65536
+
+
+class RdselUnavailable(RuntimeError):
+    pass
+
+
+class RdselError(RuntimeError):
+    def __init__(self, code: int, what: str, msg: str = ""):
+        super().__init__(f"{what}: {msg} (status {code})")
+        self.code = code
+
+
+class rd_field(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("ndim", C.c_int32), ("location", C.c_int32),
+                ("shape", C.c_int64 * 3)]
+
+
+class rd_params(C.Structure):
+    _fields_ = [("eb", C.c_double), ("eb_mode", C.c_int32), ("ec_mode", C.c_int32),
+                ("r_sp", C.c_double), ("quant_radius", C.c_int32), ("sel_rule", C.c_int32),
+                ("sz_offset", C.c_double)]
+
+
+class rd_result(C.Structure):
+    _fields_ = [
+        ("vmin", C.c_float), ("vmax", C.c_float), ("vr", C.c_double), ("eb_abs", C.c_double),
+        ("r_sp_eff", C.c_double), ("strides", C.c_int32 * 3), ("minexp", C.c_int32),
+        ("n_blocks", C.c_uint64), ("n_sampled_blocks", C.c_uint64),
+        ("br_zfp", C.c_double), ("psnr_zfp", C.c_double), ("mse_sp", C.c_double),
+        ("zfp_s2", C.c_uint64), ("zfp_npoints", C.c_uint64), ("zfp_ncoeff", C.c_uint64),
+        ("delta", C.c_double), ("br_sz", C.c_double), ("br_sz_huff", C.c_double),
+        ("psnr_sz", C.c_double), ("entropy", C.c_double),
+        ("sz_ns", C.c_uint64), ("sz_huff_bits", C.c_uint64), ("sz_nesc", C.c_uint64),
+        ("sz_nsym", C.c_uint32), ("selection", C.c_int32), ("flags", C.c_uint32),
+    ]
+
+
+class rd_truth(C.Structure):
+    _fields_ = [
+        ("eb_sz", C.c_double), ("delta", C.c_double),
+        ("br_sz_gt", C.c_double), ("psnr_sz_gt", C.c_double), ("sse_sz", C.c_double),
+        ("maxerr_sz", C.c_double),
+        ("sz_bits_gt", C.c_uint64), ("sz_huff_gt", C.c_uint64), ("sz_nesc_gt", C.c_uint64),
+        ("sz_nsym_gt", C.c_uint32),
+        ("br_zfp_gt", C.c_double), ("psnr_zfp_gt", C.c_double), ("sse_zfp", C.c_double),
+        ("maxerr_zfp", C.c_double), ("zfp_bits_gt", C.c_uint64),
+        ("best_gt", C.c_int32), ("flags", C.c_uint32),
+    ]
+
+
+# Every symbol include/rdsel.h declares, with its ctypes signature.
+_P = C.POINTER
+_SIGNATURES = {
+    "rd_context_create": (C.c_int32, [C.c_int32, C.c_size_t, _P(C.c_void_p)]),
+    "rd_context_destroy": (C.c_int32, [C.c_void_p]),
+    "rd_estimate_zfp": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), _P(rd_result), C.c_void_p]),
+    "rd_estimate_sz": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), C.c_double,
+                                   _P(rd_result), C.c_void_p]),
+    "rd_select": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), _P(rd_result), C.c_void_p]),
+    "rd_ground_truth": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), C.c_double,
+                                    _P(rd_truth), C.c_void_p]),
+    "rd_evaluate": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), _P(rd_result),
+                                _P(rd_truth), C.c_void_p]),
+    "rd_copy_histograms": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rd_zfp_blocks": (C.c_int32, [C.c_void_p, _P(rd_field), C.c_double, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rd_sz_symbols": (C.c_int32, [C.c_void_p, _P(rd_field), C.c_double, C.c_int32, C.c_void_p,
+                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rd_set_profiling": (C.c_int32, [C.c_void_p, C.c_int32]),
+    "rd_reset_profile": (C.c_int32, [C.c_void_p]),
+    "rd_kernel_stat": (C.c_int32, [C.c_void_p, C.c_int32, _P(C.c_char_p), _P(C.c_double),
+                                   _P(C.c_int64)]),
+    "rd_launch_count": (C.c_int64, [C.c_void_p]),
+    "rd_status_string": (C.c_char_p, [C.c_int32]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load librdsel.so (once).  Raises RdselUnavailable if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RdselUnavailable(
+                f"{LIB_PATH} is not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
+        try:
+            L = C.CDLL(LIB_PATH)
+        except OSError as e:
+            raise RdselUnavailable(f"cannot load {LIB_PATH}: {e}") from e
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> list:
+    return list(_SIGNATURES)
+
+
+def status_string(code: int) -> str:
+    return lib().rd_status_string(int(code)).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != RD_OK:
+        raise RdselError(rc, what, status_string(rc))
+
+
+def params(eb=1e-4, eb_mode=RD_EB_REL, ec_mode=RD_EC_PAPER, r_sp=0.05, quant_radius=32768,
+           sel_rule=RD_SEL_PAPER, sz_offset=0.5) -> rd_params:
+    return rd_params(eb, eb_mode, ec_mode, r_sp, quant_radius, sel_rule, sz_offset)
+
+
+def _todict(s: C.Structure) -> dict:
+    out = {}
+    for name, _ in s._fields_:
+        v = getattr(s, name)
+        out[name] = list(v) if isinstance(v, C.Array) else v
+    return out
+
+
+def make_field(x) -> tuple:
+    """rd_field for a float32 C-contiguous torch tensor (device or host) or
+    numpy array (host).  Returns (rd_field, keepalive)."""
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(x, torch.Tensor):
+        if x.dtype != torch.float32 or not x.is_contiguous():
+            raise ValueError("fields are contiguous float32 tensors")
+        loc = RD_LOC_DEVICE if x.is_cuda else RD_LOC_HOST
+        ptr, shape, keep = x.data_ptr(), tuple(x.shape), x
+    else:
+        a = np.asarray(x)
+        if a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("fields are C-contiguous float32 arrays")
+        loc, ptr, shape, keep = RD_LOC_HOST, a.ctypes.data, a.shape, a
+    if not 1 <= len(shape) <= 3:
+        raise ValueError("fields are 1-, 2- or 3-dimensional")
+    sh = (C.c_int64 * 3)(*(list(shape) + [1] * (3 - len(shape))))
+    return rd_field(ptr, len(shape), loc, sh), keep
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:  # pragma: no cover
+            pass
+        return C.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return C.c_void_p(t.data_ptr())
+    return C.c_void_p(t.ctypes.data)
+
+
+# ---------------------------------------------------------------------------
+# Entry points, named as in include/rdsel.h
+# ---------------------------------------------------------------------------
+
+def rd_context_create(device: int = 0, hbm_budget: int = 0):
+    h = C.c_void_p()
+    _check(lib().rd_context_create(int(device), int(hbm_budget), C.byref(h)), "rd_context_create")
+    return h
+
+
+def rd_context_destroy(ctx) -> None:
+    _check(lib().rd_context_destroy(ctx), "rd_context_destroy")
+
+
+def rd_estimate_zfp(ctx, field, prm: rd_params, stream=None) -> dict:
+    f, keep = make_field(field)
+    r = rd_result()
+    _check(lib().rd_estimate_zfp(ctx, C.byref(f), C.byref(prm), C.byref(r), _stream(stream)),
+           "rd_estimate_zfp")
+    return _todict(r)
+
+
+def rd_estimate_sz(ctx, field, prm: rd_params, delta: float = 0.0, stream=None) -> dict:
+    f, keep = make_field(field)
+    r = rd_result()
+    _check(lib().rd_estimate_sz(ctx, C.byref(f), C.byref(prm), float(delta), C.byref(r),
+                                _stream(stream)), "rd_estimate_sz")
+    return _todict(r)
+
+
+def rd_select(ctx, field, prm: rd_params, stream=None) -> dict:
+    f, keep = make_field(field)
+    r = rd_result()
+    _check(lib().rd_select(ctx, C.byref(f), C.byref(prm), C.byref(r), _stream(stream)), "rd_select")
+    return _todict(r)
+
+
+def rd_ground_truth(ctx, field, prm: rd_params, eb_sz: float = 0.0, stream=None) -> dict:
+    f, keep = make_field(field)
+    t = rd_truth()
+    _check(lib().rd_ground_truth(ctx, C.byref(f), C.byref(prm), float(eb_sz), C.byref(t),
+                                 _stream(stream)), "rd_ground_truth")
+    return _todict(t)
+
+
+def rd_evaluate(ctx, field, prm: rd_params, stream=None) -> tuple:
+    f, keep = make_field(field)
+    r, t = rd_result(), rd_truth()
+    _check(lib().rd_evaluate(ctx, C.byref(f), C.byref(prm), C.byref(r), C.byref(t),
+                             _stream(stream)), "rd_evaluate")
+    return _todict(r), _todict(t)
+
+
+def rd_copy_histograms(ctx) -> tuple:
+    est = np.zeros(RD_NSYM, np.uint32)
+    gt = np.zeros(RD_NSYM, np.uint32)
+    _check(lib().rd_copy_histograms(ctx, _ptr(est), _ptr(gt)), "rd_copy_histograms")
+    return est, gt
+
+
+def rd_zfp_blocks(ctx, field, eb_abs: float, want_coeffs: bool = False, stream=None) -> dict:
+    import torch
+
+    f, keep = make_field(field)
+    nblk = 1
+    for k in range(f.ndim):
+        nblk *= (f.shape[k] + 3) // 4
+    nb = 4 ** f.ndim
+    dev = torch.device("cuda")
+    emax = torch.zeros(nblk, dtype=torch.int32, device=dev)
+    prec = torch.zeros(nblk, dtype=torch.int32, device=dev)
+    bits = torch.zeros(nblk, dtype=torch.int64, device=dev)
+    coeffs = torch.zeros(nblk * nb, dtype=torch.int32, device=dev) if want_coeffs else None
+    _check(lib().rd_zfp_blocks(ctx, C.byref(f), float(eb_abs), _ptr(emax), _ptr(prec), _ptr(bits),
+                               _ptr(coeffs), _stream(stream)), "rd_zfp_blocks")
+    out = {"emax": emax.cpu().numpy(), "prec": prec.cpu().numpy(),
+           "bits": bits.cpu().numpy().view(np.uint64)}
+    if want_coeffs:
+        out["coeffs"] = coeffs.cpu().numpy().view(np.uint32).reshape(nblk, nb)
+    return out
+
+
+def rd_sz_symbols(ctx, field, delta: float, quant_radius: int = 32768, strides=None,
+                  stream=None) -> dict:
+    import torch
+
+    f, keep = make_field(field)
+    n = 1
+    for k in range(f.ndim):
+        n *= f.shape[k]
+    dev = torch.device("cuda")
+    est = torch.empty(n, dtype=torch.int32, device=dev)
+    gt = torch.empty(n, dtype=torch.int32, device=dev)
+    rec = torch.empty(n, dtype=torch.float32, device=dev)
+    st = None
+    if strides is not None:
+        st = np.array(list(strides), dtype=np.int32)
+    _check(lib().rd_sz_symbols(ctx, C.byref(f), float(delta), int(quant_radius), _ptr(st),
+                               _ptr(est), _ptr(gt), _ptr(rec), _stream(stream)), "rd_sz_symbols")
+    shape = tuple(f.shape[k] for k in range(f.ndim))
+    return {"est": est.cpu().numpy().reshape(shape), "gt": gt.cpu().numpy().reshape(shape),
+            "recon": rec.cpu().numpy().reshape(shape)}
+
+
+def rd_set_profiling(ctx, on: bool) -> None:
+    _check(lib().rd_set_profiling(ctx, 1 if on else 0), "rd_set_profiling")
+
+
+def rd_reset_profile(ctx) -> None:
+    _check(lib().rd_reset_profile(ctx), "rd_reset_profile")
+
+
+def rd_kernel_stats(ctx) -> dict:
+    """{kernel name: (total ms, launches)} from rd_kernel_stat."""
+    out, i = {}, 0
+    name, ms, n = C.c_char_p(), C.c_double(), C.c_int64()
+    while lib().rd_kernel_stat(ctx, i, C.byref(name), C.byref(ms), C.byref(n)) == RD_OK:
+        out[name.value.decode()] = (ms.value, n.value)
+        i += 1
+    return out
+
+
+def rd_launch_count(ctx) -> int:
+    return int(lib().rd_launch_count(ctx))
+
+
+class Context:
+    """Owns one rd_context; methods forward to the entry points above."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0):
+        self.h = rd_context_create(device, hbm_budget)
+
+    def close(self):
+        if self.h:
+            rd_context_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def estimate_zfp(self, x, p, stream=None):
+        return rd_estimate_zfp(self.h, x, p, stream)
+
+    def estimate_sz(self, x, p, delta=0.0, stream=None):
+        return rd_estimate_sz(self.h, x, p, delta, stream)
+
+    def select(self, x, p, stream=None):
+        return rd_select(self.h, x, p, stream)
+
+    def ground_truth(self, x, p, eb_sz=0.0, stream=None):
+        return rd_ground_truth(self.h, x, p, eb_sz, stream)
+
+    def evaluate(self, x, p, stream=None):
+        return rd_evaluate(self.h, x, p, stream)
+
+    def histograms(self):
+        return rd_copy_histograms(self.h)
+
+    def zfp_blocks(self, x, eb_abs, want_coeffs=False, stream=None):
+        return rd_zfp_blocks(self.h, x, eb_abs, want_coeffs, stream)
+
+    def sz_symbols(self, x, delta, quant_radius=32768, strides=None, stream=None):
+        return rd_sz_symbols(self.h, x, delta, quant_radius, strides, stream)
+
+    def set_profiling(self, on=True):
+        rd_set_profiling(self.h, on)
+
+    def reset_profile(self):
+        rd_reset_profile(self.h)
+
+    def kernel_stats(self):
+        return rd_kernel_stats(self.h)
+
+    def launch_count(self):
+        return rd_launch_count(self.h)

@@ -544,3 +544,19 @@ def test_ratios_are_reasonable_on_smooth_field():
     assert 0 < r["br_zfp"] < 12 and 0 < r["br_sz"] < 12
     assert abs(r["psnr_zfp"] - t["psnr_zfp_gt"]) < 0.1 * t["psnr_zfp_gt"]
     assert abs(r["psnr_sz"] - t["psnr_sz_gt"]) < 0.1 * t["psnr_sz_gt"]
+
+
+def test_estimate_sz_agrees_with_select_and_closed_form():
+    """rdo_estimate_sz at select's delta reproduces select's SZ fields; at
+    delta = 2 eb_abs its PSNR is Eq. (psnr-sz)."""
+    x = synth.config1_field(seed=12, shape=(60, 52))
+    p = O.params(eb=1e-3, r_sp=0.1)
+    r = O.select(x, p, want_hist=True)
+    e = O.estimate_sz(x, p, delta=r["delta"], want_hist=True)
+    for k in ("sz_ns", "sz_huff_bits", "sz_nesc", "sz_nsym", "br_sz", "entropy", "br_sz_huff",
+              "psnr_sz", "strides", "zfp_npoints", "n_sampled_blocks"):
+        assert e[k] == r[k], k
+    assert np.array_equal(e["hist"], r["hist"])
+    e2 = O.estimate_sz(x, p, delta=0.0)
+    assert e2["delta"] == 2 * e2["eb_abs"]
+    assert e2["psnr_sz"] == pytest.approx(-20 * math.log10(1e-3) + 10 * math.log10(3), rel=1e-12)
