@@ -169,6 +169,28 @@ int32_t rd_evaluate(rd_context* ctx, const rd_field* field,
                     const rd_params* params, rd_result* est,
                     rd_truth* truth, void* stream);
 
+/* rd_select for callers that may not allocate memory.  The paper has no
+ * counterpart: this exists for code that runs under a device-memory budget
+ * it does not own (an in-situ simulation holding the GPU's memory, a
+ * framework whose allocator must serve every allocation) or that cannot take
+ * the synchronisation an allocation may imply.  It needs no context and
+ * calls no cudaMalloc, cudaFree, cudaMallocHost or other allocating routine:
+ * its scratch is one fixed 1.125 MiB array inside the library, held by every
+ * GPU that loads the library until the process exits.
+ *  - field: DEVICE memory only (location RD_LOC_HOST is rejected, since a
+ *    host field would need a staging buffer), at most 2^31-1 points; larger
+ *    or malformed shapes return RD_ERR_INVALID_ARG.  The scratch does not
+ *    grow with the field, so no other size limit applies.
+ *  - The first call on a device (the current device) resolves the array's
+ *    device address and sizes the grids; make that first call before any
+ *    stream capture.
+ *  - Every call shares the array and leaves its contents behind; each call
+ *    clears what must start at zero.  Calls that overlap on the GPU (other
+ *    streams or host threads) race on the array: serialise them.
+ *  - Results equal rd_select's on the same field and parameters. */
+int32_t rd_select_static(const rd_field* field, const rd_params* params,
+                         rd_result* out, void* stream);
+
 /* ---- inspection (same kernels, per-element outputs) ------------------ */
 
 /* Copy the histograms of the last SZ estimate / SZ ground truth run on this

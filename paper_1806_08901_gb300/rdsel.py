@@ -89,6 +89,7 @@ _SIGNATURES = {
                                     _P(rd_truth), C.c_void_p]),
     "rd_evaluate": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), _P(rd_result),
                                 _P(rd_truth), C.c_void_p]),
+    "rd_select_static": (C.c_int32, [_P(rd_field), _P(rd_params), _P(rd_result), C.c_void_p]),
     "rd_copy_histograms": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "rd_zfp_blocks": (C.c_int32, [C.c_void_p, _P(rd_field), C.c_double, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -229,6 +230,17 @@ def rd_select(ctx, field, prm: rd_params, stream=None) -> dict:
     f, keep = make_field(field)
     r = rd_result()
     _check(lib().rd_select(ctx, C.byref(f), C.byref(prm), C.byref(r), _stream(stream)), "rd_select")
+    return _todict(r)
+
+
+def rd_select_static(field, prm: rd_params, stream=None) -> dict:
+    """rd_select without a context, on the library's fixed scratch array (for
+    callers that may not allocate): device fields only; calls on one device
+    must not overlap."""
+    f, keep = make_field(field)
+    r = rd_result()
+    _check(lib().rd_select_static(C.byref(f), C.byref(prm), C.byref(r), _stream(stream)),
+           "rd_select_static")
     return _todict(r)
 
 
