@@ -224,12 +224,13 @@ def main():
     p = R.params(eb=EB_REL, r_sp=R_SP)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    for _ in range(args.warmup):
+    # per-kernel CUDA events are recorded inside the call's graph from the
+    # first warm-up step on, so the timed steps replay the same graph
+    ctx.set_profiling(True)
+    for _ in range(max(args.warmup, 3)):
         flush.zero_()
         ctx.evaluate(x, p, stream)
     est_ref, truth_ref = ctx.evaluate(x, p, stream)
-
-    ctx.set_profiling(True)
     ctx.reset_profile()
     launches0 = ctx.launch_count()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]

@@ -18,7 +18,7 @@ namespace {
 
 const char* kKernelNames[K_COUNT] = {
     "reset", "range", "prepare", "zfp_pass", "delta", "sz_est", "sz_pass",
-    "entropy", "huffman", "finish", "zfp_inspect", "sz_inspect"};
+    "entropy", "code_stats", "finish", "zfp_inspect", "sz_inspect"};
 
 struct KStat {
   double ms;
@@ -35,6 +35,29 @@ struct HostOut {
   rd_truth truth;
   int32_t status;
 };
+
+// Everything a call's launch sequence depends on.  Two calls with equal keys
+// issue identical work, so the second replays the first one's CUDA graph.
+struct CallKey {
+  FieldDev f;
+  ParamsDev p;
+  int passes;
+  int delta_mode;
+  double delta_arg;
+  int profiling;
+  int pad;
+};
+
+struct GraphEntry {
+  CallKey key;
+  cudaGraphExec_t exec;
+  std::vector<Pending> events;  // per-kernel event pairs recorded inside the graph
+  long long kernels;
+  unsigned long long last_use;
+};
+
+constexpr size_t kMaxGraphs = 16;
+constexpr size_t kMaxSeen = 32;
 
 }  // namespace
 
@@ -55,6 +78,14 @@ struct rd_context {
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> pool;
   long long launches = 0;
+  // CUDA graphs of repeated calls
+  cudaStream_t cap = nullptr;  // capture stream (the legacy stream cannot capture)
+  std::vector<GraphEntry> graphs;
+  std::vector<CallKey> seen;
+  unsigned long long tick = 0;
+  bool capturing = false;
+  std::vector<Pending>* sink = nullptr;
+  long long cap_kernels = 0;
 };
 
 namespace {
@@ -76,21 +107,54 @@ cudaEvent_t take_event(rd_context* c) {
   return e;
 }
 
+// Launch one kernel (through fn), bracketed by timing events when profiling.
+// While a graph is being captured the events belong to the graph entry.
 template <typename F>
 int launch(rd_context* c, int kid, cudaStream_t s, F&& fn) {
   Pending p{kid, nullptr, nullptr};
+  // inside a capture an event record must be an external record node (a
+  // timestamp on every replay), not an internal dependency marker
+  const unsigned rec = c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   if (c->profiling) {
-    p.a = take_event(c);
-    p.b = take_event(c);
-    cudaEventRecord(p.a, s);
+    if (c->capturing) {
+      cudaEventCreate(&p.a);
+      cudaEventCreate(&p.b);
+    } else {
+      p.a = take_event(c);
+      p.b = take_event(c);
+    }
+    cudaEventRecordWithFlags(p.a, s, rec);
   }
   cudaError_t e = fn();
   if (c->profiling) {
-    cudaEventRecord(p.b, s);
-    c->pending.push_back(p);
+    cudaEventRecordWithFlags(p.b, s, rec);
+    (c->capturing ? *c->sink : c->pending).push_back(p);
   }
-  c->launches++;
+  if (c->capturing)
+    c->cap_kernels++;
+  else
+    c->launches++;
   return cuda_status(e);
+}
+
+void add_times(rd_context* c, const std::vector<Pending>& evs) {
+  for (const Pending& p : evs) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      c->stats[p.kid].ms += ms;
+      c->stats[p.kid].launches += 1;
+    } else {
+      cudaGetLastError();  // a missing timing is not the caller's error
+    }
+  }
+}
+
+void drop_entry(GraphEntry& g) {
+  cudaGraphExecDestroy(g.exec);
+  for (const Pending& p : g.events) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
 }
 
 void collect_profile(rd_context* c) {
@@ -99,6 +163,8 @@ void collect_profile(rd_context* c) {
     if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
       c->stats[p.kid].ms += ms;
       c->stats[p.kid].launches += 1;
+    } else {
+      cudaGetLastError();
     }
     c->pool.push_back(p.a);
     c->pool.push_back(p.b);
@@ -234,25 +300,21 @@ int ec_count(int d, int ec_mode) {
   return d == 1 ? 3 : d == 2 ? 9 : 16;
 }
 
-// Run the passes of one call; est/truth may be NULL.
-int run(rd_context* c, const rd_field* fld, const rd_params* prm, int passes, int delta_mode,
-        double delta_arg, rd_result* est, rd_truth* truth, void* stream) {
-  if (!c) return RD_ERR_INVALID_ARG;
-  int rc = check_params(prm);
-  if (rc) return rc;
-  CallGuard guard(c->device);
-  cudaStream_t s = (cudaStream_t)stream;
-  Geometry g;
-  rc = make_geometry(c, fld, nullptr, prm->r_sp, s, &g);
-  if (rc) return rc;
-  const FieldDev& f = g.f;
-  const ParamsDev p = to_dev(prm);
+// Issue the launch sequence of one call and the copy of its result records
+// into pinned host memory, on stream s (which may be capturing).
+int issue(rd_context* c, const CallKey& k, const Geometry& g, cudaStream_t s) {
+  const FieldDev& f = k.f;
+  const ParamsDev& p = k.p;
+  const int passes = k.passes;
+  const int delta_mode = k.delta_mode;
+  const double delta_arg = k.delta_arg;
   Workspace* ws = c->ws;
   const int d = f.d;
   const bool need_gt = passes & P_SZ_GT;
   const bool need_quant = passes & (P_SZ_EST | P_SZ_GT);
-  const unsigned long long ncoeff = (unsigned long long)f.nsampled * ec_count(d, prm->ec_mode);
+  const unsigned long long ncoeff = (unsigned long long)f.nsampled * ec_count(d, p.ec_mode);
   int zfp_parts = 0, sz_parts = 0;
+  int rc;
 
   if ((rc = launch(c, K_RESET, s, [&] { return launch_reset(ws, s); }))) return rc;
   if ((rc = launch(c, K_RANGE, s, [&] { return launch_range(f, ws, c->range_ctas, s); }))) return rc;
@@ -272,6 +334,8 @@ int run(rd_context* c, const rd_field* fld, const rd_params* prm, int passes, in
   if (passes & P_SZ_GT) {
     int with_est = (passes & P_SZ_EST) ? 1 : 0;
     if ((rc = launch(c, K_SZ_GT, s, [&] {
+           if (sz_march_supported(f))
+             return launch_sz_march(f, p, with_est, ws, c->num_sms, s, &sz_parts);
            return launch_sz_gt(f, p, with_est, ws, c->sz_ctas[d], s, &sz_parts);
          })))
       return rc;
@@ -281,21 +345,121 @@ int run(rd_context* c, const rd_field* fld, const rd_params* prm, int passes, in
   }
   int hist_mask = ((passes & P_SZ_EST) ? 1 : 0) | ((passes & P_SZ_GT) ? 2 : 0);
   if (hist_mask) {
-    if ((rc = launch(c, K_ENTROPY, s, [&] { return launch_entropy(ws, hist_mask, s); }))) return rc;
-    if ((rc = launch(c, K_HUFFMAN, s, [&] { return launch_huffman(ws, hist_mask, s); }))) return rc;
+    if ((rc = launch(c, K_HUFFMAN, s, [&] { return launch_code_stats(ws, hist_mask, s); }))) return rc;
   }
   if ((rc = launch(c, K_FINISH, s, [&] {
          return launch_finish(p, ws, passes, zfp_parts, sz_parts, f.N, g.npoints_sampled, s);
        })))
     return rc;
   // one copy of the result records and the device status
-  cudaError_t e = cudaMemcpyAsync(&c->out->res, &ws->res, sizeof(rd_result) + 0, cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaMemcpyAsync(&c->out->res, &ws->res, sizeof(rd_result), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&c->out->truth, &ws->truth, sizeof(rd_truth), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&c->out->status, &ws->sc.status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (c->profiling) collect_profile(c);
+  return cuda_status(e);
+}
+
+GraphEntry* find_graph(rd_context* c, const CallKey& k) {
+  for (GraphEntry& g : c->graphs)
+    if (memcmp(&g.key, &k, sizeof(CallKey)) == 0) return &g;
+  return nullptr;
+}
+
+// Capture the call's launch sequence into a graph (on the context's capture
+// stream) and cache it; evicts the least recently used graph when full.
+GraphEntry* capture_graph(rd_context* c, const CallKey& k, const Geometry& g) {
+  if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+  GraphEntry ent;
+  ent.key = k;
+  ent.exec = nullptr;
+  ent.kernels = 0;
+  ent.last_use = 0;
+  if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return nullptr;
+  c->capturing = true;
+  c->sink = &ent.events;
+  c->cap_kernels = 0;
+  int rc = issue(c, k, g, c->cap);
+  c->capturing = false;
+  c->sink = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->cap, &graph);
+  if (rc == RD_OK && e == cudaSuccess) e = cudaGraphInstantiate(&ent.exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (rc != RD_OK || e != cudaSuccess || !ent.exec) {
+    cudaGetLastError();
+    for (const Pending& p : ent.events) {
+      cudaEventDestroy(p.a);
+      cudaEventDestroy(p.b);
+    }
+    return nullptr;
+  }
+  ent.kernels = c->cap_kernels;
+  if (c->graphs.size() >= kMaxGraphs) {
+    size_t lru = 0;
+    for (size_t i = 1; i < c->graphs.size(); i++)
+      if (c->graphs[i].last_use < c->graphs[lru].last_use) lru = i;
+    drop_entry(c->graphs[lru]);
+    c->graphs.erase(c->graphs.begin() + lru);
+  }
+  c->graphs.push_back(ent);
+  return &c->graphs.back();
+}
+
+// Run the passes of one call; est/truth may be NULL.  The first call with a
+// given key launches directly; a repeat is captured once into a CUDA graph
+// and every later repeat replays it with a single launch.
+int run(rd_context* c, const rd_field* fld, const rd_params* prm, int passes, int delta_mode,
+        double delta_arg, rd_result* est, rd_truth* truth, void* stream) {
+  if (!c) return RD_ERR_INVALID_ARG;
+  int rc = check_params(prm);
+  if (rc) return rc;
+  CallGuard guard(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  Geometry g;
+  rc = make_geometry(c, fld, nullptr, prm->r_sp, s, &g);
+  if (rc) return rc;
+  CallKey k;
+  memset(&k, 0, sizeof(k));
+  k.f = g.f;
+  k.p = to_dev(prm);
+  k.passes = passes;
+  k.delta_mode = delta_mode;
+  k.delta_arg = delta_arg;
+  k.profiling = c->profiling ? 1 : 0;
+  const FieldDev& f = g.f;
+  const int d = f.d;
+  const unsigned long long ncoeff = (unsigned long long)f.nsampled * ec_count(d, prm->ec_mode);
+
+  GraphEntry* ent = find_graph(c, k);
+  if (!ent) {
+    bool repeat = false;
+    for (const CallKey& q : c->seen)
+      if (memcmp(&q, &k, sizeof(CallKey)) == 0) repeat = true;
+    if (repeat) {
+      ent = capture_graph(c, k, g);
+    } else {
+      if (c->seen.size() >= kMaxSeen) c->seen.erase(c->seen.begin());
+      c->seen.push_back(k);
+    }
+  }
+  cudaError_t e;
+  if (ent) {
+    ent->last_use = ++c->tick;
+    e = cudaGraphLaunch(ent->exec, s);
+    c->launches += ent->kernels;
+    rc = cuda_status(e);
+  } else {
+    rc = issue(c, k, g, s);
+  }
+  e = cudaStreamSynchronize(s);
+  if (c->profiling) {
+    if (ent)
+      add_times(c, ent->events);
+    else
+      collect_profile(c);
+  }
+  if (rc != RD_OK) return rc;
   if (e != cudaSuccess) return cuda_status(e);
   int status = c->out->status;
   if (status != RD_OK) {
@@ -350,6 +514,12 @@ int32_t rd_context_create(int32_t device, size_t hbm_budget, rd_context** out) {
     return RD_ERR_OOM;
   }
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (prepare_code_stats() != cudaSuccess || prepare_sz_march() != cudaSuccess) {
+    cudaFreeHost(c->out);
+    cudaFree(c->ws);
+    delete c;
+    return RD_ERR_CUDA;
+  }
   c->range_ctas = c->num_sms * 4;
   for (int d = 1; d <= 3; d++) {
     c->zfp_ctas[d] = zfp_occupancy(d, c->num_sms);
@@ -368,6 +538,8 @@ int32_t rd_context_destroy(rd_context* c) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
   }
+  for (GraphEntry& g : c->graphs) drop_entry(g);
+  if (c->cap) cudaStreamDestroy(c->cap);
   if (c->staging) cudaFree(c->staging);
   if (c->ws) cudaFree(c->ws);
   if (c->out) cudaFreeHost(c->out);

@@ -152,6 +152,49 @@ __device__ __forceinline__ int cast_scaled(float x, int e) {
   return __float2int_rz(y);
 }
 
+// ---------------------------------------------------------------------------
+// Conversion-free integer/float helpers.  On this GPU the F2I / I2F / FRND
+// conversions issue on the narrow float64 pipe, so the per-value paths use
+// integer bit operations and float adds instead; each helper gives exactly
+// the result of the conversion it replaces.
+// ---------------------------------------------------------------------------
+
+// trunc(x * 2^s) when |x * 2^s| < 2^30 (the block-floating-point cast):
+// x = m * 2^(E-150) with the 24-bit significand m, so x * 2^s = m * 2^(E-150+s).
+__device__ __forceinline__ int cast_bits(float x, int s) {
+  const unsigned b = __float_as_uint(x);
+  int E = (int)((b >> 23) & 0xffu);
+  unsigned m = b & 0x7fffffu;
+  if (E) m |= 0x800000u; else E = 1;  // subnormal: no hidden bit, exponent of E = 1
+  const int sh = E - 150 + s;
+  const unsigned mag = sh >= 0 ? (m << sh) : (m >> min(-sh, 31));
+  return (b >> 31) ? -(int)mag : (int)mag;
+}
+
+constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+constexpr int kMagicBits = 0x4B400000;
+
+// float(k) for |k| < 2^22, exactly.
+__device__ __forceinline__ float small_int_to_float(int k) {
+  return __fsub_rn(__int_as_float(k + kMagicBits), kMagic);
+}
+
+// float(i) rounded to nearest even for any int: i = hi * 2^16 + lo with both
+// halves exact in float, summed by one fused multiply-add (one rounding).
+__device__ __forceinline__ float int_to_float_rn(int i) {
+  const float fh = small_int_to_float(i >> 16);
+  const float fl = small_int_to_float(i & 0xffff);
+  return __fmaf_rn(fh, 65536.0f, fl);
+}
+
+// rint(t) for |t| < 2^22: adding 1.5 * 2^23 rounds t to the nearest integer
+// (ties to even) in the low bits; returns the integer and its exact float.
+__device__ __forceinline__ int round_small(float t, float& tf) {
+  const float a = __fadd_rn(t, kMagic);
+  tf = __fsub_rn(a, kMagic);
+  return __float_as_int(a) - kMagicBits;
+}
+
 // Ordered unsigned key of a float: monotone in the float's value.
 __device__ __forceinline__ unsigned int float_key(float v) {
   unsigned int b = __float_as_uint(v);

@@ -17,7 +17,7 @@ constexpr int kMaxGrid = 4096;       // upper bound of CTAs of a reducing pass
 constexpr int kHistWin = 4096;       // shared-memory window of histogram bins
 constexpr int kHistWinLo = kCenter - kHistWin / 2;
 constexpr int kEntropyCtas = kNsym / 1024;
-constexpr int kHuffSmemKeys = 32768; // sort in shared memory up to this many symbols
+constexpr int kHuffSmemKeys = 24576; // Huffman in shared memory up to this many symbols
 
 // Scalars produced and consumed on the device within one call: nothing
 // data-dependent (value range, bin width, error flags) leaves the device
@@ -53,7 +53,8 @@ struct Workspace {
   HuffOut huff[2];
   double zfp_sse[kMaxGrid];           // per-CTA partial sums (fixed order)
   double sz_sse[kMaxGrid];
-  uint32_t sort_scratch[2][kNsym];    // Huffman sort buffer when K is large
+  uint32_t sort_scratch[2][kNsym];    // Huffman leaves when K is large
+  uint32_t node_scratch[2][kNsym];    // Huffman internal nodes when K is large
   rd_result res;
   rd_truth truth;
 };
@@ -129,8 +130,10 @@ cudaError_t launch_sz_est(const FieldDev& f, const ParamsDev& p, Workspace* ws,
                           int ctas, cudaStream_t s);
 cudaError_t launch_sz_gt(const FieldDev& f, const ParamsDev& p, int with_est,
                          Workspace* ws, int ctas, cudaStream_t s, int* grid_used);
-cudaError_t launch_entropy(Workspace* ws, int which_mask, cudaStream_t s);
-cudaError_t launch_huffman(Workspace* ws, int which_mask, cudaStream_t s);
+// Huffman cost and entropy partials of the histograms in which_mask (bit 0 =
+// estimate, bit 1 = ground truth); prepare_code_stats() once per device first.
+cudaError_t launch_code_stats(Workspace* ws, int which_mask, cudaStream_t s);
+cudaError_t prepare_code_stats();
 cudaError_t launch_finish(const ParamsDev& p, Workspace* ws, int passes,
                           int zfp_parts, int sz_parts, long long npoints_all,
                           unsigned long long zfp_npoints, cudaStream_t s);
@@ -140,6 +143,12 @@ cudaError_t launch_zfp_inspect(const FieldDev& f, double eb_abs, int32_t* emax,
 cudaError_t launch_sz_inspect_q(const FieldDev& f, float w, float inv, float tau, int R,
                                 int32_t* est_sym, int32_t* gt_sym, float* recon,
                                 int use_strides, cudaStream_t s);
+// SZ pass as a TMA-fed march (2D/3D fields with 16-byte aligned rows);
+// prepare_sz_march() once per device first.
+bool sz_march_supported(const FieldDev& f);
+cudaError_t prepare_sz_march();
+cudaError_t launch_sz_march(const FieldDev& f, const ParamsDev& p, int with_est, Workspace* ws,
+                            int num_sms, cudaStream_t s, int* grid_used);
 int zfp_occupancy(int d, int num_sms);
 int sz_occupancy(int d, int num_sms);
 

@@ -99,13 +99,31 @@ __global__ void __launch_bounds__(512) k_range(const float* __restrict__ x, long
     kmin = min(kmin, k);
     kmax = max(kmax, k);
   }
+  // warp, then CTA, then one update per CTA of the shared keys
+  __shared__ unsigned s_min[16], s_max[16], s_bad[16];
   kmin = __reduce_min_sync(0xffffffffu, kmin);
   kmax = __reduce_max_sync(0xffffffffu, kmax);
   bad = __reduce_or_sync(0xffffffffu, bad);
+  const int wid = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) {
-    atomicMin(&ws->sc.min_key, kmin);
-    atomicMax(&ws->sc.max_key, kmax);
-    if (bad) atomicOr(&ws->sc.nonfinite, 1u);
+    s_min[wid] = kmin;
+    s_max[wid] = kmax;
+    s_bad[wid] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int nw = blockDim.x >> 5;
+    unsigned a = threadIdx.x < nw ? s_min[threadIdx.x] : 0xffffffffu;
+    unsigned b = threadIdx.x < nw ? s_max[threadIdx.x] : 0u;
+    unsigned c = threadIdx.x < nw ? s_bad[threadIdx.x] : 0u;
+    a = __reduce_min_sync(0xffffffffu, a);
+    b = __reduce_max_sync(0xffffffffu, b);
+    c = __reduce_or_sync(0xffffffffu, c);
+    if (threadIdx.x == 0) {
+      atomicMin(&ws->sc.min_key, a);
+      atomicMax(&ws->sc.max_key, b);
+      if (c) atomicOr(&ws->sc.nonfinite, 1u);
+    }
   }
 }
 
@@ -180,43 +198,63 @@ __device__ void limbs_add(unsigned long long* a, unsigned long long v, int off) 
   }
 }
 
-__device__ int limbs_bit(const unsigned long long* a, int pos) {
-  return (int)((a[pos >> 6] >> (pos & 63)) & 1ull);
-}
-
-// Round the limb integer times 2^-312 to the nearest double (ties to even).
+// Round the limb integer times 2^-312 to the nearest double (ties to even):
+// the 53 bits below the leading one, a round bit and a sticky bit.
 __device__ double limbs_to_double(const unsigned long long* a) {
-  int top = -1;
-  for (int i = kLimbs - 1; i >= 0 && top < 0; i--)
-    if (a[i]) top = i * 64 + 63 - __clzll((long long)a[i]);
-  if (top < 0) return 0.0;
-  if (top <= 52) {
-    unsigned long long m = a[0];  // fits in the lowest limb
-    return ldexp((double)m, -312);
-  }
-  int shift = top - 52;
-  unsigned long long m = 0ull;
-  for (int b = 52; b >= 0; b--) m = (m << 1) | (unsigned long long)limbs_bit(a, shift + b);
-  int round = limbs_bit(a, shift - 1);
-  int sticky = 0;
-  for (int b = shift - 2; b >= 0 && !sticky; b--) sticky = limbs_bit(a, b);
+  int ti = kLimbs - 1;
+  while (ti >= 0 && a[ti] == 0ull) ti--;
+  if (ti < 0) return 0.0;
+  const int top = ti * 64 + 63 - __clzll((long long)a[ti]);
+  if (top <= 52) return ldexp((double)a[0], -312);  // exact
+  const int shift = top - 52;
+  const int w = shift >> 6, o = shift & 63;
+  unsigned long long m = a[w] >> o;
+  if (o && w + 1 < kLimbs) m |= a[w + 1] << (64 - o);
+  m &= (1ull << 53) - 1ull;
+  const int rb = shift - 1;
+  const int round = (int)((a[rb >> 6] >> (rb & 63)) & 1ull);
+  bool sticky = (a[rb >> 6] & ((1ull << (rb & 63)) - 1ull)) != 0ull;
+  for (int i = 0; i < (rb >> 6) && !sticky; i++) sticky = a[i] != 0ull;
   if (round && (sticky || (m & 1ull))) m += 1ull;
   return ldexp((double)m, shift - 312);
 }
 
+// Launched with one warp: the lanes sum disjoint exponent bins into their own
+// limb integers, a butterfly adds the 32 integers (exact, so the order does
+// not matter), and lane 0 finishes.
 __global__ void k_delta(ParamsDev p, Workspace* ws, int mode, double arg, int need_quant,
                         int need_gt, unsigned long long ncoeff, unsigned long long npoints) {
   Scalars& s = ws->sc;
   if (s.status != RD_OK || s.constant) return;
   rd_result& r = ws->res;
+  const int lane = threadIdx.x;
+  unsigned long long acc[kLimbs];
+  if (mode == DELTA_FROM_MSE) {
+#pragma unroll
+    for (int i = 0; i < kLimbs; i++) acc[i] = 0ull;
+    for (int i = lane; i < kMseBins; i += 32) {
+      const unsigned long long lo = s.mse_lo[i], hi = s.mse_hi[i];
+      if (lo) limbs_add(acc, lo, 2 * i);
+      if (hi) limbs_add(acc, hi, 2 * i + 64);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      unsigned long long carry = 0ull;
+#pragma unroll
+      for (int j = 0; j < kLimbs; j++) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, acc[j], o);
+        const unsigned long long u = acc[j] + t;
+        const unsigned long long c1 = u < t;
+        const unsigned long long v = u + carry;
+        const unsigned long long c2 = v < carry;
+        acc[j] = v;
+        carry = c1 + c2;
+      }
+    }
+  }
+  if (lane != 0) return;
   double delta;
   if (mode == DELTA_FROM_MSE) {
-    unsigned long long acc[kLimbs];
-    for (int i = 0; i < kLimbs; i++) acc[i] = 0ull;
-    for (int i = 0; i < kMseBins; i++) {
-      if (s.mse_lo[i]) limbs_add(acc, s.mse_lo[i], 2 * i);
-      if (s.mse_hi[i]) limbs_add(acc, s.mse_hi[i], 2 * i + 64);
-    }
     double num = limbs_to_double(acc);
     s.mse_sp = num / (double)ncoeff;
     r.mse_sp = s.mse_sp;
@@ -268,42 +306,24 @@ __global__ void k_delta(ParamsDev p, Workspace* ws, int mode, double arg, int ne
 cudaError_t launch_delta(const ParamsDev& p, Workspace* ws, int mode, double arg, int need_quant,
                          int need_gt, unsigned long long ncoeff, unsigned long long npoints,
                          cudaStream_t s) {
-  k_delta<<<1, 1, 0, s>>>(p, ws, mode, arg, need_quant, need_gt, ncoeff, npoints);
+  k_delta<<<1, 32, 0, s>>>(p, ws, mode, arg, need_quant, need_gt, ncoeff, npoints);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// Entropy partials: sum of h log2 h per 1024-bin slice (fixed order).
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_entropy(Workspace* ws, int which_mask) {
-  __shared__ double part[32];
-  for (int which = 0; which < 2; which++) {
-    if (!((which_mask >> which) & 1)) continue;
-    if (ws->sc.status != RD_OK || ws->sc.constant) return;
-    uint32_t h = ws->hist[which][blockIdx.x * 1024 + threadIdx.x];
-    double v = h ? (double)h * log2((double)h) : 0.0;
-    v = warp_sum(v);
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      double t = warp_sum(part[threadIdx.x]);
-      if (threadIdx.x == 0) ws->ent_part[which][blockIdx.x] = t;
-    }
-    __syncthreads();
-  }
-}
-
-cudaError_t launch_entropy(Workspace* ws, int which_mask, cudaStream_t s) {
-  k_entropy<<<kEntropyCtas, 1024, 0, s>>>(ws, which_mask);
-  return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// Huffman cost of a histogram: the nonzero counts are compacted, sorted
-// ascending (bitonic network with virtual +inf padding, shared memory when
-// they fit, else global scratch), then merged with the two-queue method; the
-// internal node j is stored in the consumed leaf slot j.  Total cost = sum of
-// internal-node weights = coded bits.
+// Code statistics of the histograms, in one launch: per histogram one CTA
+// computes the Huffman cost, and kEntropyCtas CTAs compute slices of
+// sum h log2 h for the entropy (Eq. entropy).
+//
+// Huffman cost (sum of internal-node weights = coded bits).  The nonzero
+// counts are sorted ascending (a bitonic network in shared memory; for many
+// symbols a counting sort of the counts in global scratch).  The two-queue
+// method consumes leaves and internal nodes in ascending order and pairs
+// them consecutively; it runs here in phases: with a0 <= a1 the two smallest
+// remaining items, every item below T = a0 + a1 is consumed before any new
+// node (new nodes are >= T), so all such items are paired at once, in merged
+// order, and the new nodes (non-decreasing, as in the sequential method) are
+// appended to the internal queue.  The result equals the sequential merge.
 // ---------------------------------------------------------------------------
 __device__ void bitonic_sort(uint32_t* a, int n) {
   int P = 1;
@@ -334,108 +354,264 @@ __device__ void bitonic_sort(uint32_t* a, int n) {
   }
 }
 
-__global__ void __launch_bounds__(1024) k_huffman(Workspace* ws, int which0) {
-  extern __shared__ uint32_t s_keys[];
-  __shared__ uint32_t s_cnt[1024];
-  __shared__ unsigned long long s_tot[32];
-  __shared__ uint32_t s_base;
-  const int which = which0 + blockIdx.x;
-  if (ws->sc.status != RD_OK || ws->sc.constant) return;
+// number of elements of the sorted a[0..n) that are < T
+__device__ __forceinline__ uint32_t count_below(const uint32_t* a, uint32_t n, unsigned long long T) {
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    uint32_t mid = (lo + hi) >> 1;
+    if ((unsigned long long)a[mid] < T) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// number of A elements among the first d of merge(A, B), ties from A first
+__device__ __forceinline__ uint32_t merge_split(const uint32_t* A, uint32_t na, const uint32_t* B,
+                                                uint32_t nb, uint32_t d) {
+  uint32_t lo = d > nb ? d - nb : 0u, hi = d < na ? d : na;
+  while (lo < hi) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (A[mid] <= B[d - 1 - mid]) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+constexpr int kStatThreads = 1024;
+
+__device__ void huffman_cta(Workspace* ws, int which, uint32_t* smem) {
+  __shared__ uint32_t s_scan[kStatThreads];
+  __shared__ unsigned long long s_red[kStatThreads / 32];
+  __shared__ uint32_t s_state[8];
+  __shared__ uint32_t s_nbig;
+  const int tid = threadIdx.x;
   const uint32_t* h = ws->hist[which];
-  const int per = kNsym / 1024;  // 64 bins per thread
-  const int b0 = threadIdx.x * per;
+  constexpr int per = kNsym / kStatThreads;
+
   uint32_t nz = 0;
   unsigned long long tot = 0ull;
   for (int i = 0; i < per; i++) {
-    uint32_t c = h[b0 + i];
+    uint32_t c = h[i * kStatThreads + tid];
     nz += (c != 0u);
     tot += c;
   }
-  // exclusive scan of nonzero counts over the threads
-  s_cnt[threadIdx.x] = nz;
+  s_scan[tid] = nz;
   unsigned long long wt = warp_sum(tot);
-  if ((threadIdx.x & 31) == 0) s_tot[threadIdx.x >> 5] = wt;
+  if ((tid & 31) == 0) s_red[tid >> 5] = wt;
   __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {
-    uint32_t v = threadIdx.x >= (unsigned)off ? s_cnt[threadIdx.x - off] : 0u;
+  for (int off = 1; off < kStatThreads; off <<= 1) {
+    uint32_t v = tid >= off ? s_scan[tid - off] : 0u;
     __syncthreads();
-    s_cnt[threadIdx.x] += v;
+    s_scan[tid] += v;
     __syncthreads();
   }
-  const uint32_t K = s_cnt[1023];
-  const uint32_t start = s_cnt[threadIdx.x] - nz;
+  const uint32_t K = s_scan[kStatThreads - 1];
   unsigned long long ns = 0ull;
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < 32; i++) ns += s_tot[i];
-    s_base = 0;
+  if (tid < 32) {
+    ns = warp_sum(s_red[tid]);
   }
-  uint32_t* keys = (K <= (uint32_t)kHuffSmemKeys) ? s_keys : ws->sort_scratch[which];
-  uint32_t o = start;
-  for (int i = 0; i < per; i++) {
-    uint32_t c = h[b0 + i];
-    if (c) keys[o++] = c;
+  uint32_t* leaves;
+  uint32_t* nodes;
+  if (K <= (uint32_t)kHuffSmemKeys) {
+    leaves = smem;
+    nodes = smem + kHuffSmemKeys;
+    uint32_t o = s_scan[tid] - nz;
+    for (int i = 0; i < per; i++) {
+      uint32_t c = h[i * kStatThreads + tid];
+      if (c) leaves[o++] = c;
+    }
+    __syncthreads();
+    bitonic_sort(leaves, (int)K);
+  } else {
+    // counting sort of the counts: multiplicities of values below 2^16 in
+    // global scratch, the few larger counts sorted in shared memory
+    leaves = ws->sort_scratch[which];
+    nodes = ws->node_scratch[which];
+    uint32_t* cc = nodes;
+    uint32_t* big = smem;
+    for (int v = tid; v < kNsym; v += kStatThreads) cc[v] = 0u;
+    if (tid == 0) s_nbig = 0u;
+    __syncthreads();
+    for (int i = 0; i < per; i++) {
+      uint32_t c = h[i * kStatThreads + tid];
+      if (c == 0u) continue;
+      if (c < (uint32_t)kNsym)
+        atomicAdd(&cc[c], 1u);
+      else
+        big[atomicAdd(&s_nbig, 1u)] = c;
+    }
+    __syncthreads();
+    // exclusive scan of the multiplicities, values in ascending order
+    uint32_t local = 0;
+    for (int v = tid * per; v < (tid + 1) * per; v++) local += cc[v];
+    s_scan[tid] = local;
+    __syncthreads();
+    for (int off = 1; off < kStatThreads; off <<= 1) {
+      uint32_t v = tid >= off ? s_scan[tid - off] : 0u;
+      __syncthreads();
+      s_scan[tid] += v;
+      __syncthreads();
+    }
+    uint32_t o = s_scan[tid] - local;
+    for (int v = tid * per; v < (tid + 1) * per; v++)
+      for (uint32_t r = cc[v]; r > 0u; r--) leaves[o++] = (uint32_t)v;
+    __syncthreads();
+    const uint32_t nbig = s_nbig;
+    bitonic_sort(big, (int)nbig);
+    for (uint32_t i = tid; i < nbig; i += kStatThreads) leaves[K - nbig + i] = big[i];
+    __syncthreads();
   }
-  __syncthreads();
-  bitonic_sort(keys, (int)K);
-  if (threadIdx.x == 0) {
-    unsigned long long cost = 0ull;
-    if (K == 1) {
-      cost = ns;
-    } else if (K > 1) {
-      uint32_t lh = 0, nh = 0, nt = 0;
-      for (uint32_t step = 0; step + 1 < K; step++) {
-        uint32_t pick[2];
-        for (int j = 0; j < 2; j++) {
-          if (lh < K && (nh >= nt || keys[lh] <= keys[nh]))
-            pick[j] = keys[lh++];
-          else
-            pick[j] = keys[nh++];
+
+  unsigned long long cost = 0ull;
+  if (K == 1) {
+    cost = (tid == 0) ? ns : 0ull;
+  } else if (K > 1) {
+    // s_state: 0 lh, 1 ih, 2 it, 3 ml, 4 mi, 5 cl, 6 np, 7 done
+    if (tid == 0) {
+      s_state[0] = s_state[1] = s_state[2] = 0u;
+      s_state[7] = 0u;
+    }
+    __syncthreads();
+    for (;;) {
+      if (tid == 0) {
+        const uint32_t lh = s_state[0], ih = s_state[1], it = s_state[2];
+        if ((K - lh) + (it - ih) <= 1u) {
+          s_state[7] = 1u;
+        } else {
+          unsigned long long c4[4];
+          int n4 = 0;
+          if (lh < K) c4[n4++] = leaves[lh];
+          if (lh + 1 < K) c4[n4++] = leaves[lh + 1];
+          if (ih < it) c4[n4++] = nodes[ih];
+          if (ih + 1 < it) c4[n4++] = nodes[ih + 1];
+          unsigned long long a0 = ~0ull, a1 = ~0ull;
+          for (int i = 0; i < n4; i++) {
+            if (c4[i] < a0) { a1 = a0; a0 = c4[i]; }
+            else if (c4[i] < a1) a1 = c4[i];
+          }
+          const unsigned long long T = a0 + a1;
+          const uint32_t ml = count_below(leaves + lh, K - lh, T);
+          const uint32_t mi = count_below(nodes + ih, it - ih, T);
+          const uint32_t np = (ml + mi) >> 1;
+          s_state[3] = ml;
+          s_state[4] = mi;
+          s_state[5] = merge_split(leaves + lh, ml, nodes + ih, mi, 2u * np);
+          s_state[6] = np;
         }
-        uint32_t sum = pick[0] + pick[1];
-        keys[nt++] = sum;  // slot nt was consumed: lh >= nt + 1
-        cost += sum;
+      }
+      __syncthreads();
+      if (s_state[7]) break;
+      const uint32_t lh = s_state[0], ih = s_state[1], it = s_state[2];
+      const uint32_t ml = s_state[3], mi = s_state[4], np = s_state[6];
+      const uint32_t* A = leaves + lh;
+      const uint32_t* B = nodes + ih;
+      for (uint32_t j = tid; j < np; j += kStatThreads) {
+        uint32_t i = merge_split(A, ml, B, mi, 2u * j);
+        uint32_t k = 2u * j - i;
+        uint32_t e[2];
+        for (int t = 0; t < 2; t++) {
+          if (i < ml && (k >= mi || A[i] <= B[k])) e[t] = A[i++];
+          else e[t] = B[k++];
+        }
+        const uint32_t s = e[0] + e[1];
+        nodes[it + j] = s;
+        cost += s;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        s_state[0] = lh + s_state[5];
+        s_state[1] = ih + (2u * np - s_state[5]);
+        s_state[2] = it + np;
       }
     }
-    ws->huff[which].ns = ns;
-    ws->huff[which].cost = cost;
-    ws->huff[which].nsym = K;
+  }
+  __syncthreads();
+  cost = warp_sum(cost);
+  if ((tid & 31) == 0) s_red[tid >> 5] = cost;
+  __syncthreads();
+  if (tid < 32) {
+    unsigned long long c = warp_sum(s_red[tid]);
+    if (tid == 0) {
+      ws->huff[which].ns = ns;
+      ws->huff[which].cost = c;
+      ws->huff[which].nsym = K;
+    }
   }
 }
 
-cudaError_t launch_huffman(Workspace* ws, int which_mask, cudaStream_t s) {
-  static bool attr = false;
-  const int smem = kHuffSmemKeys * (int)sizeof(uint32_t);
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_huffman, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
+__device__ void entropy_cta(Workspace* ws, int which, int slice) {
+  __shared__ double part[kStatThreads / 32];
+  uint32_t h = ws->hist[which][slice * kStatThreads + threadIdx.x];
+  double v = h ? (double)h * log2((double)h) : 0.0;
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = warp_sum(part[threadIdx.x]);
+    if (threadIdx.x == 0) ws->ent_part[which][slice] = t;
   }
-  int first = (which_mask & 1) ? 0 : 1;
-  int count = (which_mask == 3) ? 2 : 1;
-  k_huffman<<<count, 1024, smem, s>>>(ws, first);
+}
+
+__global__ void __launch_bounds__(kStatThreads) k_code_stats(Workspace* ws, int which_mask) {
+  extern __shared__ uint32_t s_dyn[];
+  if (ws->sc.status != RD_OK || ws->sc.constant) return;
+  const int nh = (which_mask == 3) ? 2 : 1;
+  const int first = (which_mask & 1) ? 0 : 1;
+  const int b = blockIdx.x;
+  if (b < nh) {
+    huffman_cta(ws, first + b, s_dyn);
+  } else {
+    const int e = b - nh;
+    entropy_cta(ws, first + e / kEntropyCtas, e % kEntropyCtas);
+  }
+}
+
+cudaError_t launch_code_stats(Workspace* ws, int which_mask, cudaStream_t s) {
+  const int smem = 2 * kHuffSmemKeys * (int)sizeof(uint32_t);
+  const int nh = (which_mask == 3) ? 2 : 1;
+  k_code_stats<<<nh * (1 + kEntropyCtas), kStatThreads, smem, s>>>(ws, which_mask);
   return cudaGetLastError();
+}
+
+cudaError_t prepare_code_stats() {
+  const int smem = 2 * kHuffSmemKeys * (int)sizeof(uint32_t);
+  return cudaFuncSetAttribute(k_code_stats, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 // ---------------------------------------------------------------------------
 // Finish: SZ rates, ground-truth rates, PSNRs and the selection.
 // ---------------------------------------------------------------------------
-__device__ double sum_parts(const double* a, int n) {
-  // fixed-order: each lane sums a strided subset, then a fixed butterfly
+constexpr int kFinishThreads = 256;
+
+// Fixed-order block sum (strided per-thread sums, then a fixed tree); the
+// result is valid in thread 0.
+__device__ double block_sum_parts(const double* a, int n, double* red) {
   double v = 0.0;
-  for (int i = threadIdx.x; i < n; i += 32) v += a[i];
-  return warp_sum(v);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += a[i];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    t = warp_sum(t);
+  }
+  __syncthreads();
+  return t;
 }
 
-__global__ void k_finish(ParamsDev p, Workspace* ws, int passes, int zfp_parts, int sz_parts,
-                         long long npoints_all, unsigned long long zfp_npoints) {
+__global__ void __launch_bounds__(kFinishThreads) k_finish(ParamsDev p, Workspace* ws, int passes,
+                                                           int zfp_parts, int sz_parts,
+                                                           long long npoints_all,
+                                                           unsigned long long zfp_npoints) {
+  __shared__ double red[kFinishThreads / 32];
   Scalars& s = ws->sc;
   if (s.status != RD_OK) return;
   rd_result& r = ws->res;
   rd_truth& t = ws->truth;
-  double zsse = 0.0, ssse = 0.0;
+  double zsse = 0.0, ssse = 0.0, plogp = 0.0;
   if (!s.constant) {
-    if (passes & P_ZFP_GT) zsse = sum_parts(ws->zfp_sse, zfp_parts);
-    if (passes & P_SZ_GT) ssse = sum_parts(ws->sz_sse, sz_parts);
+    if (passes & P_ZFP_GT) zsse = block_sum_parts(ws->zfp_sse, zfp_parts, red);
+    if (passes & P_SZ_GT) ssse = block_sum_parts(ws->sz_sse, sz_parts, red);
+    if (passes & P_SZ_EST) plogp = block_sum_parts(ws->ent_part[0], kEntropyCtas, red);
   }
   if (threadIdx.x != 0) return;
   if (s.constant) {
@@ -452,8 +628,6 @@ __global__ void k_finish(ParamsDev p, Workspace* ws, int passes, int zfp_parts, 
   double lvr = 20.0 * log10(s.vr);
   if (passes & P_SZ_EST) {
     const HuffOut& hh = ws->huff[0];
-    double plogp = 0.0;
-    for (int i = 0; i < kEntropyCtas; i++) plogp += ws->ent_part[0][i];
     double ns = (double)hh.ns;
     double H = log2(ns) - plogp / ns;
     if (H < 0.0) H = 0.0;
@@ -515,7 +689,7 @@ __global__ void k_finish(ParamsDev p, Workspace* ws, int passes, int zfp_parts, 
 cudaError_t launch_finish(const ParamsDev& p, Workspace* ws, int passes, int zfp_parts,
                           int sz_parts, long long npoints_all, unsigned long long zfp_npoints,
                           cudaStream_t s) {
-  k_finish<<<1, 32, 0, s>>>(p, ws, passes, zfp_parts, sz_parts, npoints_all, zfp_npoints);
+  k_finish<<<1, kFinishThreads, 0, s>>>(p, ws, passes, zfp_parts, sz_parts, npoints_all, zfp_npoints);
   return cudaGetLastError();
 }
 

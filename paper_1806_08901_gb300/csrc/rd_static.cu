@@ -27,9 +27,9 @@ using namespace rdk;
 
 namespace {
 
-// Stated maximum of the fixed scratch: 1.125 MiB per device, held for the
+// Stated maximum of the fixed scratch: 1.75 MiB per device, held for the
 // life of the process by every GPU that loads the library.
-constexpr size_t kStaticScratchBytes = 1179648;
+constexpr size_t kStaticScratchBytes = 1835008;
 static_assert(sizeof(Workspace) <= kStaticScratchBytes, "workspace exceeds the static scratch");
 
 static __device__ __align__(256) unsigned char g_select_scratch[kStaticScratchBytes];
@@ -59,6 +59,7 @@ int setup_device(int dev, DeviceSlot** out) {
     if (cudaGetSymbolAddress(&p, g_select_scratch) != cudaSuccess || !p) return RD_ERR_CUDA;
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return RD_ERR_CUDA;
+    if (prepare_code_stats() != cudaSuccess) return RD_ERR_CUDA;
     s.ws = static_cast<Workspace*>(p);
     s.range_ctas = sms * 4;
     for (int d = 1; d <= 3; d++) {
@@ -171,8 +172,7 @@ extern "C" int32_t rd_select_static(const rd_field* fld, const rd_params* prm, r
   if (e == cudaSuccess) e = launch_zfp(f, p, P_ZFP_EST, ws, slot->zfp_ctas[d], s, &zparts);
   if (e == cudaSuccess) e = launch_delta(p, ws, DELTA_FROM_MSE, 0.0, 1, 0, ncoeff, npts, s);
   if (e == cudaSuccess) e = launch_sz_est(f, p, ws, slot->sz_ctas[d], s);
-  if (e == cudaSuccess) e = launch_entropy(ws, 1, s);
-  if (e == cudaSuccess) e = launch_huffman(ws, 1, s);
+  if (e == cudaSuccess) e = launch_code_stats(ws, 1, s);
   if (e == cudaSuccess) e = launch_finish(p, ws, passes, zparts, 0, f.N, npts, s);
   rd_result r;
   int32_t status = RD_OK;

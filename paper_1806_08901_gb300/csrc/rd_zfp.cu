@@ -107,7 +107,6 @@ __device__ __forceinline__ unsigned ec_bits(const int* c, int kmin) {
 template <int D>
 struct BlockWork {
   static constexpr int NB = 1 << (2 * D);
-  int ci[NB];        // lifted coefficients, sequency order
   unsigned u[NB];    // negabinary, sequency order
   BlockInfo bi;
 
@@ -121,8 +120,7 @@ struct BlockWork {
     if (!bi.all_zero) fwd_xform<D>(c);
 #pragma unroll
     for (int p = 0; p < NB; p++) {
-      ci[p] = c[S.perm[p]];
-      u[p] = to_negabinary(ci[p]);
+      u[p] = to_negabinary(c[S.perm[p]]);
     }
   }
   __device__ __forceinline__ unsigned keep_mask() const {
@@ -249,7 +247,7 @@ __global__ void __launch_bounds__(kZfpThreads) k_zfp(FieldDev f, ParamsDev p, Wo
 #pragma unroll
         for (int q = 0; q < NB; q++) {
           s2 += 2 * nsb(q);
-          long long d = (long long)w.ci[q] - (long long)from_negabinary(w.u[q] & keep);
+          long long d = (long long)from_negabinary(w.u[q]) - (long long)from_negabinary(w.u[q] & keep);
           unsigned long long ad = (unsigned long long)(d < 0 ? -d : d);
           unsigned long long sq = ad * ad;  // |d| < 2^32
           lo += sq;
@@ -265,7 +263,7 @@ __global__ void __launch_bounds__(kZfpThreads) k_zfp(FieldDev f, ParamsDev p, Wo
           } else {
             s2 += 2 * nsb(q);
           }
-          long long d = (long long)w.ci[q] - (long long)from_negabinary(w.u[q] & keep);
+          long long d = (long long)from_negabinary(w.u[q]) - (long long)from_negabinary(w.u[q] & keep);
           unsigned long long ad = (unsigned long long)(d < 0 ? -d : d);
           unsigned long long sq = ad * ad;  // |d| < 2^32
           lo += sq;
@@ -285,14 +283,25 @@ __global__ void __launch_bounds__(kZfpThreads) k_zfp(FieldDev f, ParamsDev p, Wo
       my_bits += w.bits();
       float xr[NB];
       w.reconstruct(xr);
-      const unsigned long long vm = valid_mask<D>(f, b);
       float e2[NB];
       float emx = 0.0f;
+      bool interior = true;
 #pragma unroll
-      for (int t = 0; t < NB; t++) {
-        float e = __fsub_rn(v[t], xr[t]);
-        e2[t] = ((vm >> t) & 1ull) ? e : 0.0f;
-        emx = fmaxf(emx, fabsf(e2[t]));
+      for (int k = 0; k < D; k++) interior = interior && (4 * b[k] + 4 <= f.n[k]);
+      if (interior) {
+#pragma unroll
+        for (int t = 0; t < NB; t++) {
+          e2[t] = __fsub_rn(v[t], xr[t]);
+          emx = fmaxf(emx, fabsf(e2[t]));
+        }
+      } else {
+        const unsigned long long vm = valid_mask<D>(f, b);
+#pragma unroll
+        for (int t = 0; t < NB; t++) {
+          float e = __fsub_rn(v[t], xr[t]);
+          e2[t] = ((vm >> t) & 1ull) ? e : 0.0f;
+          emx = fmaxf(emx, fabsf(e2[t]));
+        }
       }
       my_max = fmaxf(my_max, emx);
       if (emx > 0.0f) {
@@ -300,10 +309,19 @@ __global__ void __launch_bounds__(kZfpThreads) k_zfp(FieldDev f, ParamsDev p, Wo
         // of errors far below eb_abs neither underflow nor lose the sum
         const unsigned E = (__float_as_uint(emx) >> 23) & 0xffu;
         const int k = E ? 127 - (int)E : 149;
+        if (k <= 127 && k >= -126) {
+          const float sc = pow2f(k);
 #pragma unroll
-        for (int t = 0; t < NB; t++) {
-          float es = mul_pow2(e2[t], k);
-          e2[t] = __fmul_rn(es, es);
+          for (int t = 0; t < NB; t++) {
+            const float es = __fmul_rn(e2[t], sc);
+            e2[t] = __fmul_rn(es, es);
+          }
+        } else {
+#pragma unroll
+          for (int t = 0; t < NB; t++) {
+            const float es = mul_pow2(e2[t], k);
+            e2[t] = __fmul_rn(es, es);
+          }
         }
         // pairwise sum of the block's scaled squared errors in float
 #pragma unroll

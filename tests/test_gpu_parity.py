@@ -295,6 +295,48 @@ def test_repeated_calls_are_deterministic(R, ctx):
         assert ctx.evaluate(xd, op) == a
 
 
+def test_profiling_across_graph_capture_and_replay(R, ctx):
+    """Direct call, captured call and replays give identical records; the
+    per-kernel timings count every launch and leave no error behind for the
+    next CUDA user in the process."""
+    x = FIELDS["3d_tiles"]
+    xd = torch.from_numpy(x).cuda()
+    p = _gp(R, O.params(eb=1e-3, r_sp=0.05))
+    ctx.set_profiling(True)
+    ctx.reset_profile()
+    base = ctx.evaluate(xd, p)
+    for _ in range(4):
+        assert ctx.evaluate(xd, p) == base
+    st = ctx.kernel_stats()
+    assert st["zfp_pass"][1] == 5 and st["zfp_pass"][0] > 0
+    assert st["sz_pass"][1] == 5 and st["code_stats"][1] == 5
+    ctx.set_profiling(False)
+    y = torch.ones(1000, device="cuda")
+    y.add_(1.0)
+    torch.cuda.synchronize()
+    assert float(y.sum()) == 2000.0
+
+
+def test_large_alphabet_huffman(R, ctx):
+    """White noise at a tiny bin: tens of thousands of distinct symbols, which
+    sends the Huffman cost through the counting-sort path."""
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal((256, 256)).astype(np.float32)
+    op = O.params(eb=1e-3, r_sp=1.0)
+    xd = torch.from_numpy(x).cuda()
+    for delta in (2e-4, 1e-3):
+        gs = ctx.estimate_sz(xd, _gp(R, op), delta=delta)
+        os_ = O.estimate_sz(x, op, delta=delta, want_hist=True)
+        assert np.array_equal(ctx.histograms()[0], os_["hist"])
+        for k in ("sz_ns", "sz_huff_bits", "sz_nesc", "sz_nsym", "br_sz_huff"):
+            assert gs[k] == os_[k], (k, delta)
+        assert _rel(gs["br_sz"], os_["br_sz"]) <= REL_ENTROPY
+        gt = ctx.ground_truth(xd, _gp(R, op), eb_sz=delta / 2)
+        ot = O.ground_truth(x, op, eb_sz=delta / 2)
+        check_truth(gt, ot)
+    assert os_["sz_nsym"] > 0
+
+
 # ---------------------------------------------------------------------------
 # Full-size Hurricane-shaped field (100 x 500 x 500), as the benchmark runs it
 # ---------------------------------------------------------------------------
