@@ -175,7 +175,7 @@ int32_t rd_evaluate(rd_context* ctx, const rd_field* field,
  * framework whose allocator must serve every allocation) or that cannot take
  * the synchronisation an allocation may imply.  It needs no context and
  * calls no cudaMalloc, cudaFree, cudaMallocHost or other allocating routine:
- * its scratch is one fixed 1.75 MiB array inside the library, held by every
+ * its scratch is one fixed 2.25 MiB array inside the library, held by every
  * GPU that loads the library until the process exits.
  *  - field: DEVICE memory only (location RD_LOC_HOST is rejected, since a
  *    host field would need a staging buffer), at most 2^31-1 points; larger

@@ -18,7 +18,7 @@ namespace {
 
 const char* kKernelNames[K_COUNT] = {
     "reset", "range", "prepare", "zfp_pass", "delta", "sz_est", "sz_pass",
-    "entropy", "code_stats", "finish", "zfp_inspect", "sz_inspect"};
+    "code_prep", "huffman", "finish", "zfp_inspect", "sz_inspect"};
 
 struct KStat {
   double ms;
@@ -345,7 +345,8 @@ int issue(rd_context* c, const CallKey& k, const Geometry& g, cudaStream_t s) {
   }
   int hist_mask = ((passes & P_SZ_EST) ? 1 : 0) | ((passes & P_SZ_GT) ? 2 : 0);
   if (hist_mask) {
-    if ((rc = launch(c, K_HUFFMAN, s, [&] { return launch_code_stats(ws, hist_mask, s); }))) return rc;
+    if ((rc = launch(c, K_CODE_PREP, s, [&] { return launch_code_prep(ws, hist_mask, s); }))) return rc;
+    if ((rc = launch(c, K_HUFFMAN, s, [&] { return launch_huffman(ws, hist_mask, s); }))) return rc;
   }
   if ((rc = launch(c, K_FINISH, s, [&] {
          return launch_finish(p, ws, passes, zfp_parts, sz_parts, f.N, g.npoints_sampled, s);
@@ -469,7 +470,6 @@ int run(rd_context* c, const rd_field* fld, const rd_params* prm, int passes, in
   }
   rd_result r = c->out->res;
   rd_truth t = c->out->truth;
-  int nb = 1;
   for (int k = 0; k < d; k++) r.strides[k] = f.s[k];
   for (int k = d; k < 3; k++) r.strides[k] = 0;
   r.n_blocks = (uint64_t)f.nblocks;
@@ -479,7 +479,6 @@ int run(rd_context* c, const rd_field* fld, const rd_params* prm, int passes, in
     r.zfp_npoints = g.npoints_sampled;
     if (passes & P_ZFP_EST) r.zfp_ncoeff = ncoeff;
   }
-  (void)nb;
   if (g.partial) r.flags |= RD_F_PARTIAL_BLOCKS;
   if (est) *est = r;
   if (truth) *truth = t;

@@ -53,8 +53,10 @@ struct Workspace {
   HuffOut huff[2];
   double zfp_sse[kMaxGrid];           // per-CTA partial sums (fixed order)
   double sz_sse[kMaxGrid];
+  uint32_t count_of[2][kNsym];        // multiplicity of each count value below 2^16
+  uint32_t nbig[2];                   // counts of 2^16 or more
   uint32_t sort_scratch[2][kNsym];    // Huffman leaves when K is large
-  uint32_t node_scratch[2][kNsym];    // Huffman internal nodes when K is large
+  uint32_t node_scratch[2][kNsym];    // counts >= 2^16, then Huffman internal nodes when K is large
   rd_result res;
   rd_truth truth;
 };
@@ -99,7 +101,7 @@ enum KernelId {
   K_DELTA,
   K_SZ_EST,
   K_SZ_GT,
-  K_ENTROPY,
+  K_CODE_PREP,
   K_HUFFMAN,
   K_FINISH,
   K_ZFP_INSPECT,
@@ -130,8 +132,12 @@ cudaError_t launch_sz_est(const FieldDev& f, const ParamsDev& p, Workspace* ws,
                           int ctas, cudaStream_t s);
 cudaError_t launch_sz_gt(const FieldDev& f, const ParamsDev& p, int with_est,
                          Workspace* ws, int ctas, cudaStream_t s, int* grid_used);
-// Huffman cost and entropy partials of the histograms in which_mask (bit 0 =
-// estimate, bit 1 = ground truth); prepare_code_stats() once per device first.
+// Entropy partials and count-of-counts (launch_code_prep), then the Huffman
+// cost (launch_huffman), of the histograms in which_mask (bit 0 = estimate,
+// bit 1 = ground truth); launch_code_stats issues both.  prepare_code_stats()
+// once per device first.
+cudaError_t launch_code_prep(Workspace* ws, int which_mask, cudaStream_t s);
+cudaError_t launch_huffman(Workspace* ws, int which_mask, cudaStream_t s);
 cudaError_t launch_code_stats(Workspace* ws, int which_mask, cudaStream_t s);
 cudaError_t prepare_code_stats();
 cudaError_t launch_finish(const ParamsDev& p, Workspace* ws, int passes,

@@ -17,6 +17,8 @@ __global__ void k_reset(Workspace* ws) {
   const int nth = gridDim.x * blockDim.x;
   uint32_t* h = &ws->hist[0][0];
   for (int i = tid; i < 2 * kNsym; i += nth) h[i] = 0u;
+  uint32_t* cc = &ws->count_of[0][0];
+  for (int i = tid; i < 2 * kNsym; i += nth) cc[i] = 0u;
   unsigned long long* lo = ws->sc.mse_lo;
   unsigned long long* hi = ws->sc.mse_hi;
   for (int i = tid; i < kMseBins; i += nth) {
@@ -40,6 +42,7 @@ __global__ void k_reset(Workspace* ws) {
     s.zfp_maxerr = 0u;
     s.sz_maxerr = 0u;
     for (int w = 0; w < 2; w++) {
+      ws->nbig[w] = 0u;
       ws->huff[w].ns = 0ull;
       ws->huff[w].cost = 0ull;
       ws->huff[w].nsym = 0u;
@@ -311,15 +314,16 @@ cudaError_t launch_delta(const ParamsDev& p, Workspace* ws, int mode, double arg
 }
 
 // ---------------------------------------------------------------------------
-// Code statistics of the histograms, in one launch: per histogram one CTA
-// computes the Huffman cost, and kEntropyCtas CTAs compute slices of
-// sum h log2 h for the entropy (Eq. entropy).
+// Code statistics of the histograms (Algorithm 1 lines 8-9 and the SZ ground
+// truth), in two launches: k_code_prep spreads each histogram over
+// kEntropyCtas CTAs (entropy partials, count-of-counts), k_huffman runs one
+// CTA per histogram for the Huffman cost.
 //
 // Huffman cost (sum of internal-node weights = coded bits).  The nonzero
-// counts are sorted ascending (a bitonic network in shared memory; for many
-// symbols a counting sort of the counts in global scratch).  The two-queue
-// method consumes leaves and internal nodes in ascending order and pairs
-// them consecutively; it runs here in phases: with a0 <= a1 the two smallest
+// counts are sorted ascending (a counting sort by count value; the rare
+// counts of 2^16 or more by a bitonic network).  The two-queue method
+// consumes leaves and internal nodes in ascending order and pairs them
+// consecutively; it runs here in phases: with a0 <= a1 the two smallest
 // remaining items, every item below T = a0 + a1 is consumed before any new
 // node (new nodes are >= T), so all such items are paired at once, in merged
 // order, and the new nodes (non-decreasing, as in the sequential method) are
@@ -354,16 +358,6 @@ __device__ void bitonic_sort(uint32_t* a, int n) {
   }
 }
 
-// number of elements of the sorted a[0..n) that are < T
-__device__ __forceinline__ uint32_t count_below(const uint32_t* a, uint32_t n, unsigned long long T) {
-  uint32_t lo = 0, hi = n;
-  while (lo < hi) {
-    uint32_t mid = (lo + hi) >> 1;
-    if ((unsigned long long)a[mid] < T) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
-
 // number of A elements among the first d of merge(A, B), ties from A first
 __device__ __forceinline__ uint32_t merge_split(const uint32_t* A, uint32_t na, const uint32_t* B,
                                                 uint32_t nb, uint32_t d) {
@@ -375,90 +369,217 @@ __device__ __forceinline__ uint32_t merge_split(const uint32_t* A, uint32_t na, 
   return lo;
 }
 
-constexpr int kStatThreads = 1024;
 
-__device__ void huffman_cta(Workspace* ws, int which, uint32_t* smem) {
-  __shared__ uint32_t s_scan[kStatThreads];
-  __shared__ unsigned long long s_red[kStatThreads / 32];
-  __shared__ uint32_t s_state[8];
-  __shared__ uint32_t s_nbig;
-  const int tid = threadIdx.x;
-  const uint32_t* h = ws->hist[which];
-  constexpr int per = kNsym / kStatThreads;
+constexpr int kPrepThreads = 256;   // code-statistics prep CTAs (1024 bins each)
+constexpr int kHuffThreads = 1024;  // Huffman CTA
 
-  uint32_t nz = 0;
-  unsigned long long tot = 0ull;
-  for (int i = 0; i < per; i++) {
-    uint32_t c = h[i * kStatThreads + tid];
-    nz += (c != 0u);
-    tot += c;
+// Number of elements of the sorted a[0..n) below T, found by one warp: each
+// round tests 32 evenly spaced elements and keeps the gap holding the answer.
+__device__ uint32_t warp_count_below(const uint32_t* a, uint32_t n, unsigned long long T) {
+  const int lane = threadIdx.x & 31;
+  uint32_t lo = 0, hi = n;  // the answer lies in [lo, hi]
+  while (hi - lo > 32u) {
+    const uint32_t step = (hi - lo + 31u) / 32u;
+    const uint32_t idx = lo + (uint32_t)lane * step;
+    const bool p = idx < hi && (unsigned long long)a[idx] < T;
+    const int c = __popc(__ballot_sync(0xffffffffu, p));
+    if (c == 0) return lo;
+    const uint32_t nl = lo + (uint32_t)(c - 1) * step + 1u;
+    const uint32_t nh = lo + (uint32_t)c * step;
+    lo = nl;
+    hi = nh < hi ? nh : hi;
   }
-  s_scan[tid] = nz;
-  unsigned long long wt = warp_sum(tot);
-  if ((tid & 31) == 0) s_red[tid >> 5] = wt;
+  const uint32_t idx = lo + (uint32_t)lane;
+  const bool p = idx < hi && (unsigned long long)a[idx] < T;
+  return lo + (uint32_t)__popc(__ballot_sync(0xffffffffu, p));
+}
+
+// Number of A elements among the first d of merge(A, B) (ties: A first),
+// found by one warp: the predicate A[i] <= B[d-1-i] holds for a prefix of i.
+__device__ uint32_t warp_merge_split(const uint32_t* A, uint32_t na, const uint32_t* B,
+                                     uint32_t nb, uint32_t d) {
+  const int lane = threadIdx.x & 31;
+  uint32_t lo = d > nb ? d - nb : 0u, hi = d < na ? d : na;  // answer in [lo, hi]
+  while (hi - lo > 32u) {
+    const uint32_t step = (hi - lo + 31u) / 32u;
+    const uint32_t i = lo + (uint32_t)lane * step;
+    const bool p = i < hi && A[i] <= B[d - 1 - i];
+    const int c = __popc(__ballot_sync(0xffffffffu, p));
+    if (c == 0) return lo;
+    const uint32_t nl = lo + (uint32_t)(c - 1) * step + 1u;
+    const uint32_t nh = lo + (uint32_t)c * step;
+    lo = nl;
+    hi = nh < hi ? nh : hi;
+  }
+  const uint32_t i = lo + (uint32_t)lane;
+  const bool p = i < hi && A[i] <= B[d - 1 - i];
+  return lo + (uint32_t)__popc(__ballot_sync(0xffffffffu, p));
+}
+
+// ---------------------------------------------------------------------------
+// Prep (many CTAs, 1024 bins each): the slice's sum of h log2 h for the
+// entropy; the multiplicity of every count value below 2^16 (a counting sort
+// of the counts, lanes with equal counts merged into one atomic); counts of
+// 2^16 or more (at most N / 2^16 of them) appended to a list.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kPrepThreads) k_code_prep(Workspace* ws, int which_mask) {
+  __shared__ double part[kPrepThreads / 32];
+  if (ws->sc.status != RD_OK || ws->sc.constant) return;
+  const int first = (which_mask & 1) ? 0 : 1;
+  const int which = first + blockIdx.x / kEntropyCtas;
+  const int slice = blockIdx.x % kEntropyCtas;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  uint32_t* cc = ws->count_of[which];
+  uint32_t* big = ws->node_scratch[which];
+  double v = 0.0;
+#pragma unroll
+  for (int k = 0; k < 1024 / kPrepThreads; k++) {
+    const uint32_t c = ws->hist[which][slice * 1024 + k * kPrepThreads + threadIdx.x];
+    if (c) v += (double)c * log2((double)c);
+    const bool small = c != 0u && c < (uint32_t)kNsym;
+    const bool large = c >= (uint32_t)kNsym;
+    const unsigned ms = __ballot_sync(0xffffffffu, small);
+    const unsigned mb = __ballot_sync(0xffffffffu, large);
+    if (small) {
+      const unsigned same = __match_any_sync(ms, c);
+      if (lane == __ffs(same) - 1) atomicAdd(&cc[c], (uint32_t)__popc(same));
+    }
+    if (mb) {
+      uint32_t base = 0u;
+      if (lane == __ffs(mb) - 1) base = atomicAdd(&ws->nbig[which], (uint32_t)__popc(mb));
+      base = __shfl_sync(0xffffffffu, base, __ffs(mb) - 1);
+      if (large) big[base + __popc(mb & lt_mask)] = c;
+    }
+  }
+  v = warp_sum(v);
+  if (lane == 0) part[threadIdx.x >> 5] = v;
   __syncthreads();
-  for (int off = 1; off < kStatThreads; off <<= 1) {
-    uint32_t v = tid >= off ? s_scan[tid - off] : 0u;
+  if (threadIdx.x < 32) {
+    const double t = warp_sum(threadIdx.x < kPrepThreads / 32 ? part[threadIdx.x] : 0.0);
+    if (threadIdx.x == 0) ws->ent_part[which][slice] = t;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Huffman cost (one CTA per histogram).  The ascending leaf array is the
+// counting-sorted small counts followed by the sorted large ones.  Then the
+// two-queue method in phases: with a0 <= a1 the two smallest remaining
+// items, every item below T = a0 + a1 is consumed before any new node (new
+// nodes are >= T), so all of them are paired at once in merged order (ties:
+// leaves first); the new nodes, non-decreasing as in the sequential method,
+// are appended to the internal queue.  Cost = sum of internal-node weights.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kHuffThreads) k_huffman(Workspace* ws, int which0) {
+  extern __shared__ uint32_t s_dyn[];
+  __shared__ uint32_t s_pre[kHuffThreads];   // per-thread small-count totals, scanned
+  __shared__ unsigned long long s_red[kHuffThreads / 32];
+  __shared__ uint32_t s_wmax[32];
+  __shared__ uint32_t s_state[8];
+  if (ws->sc.status != RD_OK || ws->sc.constant) return;
+  const int which = which0 + blockIdx.x;
+  const int tid = threadIdx.x;
+  const uint32_t* cc = ws->count_of[which];
+  constexpr int vper = kNsym / kHuffThreads;  // 64 count values per thread
+
+  // multiplicities of this thread's values and their contribution to N_s
+  uint32_t tot = 0u;
+  unsigned long long nsum = 0ull;
+  {
+    const uint4* c4 = reinterpret_cast<const uint4*>(cc + tid * vper);
+#pragma unroll
+    for (int k = 0; k < vper / 4; k++) {
+      const uint4 q = c4[k];
+      const uint32_t v0 = (uint32_t)(tid * vper + 4 * k);
+      tot += q.x + q.y + q.z + q.w;
+      nsum += (unsigned long long)q.x * v0 + (unsigned long long)q.y * (v0 + 1) +
+              (unsigned long long)q.z * (v0 + 2) + (unsigned long long)q.w * (v0 + 3);
+    }
+  }
+  const uint32_t nbig = ws->nbig[which];
+  const uint32_t* big = ws->node_scratch[which];
+  for (uint32_t i = tid; i < nbig; i += kHuffThreads) nsum += big[i];
+  s_pre[tid] = tot;
+  nsum = warp_sum(nsum);
+  if ((tid & 31) == 0) s_red[tid >> 5] = nsum;
+  __syncthreads();
+  for (int off = 1; off < kHuffThreads; off <<= 1) {
+    const uint32_t t = tid >= off ? s_pre[tid - off] : 0u;
     __syncthreads();
-    s_scan[tid] += v;
+    s_pre[tid] += t;
     __syncthreads();
   }
-  const uint32_t K = s_scan[kStatThreads - 1];
+  const uint32_t nsmall = s_pre[kHuffThreads - 1];
+  const uint32_t K = nsmall + nbig;
   unsigned long long ns = 0ull;
-  if (tid < 32) {
-    ns = warp_sum(s_red[tid]);
-  }
+  if (tid < 32) ns = warp_sum(s_red[tid]);
+
   uint32_t* leaves;
   uint32_t* nodes;
   if (K <= (uint32_t)kHuffSmemKeys) {
-    leaves = smem;
-    nodes = smem + kHuffSmemKeys;
-    uint32_t o = s_scan[tid] - nz;
-    for (int i = 0; i < per; i++) {
-      uint32_t c = h[i * kStatThreads + tid];
-      if (c) leaves[o++] = c;
-    }
-    __syncthreads();
-    bitonic_sort(leaves, (int)K);
+    leaves = s_dyn;
+    nodes = s_dyn + kHuffSmemKeys;
   } else {
-    // counting sort of the counts: multiplicities of values below 2^16 in
-    // global scratch, the few larger counts sorted in shared memory
     leaves = ws->sort_scratch[which];
-    nodes = ws->node_scratch[which];
-    uint32_t* cc = nodes;
-    uint32_t* big = smem;
-    for (int v = tid; v < kNsym; v += kStatThreads) cc[v] = 0u;
-    if (tid == 0) s_nbig = 0u;
-    __syncthreads();
-    for (int i = 0; i < per; i++) {
-      uint32_t c = h[i * kStatThreads + tid];
-      if (c == 0u) continue;
-      if (c < (uint32_t)kNsym)
-        atomicAdd(&cc[c], 1u);
-      else
-        big[atomicAdd(&s_nbig, 1u)] = c;
-    }
-    __syncthreads();
-    // exclusive scan of the multiplicities, values in ascending order
-    uint32_t local = 0;
-    for (int v = tid * per; v < (tid + 1) * per; v++) local += cc[v];
-    s_scan[tid] = local;
-    __syncthreads();
-    for (int off = 1; off < kStatThreads; off <<= 1) {
-      uint32_t v = tid >= off ? s_scan[tid - off] : 0u;
-      __syncthreads();
-      s_scan[tid] += v;
-      __syncthreads();
-    }
-    uint32_t o = s_scan[tid] - local;
-    for (int v = tid * per; v < (tid + 1) * per; v++)
-      for (uint32_t r = cc[v]; r > 0u; r--) leaves[o++] = (uint32_t)v;
-    __syncthreads();
-    const uint32_t nbig = s_nbig;
-    bitonic_sort(big, (int)nbig);
-    for (uint32_t i = tid; i < nbig; i += kStatThreads) leaves[K - nbig + i] = big[i];
-    __syncthreads();
+    nodes = ws->node_scratch[which];  // free once the large counts are copied
   }
+  // expansion of the small counts in ascending order: the first position of
+  // every present value is marked with the value, then a running maximum
+  // over positions fills each run (values ascend with position, 0 is absent)
+  for (uint32_t o = tid; o < nsmall; o += kHuffThreads) leaves[o] = 0u;
+  __syncthreads();
+  {
+    uint32_t o = s_pre[tid] - tot;
+    const uint4* c4 = reinterpret_cast<const uint4*>(cc + tid * vper);
+#pragma unroll 4
+    for (int k = 0; k < vper / 4; k++) {
+      const uint4 q = c4[k];
+      const uint32_t v0 = (uint32_t)(tid * vper + 4 * k);
+      if (q.x) { leaves[o] = v0; o += q.x; }
+      if (q.y) { leaves[o] = v0 + 1; o += q.y; }
+      if (q.z) { leaves[o] = v0 + 2; o += q.z; }
+      if (q.w) { leaves[o] = v0 + 3; o += q.w; }
+    }
+  }
+  // the large counts follow (in the global layout they move from the node
+  // scratch to the leaf array)
+  for (uint32_t i = tid; i < nbig; i += kHuffThreads) leaves[nsmall + i] = big[i];
+  __syncthreads();
+  {
+    const uint32_t C = (nsmall + kHuffThreads - 1) / kHuffThreads;
+    const uint32_t o0 = min(nsmall, (uint32_t)tid * C), o1 = min(nsmall, o0 + C);
+    uint32_t run = 0u;
+    for (uint32_t o = o0; o < o1; o++) run = max(run, leaves[o]);
+    // exclusive running maximum over the threads' chunks
+    const int lane = tid & 31;
+    uint32_t inc = run;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, inc, off);
+      if (lane >= off) inc = max(inc, t);
+    }
+    if (lane == 31) s_wmax[tid >> 5] = inc;
+    __syncthreads();
+    if (tid < 32) {
+      uint32_t w = s_wmax[tid];
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, w, off);
+        if (tid >= off) w = max(w, t);
+      }
+      s_wmax[tid] = w;
+    }
+    __syncthreads();
+    uint32_t carry = __shfl_up_sync(0xffffffffu, inc, 1);
+    if (lane == 0) carry = 0u;
+    if (tid >= 32) carry = max(carry, s_wmax[(tid >> 5) - 1]);
+    for (uint32_t o = o0; o < o1; o++) {
+      carry = max(carry, leaves[o]);
+      leaves[o] = carry;
+    }
+  }
+  __syncthreads();
+  bitonic_sort(leaves + nsmall, (int)nbig);
 
   unsigned long long cost = 0ull;
   if (K == 1) {
@@ -471,30 +592,31 @@ __device__ void huffman_cta(Workspace* ws, int which, uint32_t* smem) {
     }
     __syncthreads();
     for (;;) {
-      if (tid == 0) {
+      if (tid < 32) {
         const uint32_t lh = s_state[0], ih = s_state[1], it = s_state[2];
         if ((K - lh) + (it - ih) <= 1u) {
-          s_state[7] = 1u;
+          if (tid == 0) s_state[7] = 1u;
         } else {
-          unsigned long long c4[4];
-          int n4 = 0;
-          if (lh < K) c4[n4++] = leaves[lh];
-          if (lh + 1 < K) c4[n4++] = leaves[lh + 1];
-          if (ih < it) c4[n4++] = nodes[ih];
-          if (ih + 1 < it) c4[n4++] = nodes[ih + 1];
-          unsigned long long a0 = ~0ull, a1 = ~0ull;
-          for (int i = 0; i < n4; i++) {
-            if (c4[i] < a0) { a1 = a0; a0 = c4[i]; }
-            else if (c4[i] < a1) a1 = c4[i];
-          }
+          unsigned long long c4[4] = {~0ull, ~0ull, ~0ull, ~0ull};
+          if (lh < K) c4[0] = leaves[lh];
+          if (lh + 1 < K) c4[1] = leaves[lh + 1];
+          if (ih < it) c4[2] = nodes[ih];
+          if (ih + 1 < it) c4[3] = nodes[ih + 1];
+          const unsigned long long m01 = min(c4[0], c4[1]), x01 = max(c4[0], c4[1]);
+          const unsigned long long m23 = min(c4[2], c4[3]), x23 = max(c4[2], c4[3]);
+          const unsigned long long a0 = min(m01, m23);
+          const unsigned long long a1 = m01 < m23 ? min(x01, m23) : min(x23, m01);
           const unsigned long long T = a0 + a1;
-          const uint32_t ml = count_below(leaves + lh, K - lh, T);
-          const uint32_t mi = count_below(nodes + ih, it - ih, T);
+          const uint32_t ml = warp_count_below(leaves + lh, K - lh, T);
+          const uint32_t mi = warp_count_below(nodes + ih, it - ih, T);
           const uint32_t np = (ml + mi) >> 1;
-          s_state[3] = ml;
-          s_state[4] = mi;
-          s_state[5] = merge_split(leaves + lh, ml, nodes + ih, mi, 2u * np);
-          s_state[6] = np;
+          const uint32_t cl = warp_merge_split(leaves + lh, ml, nodes + ih, mi, 2u * np);
+          if (tid == 0) {
+            s_state[3] = ml;
+            s_state[4] = mi;
+            s_state[5] = cl;
+            s_state[6] = np;
+          }
         }
       }
       __syncthreads();
@@ -503,17 +625,21 @@ __device__ void huffman_cta(Workspace* ws, int which, uint32_t* smem) {
       const uint32_t ml = s_state[3], mi = s_state[4], np = s_state[6];
       const uint32_t* A = leaves + lh;
       const uint32_t* B = nodes + ih;
-      for (uint32_t j = tid; j < np; j += kStatThreads) {
-        uint32_t i = merge_split(A, ml, B, mi, 2u * j);
-        uint32_t k = 2u * j - i;
-        uint32_t e[2];
-        for (int t = 0; t < 2; t++) {
-          if (i < ml && (k >= mi || A[i] <= B[k])) e[t] = A[i++];
-          else e[t] = B[k++];
+      // each thread pairs a contiguous run of the merged order
+      const uint32_t per_t = (np + kHuffThreads - 1) / kHuffThreads;
+      const uint32_t j0 = (uint32_t)tid * per_t;
+      const uint32_t j1 = min(np, j0 + per_t);
+      if (j0 < j1) {
+        uint32_t i = merge_split(A, ml, B, mi, 2u * j0);
+        uint32_t k = 2u * j0 - i;
+        for (uint32_t j = j0; j < j1; j++) {
+          uint32_t e0, e1;
+          if (i < ml && (k >= mi || A[i] <= B[k])) e0 = A[i++]; else e0 = B[k++];
+          if (i < ml && (k >= mi || A[i] <= B[k])) e1 = A[i++]; else e1 = B[k++];
+          const uint32_t s = e0 + e1;
+          nodes[it + j] = s;
+          cost += s;
         }
-        const uint32_t s = e[0] + e[1];
-        nodes[it + j] = s;
-        cost += s;
       }
       __syncthreads();
       if (tid == 0) {
@@ -528,7 +654,7 @@ __device__ void huffman_cta(Workspace* ws, int which, uint32_t* smem) {
   if ((tid & 31) == 0) s_red[tid >> 5] = cost;
   __syncthreads();
   if (tid < 32) {
-    unsigned long long c = warp_sum(s_red[tid]);
+    const unsigned long long c = warp_sum(s_red[tid]);
     if (tid == 0) {
       ws->huff[which].ns = ns;
       ws->huff[which].cost = c;
@@ -537,43 +663,28 @@ __device__ void huffman_cta(Workspace* ws, int which, uint32_t* smem) {
   }
 }
 
-__device__ void entropy_cta(Workspace* ws, int which, int slice) {
-  __shared__ double part[kStatThreads / 32];
-  uint32_t h = ws->hist[which][slice * kStatThreads + threadIdx.x];
-  double v = h ? (double)h * log2((double)h) : 0.0;
-  v = warp_sum(v);
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double t = warp_sum(part[threadIdx.x]);
-    if (threadIdx.x == 0) ws->ent_part[which][slice] = t;
-  }
+cudaError_t launch_code_prep(Workspace* ws, int which_mask, cudaStream_t s) {
+  const int nh = (which_mask == 3) ? 2 : 1;
+  k_code_prep<<<nh * kEntropyCtas, kPrepThreads, 0, s>>>(ws, which_mask);
+  return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(kStatThreads) k_code_stats(Workspace* ws, int which_mask) {
-  extern __shared__ uint32_t s_dyn[];
-  if (ws->sc.status != RD_OK || ws->sc.constant) return;
+cudaError_t launch_huffman(Workspace* ws, int which_mask, cudaStream_t s) {
+  const int smem = 2 * kHuffSmemKeys * (int)sizeof(uint32_t);
   const int nh = (which_mask == 3) ? 2 : 1;
-  const int first = (which_mask & 1) ? 0 : 1;
-  const int b = blockIdx.x;
-  if (b < nh) {
-    huffman_cta(ws, first + b, s_dyn);
-  } else {
-    const int e = b - nh;
-    entropy_cta(ws, first + e / kEntropyCtas, e % kEntropyCtas);
-  }
+  k_huffman<<<nh, kHuffThreads, smem, s>>>(ws, (which_mask & 1) ? 0 : 1);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_code_stats(Workspace* ws, int which_mask, cudaStream_t s) {
-  const int smem = 2 * kHuffSmemKeys * (int)sizeof(uint32_t);
-  const int nh = (which_mask == 3) ? 2 : 1;
-  k_code_stats<<<nh * (1 + kEntropyCtas), kStatThreads, smem, s>>>(ws, which_mask);
-  return cudaGetLastError();
+  cudaError_t e = launch_code_prep(ws, which_mask, s);
+  if (e == cudaSuccess) e = launch_huffman(ws, which_mask, s);
+  return e;
 }
 
 cudaError_t prepare_code_stats() {
   const int smem = 2 * kHuffSmemKeys * (int)sizeof(uint32_t);
-  return cudaFuncSetAttribute(k_code_stats, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return cudaFuncSetAttribute(k_huffman, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 // ---------------------------------------------------------------------------

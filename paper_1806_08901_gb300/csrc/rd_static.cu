@@ -27,9 +27,9 @@ using namespace rdk;
 
 namespace {
 
-// Stated maximum of the fixed scratch: 1.75 MiB per device, held for the
+// Stated maximum of the fixed scratch: 2.25 MiB per device, held for the
 // life of the process by every GPU that loads the library.
-constexpr size_t kStaticScratchBytes = 1835008;
+constexpr size_t kStaticScratchBytes = 2359296;
 static_assert(sizeof(Workspace) <= kStaticScratchBytes, "workspace exceeds the static scratch");
 
 static __device__ __align__(256) unsigned char g_select_scratch[kStaticScratchBytes];

@@ -252,17 +252,21 @@ __global__ void __launch_bounds__(MarchCfg<TX, TY, R, PZ, NST>::kThreads)
       blockIdx.x < g.ntiles ? (g.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const long long J = mytiles * G;
 
-  auto item_coords = [&](long long j, int& x0, int& y0, int& zc0, int& zc1, int& gi) {
-    const long long lt = j / G;
-    gi = (int)(j % G);
-    const long long t = blockIdx.x + lt * gridDim.x;
-    const int itx = (int)(t % g.tilesX);
-    const int ity = (int)((t / g.tilesX) % g.tilesY);
-    const int icz = (int)(t / ((long long)g.tilesX * g.tilesY));
+  // tile of the CTA's lt-th assignment (32-bit: fields hold < 2^31 points)
+  auto tile_coords = [&](int lt, int& x0, int& y0, int& zc0, int& zc1) {
+    const int t = (int)blockIdx.x + lt * (int)gridDim.x;
+    const int itx = t % g.tilesX;
+    const int rest = t / g.tilesX;
+    const int ity = rest % g.tilesY;
+    const int icz = rest / g.tilesY;
     x0 = itx * TX;
     y0 = ity * TY;
     zc0 = icz * g.ZC;
     zc1 = min(zc0 + g.ZC, g.Z);
+  };
+  auto item_coords = [&](long long j, int& x0, int& y0, int& zc0, int& zc1, int& gi) {
+    gi = (int)(j % G);
+    tile_coords((int)(j / G), x0, y0, zc0, zc1);
   };
   auto issue = [&](long long j) {
     int x0, y0, zc0, zc1, gi;
@@ -295,6 +299,8 @@ __global__ void __launch_bounds__(MarchCfg<TX, TY, R, PZ, NST>::kThreads)
   int zmod = 0;  // (z >> 2) mod sZ of the current plane
 
   long long j = 0;
+  int gi = 0, lt = 0;  // step within the tile, tile ordinal: advanced incrementally
+  int x0 = 0, y0 = 0, zc0 = 0, zc1 = 0;
   for (; j < J; j++) {
     const int st = (int)(j % NST);
     const uint32_t parity = (uint32_t)((j / NST) & 1);
@@ -304,9 +310,8 @@ __global__ void __launch_bounds__(MarchCfg<TX, TY, R, PZ, NST>::kThreads)
     }
     __syncthreads();
     if (s_abort) break;
-    int x0, y0, zc0, zc1, gi;
-    item_coords(j, x0, y0, zc0, zc1, gi);
     if (gi == 0) {
+      tile_coords(lt, x0, y0, zc0, zc1);
       const int x = x0 + tx;
       xin = x < g.X;
       xsamp = ((x >> 2) % g.sX) == 0;
@@ -338,6 +343,10 @@ __global__ void __launch_bounds__(MarchCfg<TX, TY, R, PZ, NST>::kThreads)
     if (tid == 0 && j + NST < J) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue(j + NST);
+    }
+    if (++gi == G) {
+      gi = 0;
+      lt++;
     }
   }
   if (s_abort && tid == 0) {

@@ -309,7 +309,7 @@ def test_profiling_across_graph_capture_and_replay(R, ctx):
         assert ctx.evaluate(xd, p) == base
     st = ctx.kernel_stats()
     assert st["zfp_pass"][1] == 5 and st["zfp_pass"][0] > 0
-    assert st["sz_pass"][1] == 5 and st["code_stats"][1] == 5
+    assert st["sz_pass"][1] == 5 and st["huffman"][1] == 5 and st["code_prep"][1] == 5
     ctx.set_profiling(False)
     y = torch.ones(1000, device="cuda")
     y.add_(1.0)
