@@ -175,15 +175,16 @@ int32_t rd_evaluate(rd_context* ctx, const rd_field* field,
  * framework whose allocator must serve every allocation) or that cannot take
  * the synchronisation an allocation may imply.  It needs no context and
  * calls no cudaMalloc, cudaFree, cudaMallocHost or other allocating routine:
- * its scratch is one fixed 2.25 MiB array inside the library, held by every
+ * its scratch is one fixed 3.25 MiB array inside the library, held by every
  * GPU that loads the library until the process exits.
  *  - field: DEVICE memory only (location RD_LOC_HOST is rejected, since a
  *    host field would need a staging buffer), at most 2^31-1 points; larger
  *    or malformed shapes return RD_ERR_INVALID_ARG.  The scratch does not
  *    grow with the field, so no other size limit applies.
  *  - The first call on a device (the current device) resolves the array's
- *    device address and sizes the grids; make that first call before any
- *    stream capture.
+ *    device address, sizes the grids and fills a constant table in the
+ *    array (one kernel on the legacy default stream, then a wait for it);
+ *    make that first call before any stream capture.
  *  - Every call shares the array and leaves its contents behind; each call
  *    clears what must start at zero.  Calls that overlap on the GPU (other
  *    streams or host threads) race on the array: serialise them.

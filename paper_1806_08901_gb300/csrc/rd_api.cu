@@ -513,7 +513,8 @@ int32_t rd_context_create(int32_t device, size_t hbm_budget, rd_context** out) {
     return RD_ERR_OOM;
   }
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
-  if (prepare_code_stats() != cudaSuccess || prepare_sz_march() != cudaSuccess) {
+  if (prepare_code_stats() != cudaSuccess || prepare_sz_march() != cudaSuccess ||
+      launch_init_tables(c->ws, 0) != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess) {
     cudaFreeHost(c->out);
     cudaFree(c->ws);
     delete c;

@@ -42,6 +42,7 @@ struct Scalars {
 struct HuffOut {
   unsigned long long ns;    // total count
   unsigned long long cost;  // Huffman-coded bits (sum of internal weights)
+  double plogp;             // sum of h log2 h over the bins
   uint32_t nsym;            // nonzero symbols
   uint32_t pad;
 };
@@ -54,7 +55,10 @@ struct Workspace {
   double zfp_sse[kMaxGrid];           // per-CTA partial sums (fixed order)
   double sz_sse[kMaxGrid];
   uint32_t count_of[2][kNsym];        // multiplicity of each count value below 2^16
+  uint32_t present[2][kNsym / 32];    // bitmap of the count values present
   uint32_t nbig[2];                   // counts of 2^16 or more
+  uint32_t distinct[2][kNsym];        // sorted distinct counts when there are many
+  double xlogx[kNsym];                // v log2 v, filled once per workspace
   uint32_t sort_scratch[2][kNsym];    // Huffman leaves when K is large
   uint32_t node_scratch[2][kNsym];    // counts >= 2^16, then Huffman internal nodes when K is large
   rd_result res;
@@ -120,6 +124,8 @@ enum PassFlags : int {
 enum DeltaMode { DELTA_FROM_MSE = 0, DELTA_EXPLICIT = 1, DELTA_FROM_EB_SZ = 2 };
 
 // ---- launchers (each returns the cudaError_t of the launch) ----
+// constant tables of a new workspace (once, before its first call)
+cudaError_t launch_init_tables(Workspace* ws, cudaStream_t s);
 cudaError_t launch_reset(Workspace* ws, cudaStream_t s);
 cudaError_t launch_range(const FieldDev& f, Workspace* ws, int ctas, cudaStream_t s);
 cudaError_t launch_prepare(const ParamsDev& p, Workspace* ws, cudaStream_t s);

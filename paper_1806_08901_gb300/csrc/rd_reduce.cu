@@ -19,6 +19,8 @@ __global__ void k_reset(Workspace* ws) {
   for (int i = tid; i < 2 * kNsym; i += nth) h[i] = 0u;
   uint32_t* cc = &ws->count_of[0][0];
   for (int i = tid; i < 2 * kNsym; i += nth) cc[i] = 0u;
+  uint32_t* pr = &ws->present[0][0];
+  for (int i = tid; i < 2 * (kNsym / 32); i += nth) pr[i] = 0u;
   unsigned long long* lo = ws->sc.mse_lo;
   unsigned long long* hi = ws->sc.mse_hi;
   for (int i = tid; i < kMseBins; i += nth) {
@@ -46,6 +48,7 @@ __global__ void k_reset(Workspace* ws) {
       ws->huff[w].ns = 0ull;
       ws->huff[w].cost = 0ull;
       ws->huff[w].nsym = 0u;
+      ws->huff[w].plogp = 0.0;
     }
     unsigned char* r = reinterpret_cast<unsigned char*>(&ws->res);
     for (size_t i = 0; i < sizeof(rd_result); i++) r[i] = 0;
@@ -184,104 +187,137 @@ cudaError_t launch_prepare(const ParamsDev& p, Workspace* ws, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 constexpr int kLimbs = 12;  // 768 bits
 
-__device__ void limbs_add(unsigned long long* a, unsigned long long v, int off) {
-  int w = off >> 6, sh = off & 63;
-  unsigned long long lo = v << sh;
-  unsigned long long hi = sh ? (v >> (64 - sh)) : 0ull;
-  unsigned long long carry = 0ull;
-  for (int i = w; i < kLimbs; i++) {
-    unsigned long long add = (i == w) ? lo : (i == w + 1) ? hi : 0ull;
-    unsigned long long t = a[i] + add;
-    unsigned long long c1 = t < add;
-    unsigned long long t2 = t + carry;
-    unsigned long long c2 = t2 < carry;
-    a[i] = t2;
-    carry = c1 + c2;
-    if (i > w + 1 && carry == 0ull) break;
-  }
-}
-
 // Round the limb integer times 2^-312 to the nearest double (ties to even):
-// the 53 bits below the leading one, a round bit and a sticky bit.
-__device__ double limbs_to_double(const unsigned long long* a) {
-  int ti = kLimbs - 1;
-  while (ti >= 0 && a[ti] == 0ull) ti--;
+// the 53 bits below the leading one, a round bit and a sticky bit.  Every
+// limb index is a compile-time constant, so the limbs stay in registers.
+__device__ __forceinline__ double limbs_to_double(const unsigned long long (&a)[kLimbs]) {
+  // rolling window (w2, w1, w0) = limbs i, i-1, i-2 and the OR of the
+  // limbs below it, captured at the highest nonzero limb
+  unsigned long long w2 = 0ull, w1 = 0ull, w0 = 0ull;
+  bool bl = false;
+  unsigned long long h = 0ull, m = 0ull, l = 0ull;
+  bool below = false;
+  int ti = -1;
+#pragma unroll
+  for (int i = 0; i < kLimbs; i++) {
+    bl = bl || (w0 != 0ull);
+    w0 = w1;
+    w1 = w2;
+    w2 = a[i];
+    if (w2) {
+      h = w2;
+      m = w1;
+      l = w0;
+      below = bl;
+      ti = i;
+    }
+  }
   if (ti < 0) return 0.0;
-  const int top = ti * 64 + 63 - __clzll((long long)a[ti]);
-  if (top <= 52) return ldexp((double)a[0], -312);  // exact
-  const int shift = top - 52;
-  const int w = shift >> 6, o = shift & 63;
-  unsigned long long m = a[w] >> o;
-  if (o && w + 1 < kLimbs) m |= a[w + 1] << (64 - o);
-  m &= (1ull << 53) - 1ull;
-  const int rb = shift - 1;
-  const int round = (int)((a[rb >> 6] >> (rb & 63)) & 1ull);
-  bool sticky = (a[rb >> 6] & ((1ull << (rb & 63)) - 1ull)) != 0ull;
-  for (int i = 0; i < (rb >> 6) && !sticky; i++) sticky = a[i] != 0ull;
-  if (round && (sticky || (m & 1ull))) m += 1ull;
-  return ldexp((double)m, shift - 312);
+  // normalise the 192-bit window h:m:l so that bit 63 of h is the leading one
+  const int lz = __clzll((long long)h);
+  if (lz) {
+    h = (h << lz) | (m >> (64 - lz));
+    m = (m << lz) | (l >> (64 - lz));
+    l <<= lz;
+  }
+  unsigned long long mant = h >> 11;  // 53 bits
+  const bool round = (h >> 10) & 1ull;
+  const bool sticky = (h & 0x3ffull) || m || l || below;
+  if (round && (sticky || (mant & 1ull))) mant += 1ull;  // 2^53 stays exact
+  const int lead = ti * 64 + 63 - lz;  // bit index of the leading one
+  return ldexp((double)mant, lead - 52 - 312);
 }
 
-// Launched with one warp: the lanes sum disjoint exponent bins into their own
-// limb integers, a butterfly adds the 32 integers (exact, so the order does
-// not matter), and lane 0 finishes.
+// Launched with one warp.  Bin i holds a 128-bit sum at bit offset 2i, so
+// the bins of lane l (i = l + 32k) all sit at shift 2l within limb k: each
+// lane adds its bins as one multi-limb integer, shifts it by 2l, and a
+// butterfly adds the 32 integers (exact, so the order does not matter).
+// The logarithms of the PSNRs run in separate lanes.
 __global__ void k_delta(ParamsDev p, Workspace* ws, int mode, double arg, int need_quant,
                         int need_gt, unsigned long long ncoeff, unsigned long long npoints) {
   Scalars& s = ws->sc;
   if (s.status != RD_OK || s.constant) return;
   rd_result& r = ws->res;
   const int lane = threadIdx.x;
-  unsigned long long acc[kLimbs];
+  double delta, mse_sp = 0.0;
+  bool clamped = false;
   if (mode == DELTA_FROM_MSE) {
+    unsigned long long acc[kLimbs];
+    unsigned long long lo[9], hi[9];
 #pragma unroll
-    for (int i = 0; i < kLimbs; i++) acc[i] = 0ull;
-    for (int i = lane; i < kMseBins; i += 32) {
-      const unsigned long long lo = s.mse_lo[i], hi = s.mse_hi[i];
-      if (lo) limbs_add(acc, lo, 2 * i);
-      if (hi) limbs_add(acc, hi, 2 * i + 64);
+    for (int k = 0; k < 9; k++) {
+      const int i = lane + 32 * k;
+      lo[k] = i < kMseBins ? s.mse_lo[i] : 0ull;
+      hi[k] = i < kMseBins ? s.mse_hi[i] : 0ull;
+    }
+    unsigned long long carry = 0ull;
+#pragma unroll
+    for (int k = 0; k < 10; k++) {
+      const unsigned long long a0 = k < 9 ? lo[k] : 0ull;
+      const unsigned long long a1 = k >= 1 ? hi[k - 1] : 0ull;
+      const unsigned long long t = a0 + a1;
+      const unsigned long long c1 = t < a0;
+      const unsigned long long u = t + carry;
+      const unsigned long long c2 = u < carry;
+      acc[k] = u;
+      carry = c1 + c2;
+    }
+    acc[10] = carry;
+    acc[11] = 0ull;
+    const int sh = 2 * lane;
+    if (sh) {
+#pragma unroll
+      for (int j = kLimbs - 1; j > 0; j--) acc[j] = (acc[j] << sh) | (acc[j - 1] >> (64 - sh));
+      acc[0] <<= sh;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      unsigned long long carry = 0ull;
+      unsigned long long c = 0ull;
 #pragma unroll
       for (int j = 0; j < kLimbs; j++) {
         const unsigned long long t = __shfl_xor_sync(0xffffffffu, acc[j], o);
         const unsigned long long u = acc[j] + t;
         const unsigned long long c1 = u < t;
-        const unsigned long long v = u + carry;
-        const unsigned long long c2 = v < carry;
+        const unsigned long long v = u + c;
+        const unsigned long long c2 = v < c;
         acc[j] = v;
-        carry = c1 + c2;
+        c = c1 + c2;
       }
     }
-  }
-  if (lane != 0) return;
-  double delta;
-  if (mode == DELTA_FROM_MSE) {
-    double num = limbs_to_double(acc);
-    s.mse_sp = num / (double)ncoeff;
-    r.mse_sp = s.mse_sp;
-    r.zfp_s2 = s.s2;
-    r.br_zfp = (double)s.s2 / (2.0 * (double)npoints);
-    r.psnr_zfp = s.mse_sp > 0.0 ? 20.0 * log10(s.vr) - 10.0 * log10(s.mse_sp) : INFINITY;
-    if (s.mse_sp == 0.0) {
+    mse_sp = limbs_to_double(acc) / (double)ncoeff;
+    if (mse_sp == 0.0) {
       delta = 2.0 * s.eb_abs;
-      s.flags |= RD_F_MSE_ZERO;
     } else {
-      delta = sqrt(12.0 * s.mse_sp);
-      if (delta > 2.0 * s.eb_abs) {
-        delta = 2.0 * s.eb_abs;
-        s.flags |= RD_F_DELTA_CLAMPED;
-      }
+      delta = sqrt(12.0 * mse_sp);
+      clamped = delta > 2.0 * s.eb_abs;
+      if (clamped) delta = 2.0 * s.eb_abs;
     }
   } else if (mode == DELTA_EXPLICIT) {
     delta = arg > 0.0 ? arg : 2.0 * s.eb_abs;
   } else {
     delta = 2.0 * arg;
   }
+  // lane 0: log10 VR, lane 1: log10 MSE_sp, lane 2: log10 (VR / delta),
+  // lane 3: log10 12
+  const double larg = lane == 0 ? s.vr : lane == 1 ? mse_sp : lane == 2 ? s.vr / delta : 12.0;
+  const double lg = log10(larg);
+  const double l_vr = __shfl_sync(0xffffffffu, lg, 0);
+  const double l_mse = __shfl_sync(0xffffffffu, lg, 1);
+  const double l_vd = __shfl_sync(0xffffffffu, lg, 2);
+  const double l_12 = __shfl_sync(0xffffffffu, lg, 3);
+  if (lane != 0) return;
+  if (mode == DELTA_FROM_MSE) {
+    s.mse_sp = mse_sp;
+    r.mse_sp = mse_sp;
+    r.zfp_s2 = s.s2;
+    r.br_zfp = (double)s.s2 / (2.0 * (double)npoints);
+    r.psnr_zfp = mse_sp > 0.0 ? 20.0 * l_vr - 10.0 * l_mse : INFINITY;
+    if (mse_sp == 0.0) s.flags |= RD_F_MSE_ZERO;
+    if (clamped) s.flags |= RD_F_DELTA_CLAMPED;
+  }
   s.delta = delta;
   r.delta = delta;
-  r.psnr_sz = 20.0 * log10(s.vr / delta) + 10.0 * log10(12.0);
+  r.psnr_sz = 20.0 * l_vd + 10.0 * l_12;
   if (!need_quant) return;
   // float quantiser: w = float(delta), 1/w, and tau = the largest float not
   // above (delta / 2)(1 - 2^-23), so that a float |x - xhat| <= tau proves
@@ -417,10 +453,24 @@ __device__ uint32_t warp_merge_split(const uint32_t* A, uint32_t na, const uint3
 }
 
 // ---------------------------------------------------------------------------
-// Prep (many CTAs, 1024 bins each): the slice's sum of h log2 h for the
-// entropy; the multiplicity of every count value below 2^16 (a counting sort
-// of the counts, lanes with equal counts merged into one atomic); counts of
-// 2^16 or more (at most N / 2^16 of them) appended to a list.
+// Table of v log2 v for the entropy (v < 2^16), filled once per workspace.
+// ---------------------------------------------------------------------------
+__global__ void k_init_xlogx(Workspace* ws) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < kNsym) ws->xlogx[v] = v > 1 ? (double)v * log2((double)v) : 0.0;
+}
+
+cudaError_t launch_init_tables(Workspace* ws, cudaStream_t s) {
+  k_init_xlogx<<<kNsym / 256, 256, 0, s>>>(ws);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Prep (kEntropyCtas CTAs per histogram, 1024 bins each, integer work only):
+// the multiplicity of every count value below 2^16 (a counting sort of the
+// counts; lanes holding equal counts merge into one atomic), a bitmap of the
+// count values present, and the counts of 2^16 or more (at most N / 2^16 of
+// them) appended to a list, with their share c log2 c of the entropy sum.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kPrepThreads) k_code_prep(Workspace* ws, int which_mask) {
   __shared__ double part[kPrepThreads / 32];
@@ -431,25 +481,31 @@ __global__ void __launch_bounds__(kPrepThreads) k_code_prep(Workspace* ws, int w
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   uint32_t* cc = ws->count_of[which];
+  uint32_t* present = ws->present[which];
   uint32_t* big = ws->node_scratch[which];
   double v = 0.0;
 #pragma unroll
   for (int k = 0; k < 1024 / kPrepThreads; k++) {
     const uint32_t c = ws->hist[which][slice * 1024 + k * kPrepThreads + threadIdx.x];
-    if (c) v += (double)c * log2((double)c);
     const bool small = c != 0u && c < (uint32_t)kNsym;
     const bool large = c >= (uint32_t)kNsym;
     const unsigned ms = __ballot_sync(0xffffffffu, small);
     const unsigned mb = __ballot_sync(0xffffffffu, large);
     if (small) {
       const unsigned same = __match_any_sync(ms, c);
-      if (lane == __ffs(same) - 1) atomicAdd(&cc[c], (uint32_t)__popc(same));
+      if (lane == __ffs(same) - 1) {
+        if (atomicAdd(&cc[c], (uint32_t)__popc(same)) == 0u)
+          atomicOr(&present[c >> 5], 1u << (c & 31u));
+      }
     }
     if (mb) {
       uint32_t base = 0u;
       if (lane == __ffs(mb) - 1) base = atomicAdd(&ws->nbig[which], (uint32_t)__popc(mb));
       base = __shfl_sync(0xffffffffu, base, __ffs(mb) - 1);
-      if (large) big[base + __popc(mb & lt_mask)] = c;
+      if (large) {
+        big[base + __popc(mb & lt_mask)] = c;
+        v += (double)c * log2((double)c);
+      }
     }
   }
   v = warp_sum(v);
@@ -461,88 +517,177 @@ __global__ void __launch_bounds__(kPrepThreads) k_code_prep(Workspace* ws, int w
   }
 }
 
+// Block-wide scans and sums for kHuffThreads threads (32 warps); s_w holds
+// 32 words of scratch.  Each ends with a barrier, so s_w can be reused.
+__device__ uint32_t block_excl_sum(uint32_t v, uint32_t* s_w, uint32_t* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t inc = v;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, inc, off);
+    if (lane >= off) inc += t;
+  }
+  if (lane == 31) s_w[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t w = s_w[lane];
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, w, off);
+      if (lane >= off) w += t;
+    }
+    s_w[lane] = w;
+  }
+  __syncthreads();
+  const uint32_t base = wid ? s_w[wid - 1] : 0u;
+  *total = s_w[31];
+  __syncthreads();
+  return base + inc - v;
+}
+
+// exclusive running maximum
+__device__ uint32_t block_excl_max(uint32_t v, uint32_t* s_w) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t inc = v;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, inc, off);
+    if (lane >= off) inc = max(inc, t);
+  }
+  if (lane == 31) s_w[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t w = s_w[lane];
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, w, off);
+      if (lane >= off) w = max(w, t);
+    }
+    s_w[lane] = w;
+  }
+  __syncthreads();
+  uint32_t ex = __shfl_up_sync(0xffffffffu, inc, 1);
+  if (lane == 0) ex = 0u;
+  if (wid) ex = max(ex, s_w[wid - 1]);
+  __syncthreads();
+  return ex;
+}
+
+// fixed-order block sums, valid in every thread
+__device__ unsigned long long block_sum_u64(unsigned long long v, unsigned long long* s_w) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
+  __syncthreads();
+  const unsigned long long t = warp_sum(s_w[threadIdx.x & 31]);
+  __syncthreads();
+  return t;
+}
+
+__device__ double block_sum_f64(double v, double* s_w) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
+  __syncthreads();
+  const double t = warp_sum(s_w[threadIdx.x & 31]);
+  __syncthreads();
+  return t;
+}
+
 // ---------------------------------------------------------------------------
-// Huffman cost (one CTA per histogram).  The ascending leaf array is the
-// counting-sorted small counts followed by the sorted large ones.  Then the
-// two-queue method in phases: with a0 <= a1 the two smallest remaining
-// items, every item below T = a0 + a1 is consumed before any new node (new
-// nodes are >= T), so all of them are paired at once in merged order (ties:
-// leaves first); the new nodes, non-decreasing as in the sequential method,
-// are appended to the internal queue.  Cost = sum of internal-node weights.
+// Huffman cost and entropy sum (one CTA per histogram).
+//  1. The bitmap of present count values gives each its rank d in ascending
+//     order; the D distinct values and their multiplicities (packed as
+//     v << 16 | (m - 1)) are gathered in that order.  The entropy sum is
+//     sum m v log2 v over them, from the table, plus the large counts' share.
+//  2. The ascending leaf array: the first position of every distinct value
+//     is marked with the value and a running maximum over positions fills
+//     each run; the large counts follow, sorted by a bitonic network.
+//  3. The phased two-queue merge.  Every warp computes the phase threshold
+//     and split points itself from the shared arrays, so one barrier per
+//     phase suffices: in a phase nodes are written only above the queue
+//     tail, which no warp reads until the barrier.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kHuffThreads) k_huffman(Workspace* ws, int which0) {
   extern __shared__ uint32_t s_dyn[];
-  __shared__ uint32_t s_pre[kHuffThreads];   // per-thread small-count totals, scanned
-  __shared__ unsigned long long s_red[kHuffThreads / 32];
-  __shared__ uint32_t s_wmax[32];
-  __shared__ uint32_t s_state[8];
+  __shared__ uint32_t s_w[32];
+  __shared__ unsigned long long s_w64[32];
+  __shared__ double s_wd[32];
   if (ws->sc.status != RD_OK || ws->sc.constant) return;
   const int which = which0 + blockIdx.x;
   const int tid = threadIdx.x;
   const uint32_t* cc = ws->count_of[which];
-  constexpr int vper = kNsym / kHuffThreads;  // 64 count values per thread
 
-  // multiplicities of this thread's values and their contribution to N_s
-  uint32_t tot = 0u;
-  unsigned long long nsum = 0ull;
+  // 1. distinct values in ascending order
+  const uint2 pw = reinterpret_cast<const uint2*>(ws->present[which])[tid];
+  uint32_t D;
+  const uint32_t dbase = block_excl_sum(__popc(pw.x) + __popc(pw.y), s_w, &D);
+  uint32_t* dv = (D <= (uint32_t)kHuffSmemKeys) ? s_dyn + kHuffSmemKeys : ws->distinct[which];
   {
-    const uint4* c4 = reinterpret_cast<const uint4*>(cc + tid * vper);
+    uint32_t d = dbase;
+    for (uint32_t w = pw.x; w; w &= w - 1u) dv[d++] = 64u * tid + (uint32_t)(__ffs(w) - 1);
+    for (uint32_t w = pw.y; w; w &= w - 1u) dv[d++] = 64u * tid + 32u + (uint32_t)(__ffs(w) - 1);
+  }
+  __syncthreads();
+  uint32_t msum = 0u;
+  unsigned long long nsum = 0ull;
+  double ent = 0.0;
+  for (uint32_t d0 = tid; d0 < D; d0 += 4u * kHuffThreads) {
+    uint32_t vv[4], mm[4];
+    double xl[4];
 #pragma unroll
-    for (int k = 0; k < vper / 4; k++) {
-      const uint4 q = c4[k];
-      const uint32_t v0 = (uint32_t)(tid * vper + 4 * k);
-      tot += q.x + q.y + q.z + q.w;
-      nsum += (unsigned long long)q.x * v0 + (unsigned long long)q.y * (v0 + 1) +
-              (unsigned long long)q.z * (v0 + 2) + (unsigned long long)q.w * (v0 + 3);
+    for (int u = 0; u < 4; u++) {
+      const uint32_t d = d0 + (uint32_t)u * kHuffThreads;
+      vv[u] = d < D ? dv[d] : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const uint32_t d = d0 + (uint32_t)u * kHuffThreads;
+      mm[u] = d < D ? cc[vv[u]] : 0u;
+      xl[u] = d < D ? ws->xlogx[vv[u]] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const uint32_t d = d0 + (uint32_t)u * kHuffThreads;
+      if (d < D) {
+        dv[d] = (vv[u] << 16) | (mm[u] - 1u);
+        msum += mm[u];
+        nsum += (unsigned long long)mm[u] * vv[u];
+        ent += (double)mm[u] * xl[u];
+      }
     }
   }
   const uint32_t nbig = ws->nbig[which];
   const uint32_t* big = ws->node_scratch[which];
   for (uint32_t i = tid; i < nbig; i += kHuffThreads) nsum += big[i];
-  s_pre[tid] = tot;
-  nsum = warp_sum(nsum);
-  if ((tid & 31) == 0) s_red[tid >> 5] = nsum;
-  __syncthreads();
-  for (int off = 1; off < kHuffThreads; off <<= 1) {
-    const uint32_t t = tid >= off ? s_pre[tid - off] : 0u;
-    __syncthreads();
-    s_pre[tid] += t;
-    __syncthreads();
-  }
-  const uint32_t nsmall = s_pre[kHuffThreads - 1];
+  if (tid < kEntropyCtas) ent += ws->ent_part[which][tid];
+  uint32_t nsmall;
+  (void)block_excl_sum(msum, s_w, &nsmall);
+  const unsigned long long ns = block_sum_u64(nsum, s_w64);
+  const double plogp = block_sum_f64(ent, s_wd);
   const uint32_t K = nsmall + nbig;
-  unsigned long long ns = 0ull;
-  if (tid < 32) ns = warp_sum(s_red[tid]);
 
+  // 2. leaves
   uint32_t* leaves;
   uint32_t* nodes;
   if (K <= (uint32_t)kHuffSmemKeys) {
     leaves = s_dyn;
-    nodes = s_dyn + kHuffSmemKeys;
+    nodes = s_dyn + kHuffSmemKeys;  // the distinct list lives here until the phases
   } else {
     leaves = ws->sort_scratch[which];
     nodes = ws->node_scratch[which];  // free once the large counts are copied
   }
-  // expansion of the small counts in ascending order: the first position of
-  // every present value is marked with the value, then a running maximum
-  // over positions fills each run (values ascend with position, 0 is absent)
+  const uint32_t Cd = (D + kHuffThreads - 1) / kHuffThreads;
+  const uint32_t e0 = min(D, (uint32_t)tid * Cd), e1 = min(D, e0 + Cd);
+  uint32_t mloc = 0u;
+  for (uint32_t d = e0; d < e1; d++) mloc += (dv[d] & 0xffffu) + 1u;
+  uint32_t tot;
+  uint32_t start = block_excl_sum(mloc, s_w, &tot);
   for (uint32_t o = tid; o < nsmall; o += kHuffThreads) leaves[o] = 0u;
   __syncthreads();
-  {
-    uint32_t o = s_pre[tid] - tot;
-    const uint4* c4 = reinterpret_cast<const uint4*>(cc + tid * vper);
-#pragma unroll 4
-    for (int k = 0; k < vper / 4; k++) {
-      const uint4 q = c4[k];
-      const uint32_t v0 = (uint32_t)(tid * vper + 4 * k);
-      if (q.x) { leaves[o] = v0; o += q.x; }
-      if (q.y) { leaves[o] = v0 + 1; o += q.y; }
-      if (q.z) { leaves[o] = v0 + 2; o += q.z; }
-      if (q.w) { leaves[o] = v0 + 3; o += q.w; }
-    }
+  for (uint32_t d = e0; d < e1; d++) {
+    const uint32_t q = dv[d];
+    leaves[start] = q >> 16;
+    start += (q & 0xffffu) + 1u;
   }
-  // the large counts follow (in the global layout they move from the node
-  // scratch to the leaf array)
   for (uint32_t i = tid; i < nbig; i += kHuffThreads) leaves[nsmall + i] = big[i];
   __syncthreads();
   {
@@ -550,29 +695,7 @@ __global__ void __launch_bounds__(kHuffThreads) k_huffman(Workspace* ws, int whi
     const uint32_t o0 = min(nsmall, (uint32_t)tid * C), o1 = min(nsmall, o0 + C);
     uint32_t run = 0u;
     for (uint32_t o = o0; o < o1; o++) run = max(run, leaves[o]);
-    // exclusive running maximum over the threads' chunks
-    const int lane = tid & 31;
-    uint32_t inc = run;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const uint32_t t = __shfl_up_sync(0xffffffffu, inc, off);
-      if (lane >= off) inc = max(inc, t);
-    }
-    if (lane == 31) s_wmax[tid >> 5] = inc;
-    __syncthreads();
-    if (tid < 32) {
-      uint32_t w = s_wmax[tid];
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, w, off);
-        if (tid >= off) w = max(w, t);
-      }
-      s_wmax[tid] = w;
-    }
-    __syncthreads();
-    uint32_t carry = __shfl_up_sync(0xffffffffu, inc, 1);
-    if (lane == 0) carry = 0u;
-    if (tid >= 32) carry = max(carry, s_wmax[(tid >> 5) - 1]);
+    uint32_t carry = block_excl_max(run, s_w);
     for (uint32_t o = o0; o < o1; o++) {
       carry = max(carry, leaves[o]);
       leaves[o] = carry;
@@ -581,48 +704,28 @@ __global__ void __launch_bounds__(kHuffThreads) k_huffman(Workspace* ws, int whi
   __syncthreads();
   bitonic_sort(leaves + nsmall, (int)nbig);
 
+  // 3. phases
   unsigned long long cost = 0ull;
   if (K == 1) {
     cost = (tid == 0) ? ns : 0ull;
   } else if (K > 1) {
-    // s_state: 0 lh, 1 ih, 2 it, 3 ml, 4 mi, 5 cl, 6 np, 7 done
-    if (tid == 0) {
-      s_state[0] = s_state[1] = s_state[2] = 0u;
-      s_state[7] = 0u;
-    }
-    __syncthreads();
+    uint32_t lh = 0u, ih = 0u, it = 0u;  // leaf head, node head, node tail
     for (;;) {
-      if (tid < 32) {
-        const uint32_t lh = s_state[0], ih = s_state[1], it = s_state[2];
-        if ((K - lh) + (it - ih) <= 1u) {
-          if (tid == 0) s_state[7] = 1u;
-        } else {
-          unsigned long long c4[4] = {~0ull, ~0ull, ~0ull, ~0ull};
-          if (lh < K) c4[0] = leaves[lh];
-          if (lh + 1 < K) c4[1] = leaves[lh + 1];
-          if (ih < it) c4[2] = nodes[ih];
-          if (ih + 1 < it) c4[3] = nodes[ih + 1];
-          const unsigned long long m01 = min(c4[0], c4[1]), x01 = max(c4[0], c4[1]);
-          const unsigned long long m23 = min(c4[2], c4[3]), x23 = max(c4[2], c4[3]);
-          const unsigned long long a0 = min(m01, m23);
-          const unsigned long long a1 = m01 < m23 ? min(x01, m23) : min(x23, m01);
-          const unsigned long long T = a0 + a1;
-          const uint32_t ml = warp_count_below(leaves + lh, K - lh, T);
-          const uint32_t mi = warp_count_below(nodes + ih, it - ih, T);
-          const uint32_t np = (ml + mi) >> 1;
-          const uint32_t cl = warp_merge_split(leaves + lh, ml, nodes + ih, mi, 2u * np);
-          if (tid == 0) {
-            s_state[3] = ml;
-            s_state[4] = mi;
-            s_state[5] = cl;
-            s_state[6] = np;
-          }
-        }
-      }
-      __syncthreads();
-      if (s_state[7]) break;
-      const uint32_t lh = s_state[0], ih = s_state[1], it = s_state[2];
-      const uint32_t ml = s_state[3], mi = s_state[4], np = s_state[6];
+      if ((K - lh) + (it - ih) <= 1u) break;
+      unsigned long long c4[4] = {~0ull, ~0ull, ~0ull, ~0ull};
+      if (lh < K) c4[0] = leaves[lh];
+      if (lh + 1 < K) c4[1] = leaves[lh + 1];
+      if (ih < it) c4[2] = nodes[ih];
+      if (ih + 1 < it) c4[3] = nodes[ih + 1];
+      const unsigned long long m01 = min(c4[0], c4[1]), x01 = max(c4[0], c4[1]);
+      const unsigned long long m23 = min(c4[2], c4[3]), x23 = max(c4[2], c4[3]);
+      const unsigned long long a0 = min(m01, m23);
+      const unsigned long long a1 = m01 < m23 ? min(x01, m23) : min(x23, m01);
+      const unsigned long long T = a0 + a1;
+      const uint32_t ml = warp_count_below(leaves + lh, K - lh, T);
+      const uint32_t mi = warp_count_below(nodes + ih, it - ih, T);
+      const uint32_t np = (ml + mi) >> 1;
+      const uint32_t cl = warp_merge_split(leaves + lh, ml, nodes + ih, mi, 2u * np);
       const uint32_t* A = leaves + lh;
       const uint32_t* B = nodes + ih;
       // each thread pairs a contiguous run of the merged order
@@ -633,33 +736,26 @@ __global__ void __launch_bounds__(kHuffThreads) k_huffman(Workspace* ws, int whi
         uint32_t i = merge_split(A, ml, B, mi, 2u * j0);
         uint32_t k = 2u * j0 - i;
         for (uint32_t j = j0; j < j1; j++) {
-          uint32_t e0, e1;
-          if (i < ml && (k >= mi || A[i] <= B[k])) e0 = A[i++]; else e0 = B[k++];
-          if (i < ml && (k >= mi || A[i] <= B[k])) e1 = A[i++]; else e1 = B[k++];
-          const uint32_t s = e0 + e1;
-          nodes[it + j] = s;
-          cost += s;
+          uint32_t e0v, e1v;
+          if (i < ml && (k >= mi || A[i] <= B[k])) e0v = A[i++]; else e0v = B[k++];
+          if (i < ml && (k >= mi || A[i] <= B[k])) e1v = A[i++]; else e1v = B[k++];
+          const uint32_t sum = e0v + e1v;
+          nodes[it + j] = sum;
+          cost += sum;
         }
       }
       __syncthreads();
-      if (tid == 0) {
-        s_state[0] = lh + s_state[5];
-        s_state[1] = ih + (2u * np - s_state[5]);
-        s_state[2] = it + np;
-      }
+      lh += cl;
+      ih += 2u * np - cl;
+      it += np;
     }
   }
-  __syncthreads();
-  cost = warp_sum(cost);
-  if ((tid & 31) == 0) s_red[tid >> 5] = cost;
-  __syncthreads();
-  if (tid < 32) {
-    const unsigned long long c = warp_sum(s_red[tid]);
-    if (tid == 0) {
-      ws->huff[which].ns = ns;
-      ws->huff[which].cost = c;
-      ws->huff[which].nsym = K;
-    }
+  cost = block_sum_u64(cost, s_w64);
+  if (tid == 0) {
+    ws->huff[which].ns = ns;
+    ws->huff[which].cost = cost;
+    ws->huff[which].nsym = K;
+    ws->huff[which].plogp = plogp;
   }
 }
 
@@ -718,13 +814,25 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(ParamsDev p, Workspac
   if (s.status != RD_OK) return;
   rd_result& r = ws->res;
   rd_truth& t = ws->truth;
-  double zsse = 0.0, ssse = 0.0, plogp = 0.0;
+  double zsse = 0.0, ssse = 0.0;
   if (!s.constant) {
     if (passes & P_ZFP_GT) zsse = block_sum_parts(ws->zfp_sse, zfp_parts, red);
     if (passes & P_SZ_GT) ssse = block_sum_parts(ws->sz_sse, sz_parts, red);
-    if (passes & P_SZ_EST) plogp = block_sum_parts(ws->ent_part[0], kEntropyCtas, red);
   }
-  if (threadIdx.x != 0) return;
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  // the logarithms in separate lanes: 0 VR, 1 N_s, 2 ZFP truth MSE, 3 SZ truth MSE
+  const double ns_d = (double)ws->huff[0].ns;
+  const double mse_z = zsse / (double)npoints_all;
+  const double mse_s = ssse / (double)npoints_all;
+  const double larg = lane == 0 ? s.vr : lane == 1 ? ns_d : lane == 2 ? mse_z : mse_s;
+  const double lg2 = log2(larg);
+  const double kLog10of2 = 0.30102999566398119521;
+  const double l_vr = __shfl_sync(0xffffffffu, lg2, 0) * kLog10of2;
+  const double l_ns = __shfl_sync(0xffffffffu, lg2, 1);
+  const double l_mz = __shfl_sync(0xffffffffu, lg2, 2) * kLog10of2;
+  const double l_ms = __shfl_sync(0xffffffffu, lg2, 3) * kLog10of2;
+  if (lane != 0) return;
   if (s.constant) {
     r.flags = s.flags;
     r.psnr_zfp = INFINITY;
@@ -736,11 +844,11 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(ParamsDev p, Workspac
     t.best_gt = 1;
     return;
   }
-  double lvr = 20.0 * log10(s.vr);
+  const double lvr = 20.0 * l_vr;
   if (passes & P_SZ_EST) {
     const HuffOut& hh = ws->huff[0];
     double ns = (double)hh.ns;
-    double H = log2(ns) - plogp / ns;
+    double H = l_ns - hh.plogp / ns;
     if (H < 0.0) H = 0.0;
     uint32_t h0 = ws->hist[0][0];
     r.entropy = H;
@@ -775,8 +883,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(ParamsDev p, Workspac
     t.br_zfp_gt = (double)s.zfp_bits / (double)npoints_all;
     t.sse_zfp = zsse;
     t.maxerr_zfp = (double)__uint_as_float(s.zfp_maxerr);
-    double mse = zsse / (double)npoints_all;
-    t.psnr_zfp_gt = mse > 0.0 ? lvr - 10.0 * log10(mse) : INFINITY;
+    t.psnr_zfp_gt = mse_z > 0.0 ? lvr - 10.0 * l_mz : INFINITY;
   }
   if (passes & P_SZ_GT) {
     const HuffOut& hg = ws->huff[1];
@@ -790,8 +897,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(ParamsDev p, Workspac
     t.br_sz_gt = (double)t.sz_bits_gt / (double)npoints_all;
     t.sse_sz = ssse;
     t.maxerr_sz = (double)__uint_as_float(s.sz_maxerr);
-    double mse = ssse / (double)npoints_all;
-    t.psnr_sz_gt = mse > 0.0 ? lvr - 10.0 * log10(mse) : INFINITY;
+    t.psnr_sz_gt = mse_s > 0.0 ? lvr - 10.0 * l_ms : INFINITY;
     if (passes & P_ZFP_GT) t.best_gt = t.br_sz_gt < t.br_zfp_gt ? 0 : 1;
   }
   t.flags = s.flags & (RD_F_DELTA_CLAMPED | RD_F_MSE_ZERO | RD_F_CONSTANT);

@@ -27,9 +27,9 @@ using namespace rdk;
 
 namespace {
 
-// Stated maximum of the fixed scratch: 2.25 MiB per device, held for the
+// Stated maximum of the fixed scratch: 3.25 MiB per device, held for the
 // life of the process by every GPU that loads the library.
-constexpr size_t kStaticScratchBytes = 2359296;
+constexpr size_t kStaticScratchBytes = 3407872;
 static_assert(sizeof(Workspace) <= kStaticScratchBytes, "workspace exceeds the static scratch");
 
 static __device__ __align__(256) unsigned char g_select_scratch[kStaticScratchBytes];
@@ -61,6 +61,8 @@ int setup_device(int dev, DeviceSlot** out) {
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return RD_ERR_CUDA;
     if (prepare_code_stats() != cudaSuccess) return RD_ERR_CUDA;
     s.ws = static_cast<Workspace*>(p);
+    if (launch_init_tables(s.ws, 0) != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess)
+      return RD_ERR_CUDA;
     s.range_ctas = sms * 4;
     for (int d = 1; d <= 3; d++) {
       s.zfp_ctas[d] = zfp_occupancy(d, sms);
