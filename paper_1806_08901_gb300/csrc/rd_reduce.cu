@@ -394,12 +394,33 @@ __device__ void bitonic_sort(uint32_t* a, int n) {
   }
 }
 
-// number of A elements among the first d of merge(A, B), ties from A first
+// Number of A elements among the first d of merge(A, B), ties from A first:
+// the predicate A[i] <= B[d-1-i] holds for a prefix of i in [lo, hi].  A
+// 4-way search (three probes per step, loaded together) shortens the chain
+// of dependent loads, then binary steps finish.
 __device__ __forceinline__ uint32_t merge_split(const uint32_t* A, uint32_t na, const uint32_t* B,
                                                 uint32_t nb, uint32_t d) {
   uint32_t lo = d > nb ? d - nb : 0u, hi = d < na ? d : na;
+  while (hi - lo > 3u) {
+    const uint32_t q = (hi - lo) >> 2;
+    const uint32_t m1 = lo + q, m2 = lo + 2u * q, m3 = lo + 3u * q;
+    const bool p1 = A[m1] <= B[d - 1 - m1];
+    const bool p2 = A[m2] <= B[d - 1 - m2];
+    const bool p3 = A[m3] <= B[d - 1 - m3];
+    if (!p1) {
+      hi = m1;
+    } else if (!p2) {
+      lo = m1 + 1u;
+      hi = m2;
+    } else if (!p3) {
+      lo = m2 + 1u;
+      hi = m3;
+    } else {
+      lo = m3 + 1u;
+    }
+  }
   while (lo < hi) {
-    uint32_t mid = (lo + hi) >> 1;
+    const uint32_t mid = (lo + hi) >> 1;
     if (A[mid] <= B[d - 1 - mid]) lo = mid + 1; else hi = mid;
   }
   return lo;
@@ -408,48 +429,60 @@ __device__ __forceinline__ uint32_t merge_split(const uint32_t* A, uint32_t na, 
 
 constexpr int kPrepThreads = 256;   // code-statistics prep CTAs (1024 bins each)
 constexpr int kHuffThreads = 1024;  // Huffman CTA
+constexpr uint32_t kMinPairs = 1;   // fewest pairs per thread in a Huffman phase
 
-// Number of elements of the sorted a[0..n) below T, found by one warp: each
-// round tests 32 evenly spaced elements and keeps the gap holding the answer.
-__device__ uint32_t warp_count_below(const uint32_t* a, uint32_t n, unsigned long long T) {
-  const int lane = threadIdx.x & 31;
-  uint32_t lo = 0, hi = n;  // the answer lies in [lo, hi]
-  while (hi - lo > 32u) {
-    const uint32_t step = (hi - lo + 31u) / 32u;
-    const uint32_t idx = lo + (uint32_t)lane * step;
-    const bool p = idx < hi && (unsigned long long)a[idx] < T;
-    const int c = __popc(__ballot_sync(0xffffffffu, p));
-    if (c == 0) return lo;
-    const uint32_t nl = lo + (uint32_t)(c - 1) * step + 1u;
-    const uint32_t nh = lo + (uint32_t)c * step;
-    lo = nl;
-    hi = nh < hi ? nh : hi;
+// Numbers of elements below T of the sorted a[0..na) and b[0..nb), found
+// together by one warp: each round tests 32 evenly spaced elements of every
+// range still wider than 32 and keeps the gap holding the answer; a range of
+// at most 32 is answered by one ballot.  T < 2^33; a T of 2^32 or more
+// exceeds every 32-bit element.
+__device__ __forceinline__ void warp_count_below2(const uint32_t* a, uint32_t na,
+                                                  const uint32_t* b, uint32_t nb,
+                                                  unsigned long long T, uint32_t& ra,
+                                                  uint32_t& rb) {
+  if (T > 0xffffffffull) {
+    ra = na;
+    rb = nb;
+    return;
   }
-  const uint32_t idx = lo + (uint32_t)lane;
-  const bool p = idx < hi && (unsigned long long)a[idx] < T;
-  return lo + (uint32_t)__popc(__ballot_sync(0xffffffffu, p));
-}
-
-// Number of A elements among the first d of merge(A, B) (ties: A first),
-// found by one warp: the predicate A[i] <= B[d-1-i] holds for a prefix of i.
-__device__ uint32_t warp_merge_split(const uint32_t* A, uint32_t na, const uint32_t* B,
-                                     uint32_t nb, uint32_t d) {
-  const int lane = threadIdx.x & 31;
-  uint32_t lo = d > nb ? d - nb : 0u, hi = d < na ? d : na;  // answer in [lo, hi]
-  while (hi - lo > 32u) {
-    const uint32_t step = (hi - lo + 31u) / 32u;
-    const uint32_t i = lo + (uint32_t)lane * step;
-    const bool p = i < hi && A[i] <= B[d - 1 - i];
-    const int c = __popc(__ballot_sync(0xffffffffu, p));
-    if (c == 0) return lo;
-    const uint32_t nl = lo + (uint32_t)(c - 1) * step + 1u;
-    const uint32_t nh = lo + (uint32_t)c * step;
-    lo = nl;
-    hi = nh < hi ? nh : hi;
+  const uint32_t t = (uint32_t)T;
+  const uint32_t lane = threadIdx.x & 31u;
+  constexpr uint32_t kOpen = 0xffffffffu;
+  uint32_t alo = 0u, ahi = na, blo = 0u, bhi = nb;
+  ra = kOpen;
+  rb = kOpen;
+  while (ra == kOpen || rb == kOpen) {
+    const bool wa = ahi - alo > 32u, wb = bhi - blo > 32u;
+    const uint32_t sa = wa ? (ahi - alo + 31u) >> 5 : 1u;
+    const uint32_t sb = wb ? (bhi - blo + 31u) >> 5 : 1u;
+    const uint32_t ia = alo + lane * sa, ib = blo + lane * sb;
+    const bool pa = ra == kOpen && ia < ahi && a[ia] < t;
+    const bool pb = rb == kOpen && ib < bhi && b[ib] < t;
+    const uint32_t ca = (uint32_t)__popc(__ballot_sync(0xffffffffu, pa));
+    const uint32_t cb = (uint32_t)__popc(__ballot_sync(0xffffffffu, pb));
+    if (ra == kOpen) {
+      if (!wa) {
+        ra = alo + ca;
+      } else if (ca == 0u) {
+        ra = alo;
+      } else {
+        const uint32_t nh = alo + ca * sa;
+        alo += (ca - 1u) * sa + 1u;
+        ahi = nh < ahi ? nh : ahi;
+      }
+    }
+    if (rb == kOpen) {
+      if (!wb) {
+        rb = blo + cb;
+      } else if (cb == 0u) {
+        rb = blo;
+      } else {
+        const uint32_t nh = blo + cb * sb;
+        blo += (cb - 1u) * sb + 1u;
+        bhi = nh < bhi ? nh : bhi;
+      }
+    }
   }
-  const uint32_t i = lo + (uint32_t)lane;
-  const bool p = i < hi && A[i] <= B[d - 1 - i];
-  return lo + (uint32_t)__popc(__ballot_sync(0xffffffffu, p));
 }
 
 // ---------------------------------------------------------------------------
@@ -601,10 +634,10 @@ __device__ double block_sum_f64(double v, double* s_w) {
 //  2. The ascending leaf array: the first position of every distinct value
 //     is marked with the value and a running maximum over positions fills
 //     each run; the large counts follow, sorted by a bitonic network.
-//  3. The phased two-queue merge.  Every warp computes the phase threshold
-//     and split points itself from the shared arrays, so one barrier per
-//     phase suffices: in a phase nodes are written only above the queue
-//     tail, which no warp reads until the barrier.
+//  3. The phased two-queue merge: one warp finds the phase threshold and
+//     the numbers of leaves and nodes below it, then the threads pair
+//     contiguous runs of the merged order (nodes are written only above the
+//     queue tail, which no thread reads until the next barrier).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kHuffThreads) k_huffman(Workspace* ws, int which0) {
   extern __shared__ uint32_t s_dyn[];
@@ -618,6 +651,8 @@ __global__ void __launch_bounds__(kHuffThreads) k_huffman(Workspace* ws, int whi
 
   // 1. distinct values in ascending order
   const uint2 pw = reinterpret_cast<const uint2*>(ws->present[which])[tid];
+  const uint32_t nbig = ws->nbig[which];
+  double ent = tid < kEntropyCtas ? ws->ent_part[which][tid] : 0.0;
   uint32_t D;
   const uint32_t dbase = block_excl_sum(__popc(pw.x) + __popc(pw.y), s_w, &D);
   uint32_t* dv = (D <= (uint32_t)kHuffSmemKeys) ? s_dyn + kHuffSmemKeys : ws->distinct[which];
@@ -629,7 +664,6 @@ __global__ void __launch_bounds__(kHuffThreads) k_huffman(Workspace* ws, int whi
   __syncthreads();
   uint32_t msum = 0u;
   unsigned long long nsum = 0ull;
-  double ent = 0.0;
   for (uint32_t d0 = tid; d0 < D; d0 += 4u * kHuffThreads) {
     uint32_t vv[4], mm[4];
     double xl[4];
@@ -655,10 +689,8 @@ __global__ void __launch_bounds__(kHuffThreads) k_huffman(Workspace* ws, int whi
       }
     }
   }
-  const uint32_t nbig = ws->nbig[which];
   const uint32_t* big = ws->node_scratch[which];
   for (uint32_t i = tid; i < nbig; i += kHuffThreads) nsum += big[i];
-  if (tid < kEntropyCtas) ent += ws->ent_part[which][tid];
   uint32_t nsmall;
   (void)block_excl_sum(msum, s_w, &nsmall);
   const unsigned long long ns = block_sum_u64(nsum, s_w64);
@@ -712,24 +744,39 @@ __global__ void __launch_bounds__(kHuffThreads) k_huffman(Workspace* ws, int whi
     uint32_t lh = 0u, ih = 0u, it = 0u;  // leaf head, node head, node tail
     for (;;) {
       if ((K - lh) + (it - ih) <= 1u) break;
-      unsigned long long c4[4] = {~0ull, ~0ull, ~0ull, ~0ull};
-      if (lh < K) c4[0] = leaves[lh];
-      if (lh + 1 < K) c4[1] = leaves[lh + 1];
-      if (ih < it) c4[2] = nodes[ih];
-      if (ih + 1 < it) c4[3] = nodes[ih + 1];
-      const unsigned long long m01 = min(c4[0], c4[1]), x01 = max(c4[0], c4[1]);
-      const unsigned long long m23 = min(c4[2], c4[3]), x23 = max(c4[2], c4[3]);
-      const unsigned long long a0 = min(m01, m23);
-      const unsigned long long a1 = m01 < m23 ? min(x01, m23) : min(x23, m01);
-      const unsigned long long T = a0 + a1;
-      const uint32_t ml = warp_count_below(leaves + lh, K - lh, T);
-      const uint32_t mi = warp_count_below(nodes + ih, it - ih, T);
+      if (tid < 32) {
+        unsigned long long c4[4] = {~0ull, ~0ull, ~0ull, ~0ull};
+        if (lh < K) c4[0] = leaves[lh];
+        if (lh + 1 < K) c4[1] = leaves[lh + 1];
+        if (ih < it) c4[2] = nodes[ih];
+        if (ih + 1 < it) c4[3] = nodes[ih + 1];
+        const unsigned long long m01 = min(c4[0], c4[1]), x01 = max(c4[0], c4[1]);
+        const unsigned long long m23 = min(c4[2], c4[3]), x23 = max(c4[2], c4[3]);
+        const unsigned long long a0 = min(m01, m23);
+        const unsigned long long a1 = m01 < m23 ? min(x01, m23) : min(x23, m01);
+        uint32_t ml, mi;
+        warp_count_below2(leaves + lh, K - lh, nodes + ih, it - ih, a0 + a1, ml, mi);
+        // leaves among the 2 np paired items: all ml, unless the count is
+        // odd and the last item below T in merged order (ties: leaves
+        // first) is a leaf; that item waits for the next phase
+        uint32_t cl = ml;
+        if ((ml + mi) & 1u) {
+          if (mi == 0u || (ml > 0u && leaves[lh + ml - 1] > nodes[ih + mi - 1])) cl = ml - 1u;
+        }
+        if (tid == 0) {
+          s_w[0] = ml;
+          s_w[1] = mi;
+          s_w[2] = cl;
+        }
+      }
+      __syncthreads();
+      const uint32_t ml = s_w[0], mi = s_w[1], cl = s_w[2];
       const uint32_t np = (ml + mi) >> 1;
-      const uint32_t cl = warp_merge_split(leaves + lh, ml, nodes + ih, mi, 2u * np);
       const uint32_t* A = leaves + lh;
       const uint32_t* B = nodes + ih;
-      // each thread pairs a contiguous run of the merged order
-      const uint32_t per_t = (np + kHuffThreads - 1) / kHuffThreads;
+      // each thread pairs a contiguous run of the merged order (at least
+      // kMinPairs, so that few warps search when the phase is small)
+      const uint32_t per_t = max(kMinPairs, (np + kHuffThreads - 1) / kHuffThreads);
       const uint32_t j0 = (uint32_t)tid * per_t;
       const uint32_t j1 = min(np, j0 + per_t);
       if (j0 < j1) {
