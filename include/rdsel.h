@@ -175,8 +175,9 @@ int32_t rd_evaluate(rd_context* ctx, const rd_field* field,
  * framework whose allocator must serve every allocation) or that cannot take
  * the synchronisation an allocation may imply.  It needs no context and
  * calls no cudaMalloc, cudaFree, cudaMallocHost or other allocating routine:
- * its scratch is one fixed 3.25 MiB array inside the library, held by every
- * GPU that loads the library until the process exits.
+ * its scratch is fixed arrays inside the library (2.75 MiB of workspace and
+ * a 0.5 MiB table), held by every GPU that loads the library until the
+ * process exits.
  *  - field: DEVICE memory only (location RD_LOC_HOST is rejected, since a
  *    host field would need a staging buffer), at most 2^31-1 points; larger
  *    or malformed shapes return RD_ERR_INVALID_ARG.  The scratch does not
@@ -191,6 +192,51 @@ int32_t rd_evaluate(rd_context* ctx, const rd_field* field,
  *  - Results equal rd_select's on the same field and parameters. */
 int32_t rd_select_static(const rd_field* field, const rd_params* params,
                          rd_result* out, void* stream);
+
+/* ---- batched estimate ------------------------------------------------ */
+
+/* Work split of the batched passes.  The results do not depend on it. */
+typedef struct {
+  int64_t range_values; /* values per work item of the range pass (multiple of 4) */
+  int32_t zfp_blocks;   /* sampled ZFP blocks per work item */
+  int32_t sz_points;    /* points of sampled blocks per SZ work item */
+  int32_t range_ctas;   /* persistent grids; 0 = every CTA the SMs hold at once */
+  int32_t zfp_ctas;
+  int32_t sz_ctas;
+  int32_t tuned;        /* output: 1 when the autotuner chose this split */
+} rd_batch_config;
+
+/* Algorithm 1 lines 2-12 for n fields at once, e.g. every field of a
+ * simulation snapshot, of uneven 2D/3D sizes (the paper's algorithm loops
+ * over the fields of a snapshot).  Six persistent launches cover all fields:
+ * reset; value range (the CTA that ends a field's last work item also
+ * derives VR and eb_abs); sampled ZFP blocks (the CTA that ends a field's
+ * last item also derives delta); sampled SZ points; count-of-counts; one CTA
+ * per field for the Huffman cost, entropy, rates, PSNRs and selection.
+ *  - fields[i]: DEVICE memory only (RD_ERR_INVALID_ARG otherwise);
+ *    params[i]: the parameters of field i.  n >= 1.
+ *  - results[n] is required; truths[n] may be NULL, else each field's ground
+ *    truth at delta/2 is added as in rd_evaluate; status[n] may be NULL, else
+ *    it receives each field's status.
+ *  - Return: RD_OK when every field succeeded; else the status of the first
+ *    failing field (whose records are zeroed; the others stay valid), or a
+ *    call-level error (RD_ERR_INVALID_ARG, _OOM, _BUDGET, _CUDA) with every
+ *    record zeroed.
+ *  - The context holds one workspace per field (about 2.6 MB each) and caches
+ *    a plan per distinct set of fields and parameters: the plan's first call
+ *    runs the autotuner (three work splits, each pass timed, the fastest
+ *    split per pass kept) unless rd_batch_set_config forced one; its second
+ *    call captures a CUDA graph that later calls replay.
+ *  - Each field's records equal those of rd_select (and of rd_evaluate for
+ *    the truth) on that field alone. */
+int32_t rd_select_batch(rd_context* ctx, const rd_field* fields,
+                        const rd_params* params, int32_t n, rd_result* results,
+                        rd_truth* truths, int32_t* status, void* stream);
+/* Force the work split of later batch calls (NULL: autotune, the default).
+ * Zero item sizes take the middle of the autotuner's candidates. */
+int32_t rd_batch_set_config(rd_context* ctx, const rd_batch_config* cfg);
+/* The work split of the last batch call. */
+int32_t rd_batch_get_config(rd_context* ctx, rd_batch_config* out);
 
 /* ---- inspection (same kernels, per-element outputs) ------------------ */
 

@@ -18,7 +18,9 @@ namespace {
 
 const char* kKernelNames[K_COUNT] = {
     "reset", "range", "prepare", "zfp_pass", "delta", "sz_est", "sz_pass",
-    "code_prep", "huffman", "finish", "zfp_inspect", "sz_inspect"};
+    "code_prep", "huffman", "finish", "zfp_inspect", "sz_inspect",
+    "batch_reset", "batch_range", "batch_zfp_est", "batch_sz_est", "batch_code_prep",
+    "batch_final", "batch_truth"};
 
 struct KStat {
   double ms;
@@ -59,6 +61,38 @@ struct GraphEntry {
 constexpr size_t kMaxGraphs = 16;
 constexpr size_t kMaxSeen = 32;
 
+struct Geometry {
+  FieldDev f;
+  unsigned long long npoints_sampled;  // valid points of sampled blocks
+  int partial;
+};
+
+// A batch of fields as planned once: device tables of fields and work items
+// for one work split, and the CUDA graph of its launches once captured.
+struct BatchPlan {
+  std::vector<unsigned char> key;  // n, truth flag, split mode, fields and parameters
+  int n = 0;
+  int need_gt = 0;
+  rd_batch_config cfg;
+  std::vector<BatchField> hbf;
+  std::vector<Geometry> geo;
+  BatchField* dbf = nullptr;
+  BatchItem* ditems = nullptr;
+  int n_range = 0, n_zfp = 0, n_sz = 0;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<Pending> events;
+  long long kernels = 0;
+  int uses = 0;
+  unsigned long long last_use = 0;
+};
+
+constexpr size_t kMaxPlans = 8;
+
+// Candidate work splits of the autotuner (small, middle, large).
+constexpr long long kRangeValues[3] = {1ll << 16, 1ll << 18, 1ll << 20};
+constexpr int kZfpBlocks[3] = {256, 1024, 4096};
+constexpr int kSzPoints[3] = {4096, 16384, 65536};
+
 }  // namespace
 
 struct rd_context {
@@ -66,6 +100,7 @@ struct rd_context {
   size_t budget = 0;
   size_t held = 0;
   Workspace* ws = nullptr;
+  double* xlogx = nullptr;  // v log2 v table of the entropy sums
   HostOut* out = nullptr;  // pinned
   float* staging = nullptr;
   size_t staging_bytes = 0;
@@ -73,6 +108,7 @@ struct rd_context {
   int range_ctas = 0;
   int zfp_ctas[4] = {0, 0, 0, 0};
   int sz_ctas[4] = {0, 0, 0, 0};
+  int b_range_ctas = 0, b_zfp_ctas = 0, b_sz_ctas = 0;  // resident CTAs of the batched passes
   bool profiling = false;
   KStat stats[K_COUNT];
   std::vector<Pending> pending;
@@ -86,6 +122,19 @@ struct rd_context {
   bool capturing = false;
   std::vector<Pending>* sink = nullptr;
   long long cap_kernels = 0;
+  // batches: one workspace per field, gathered records, cached plans
+  Workspace* bws = nullptr;
+  int bws_n = 0;
+  rd_result* d_bres = nullptr;
+  rd_truth* d_btruth = nullptr;
+  int32_t* d_bstatus = nullptr;
+  rd_result* h_bres = nullptr;  // pinned
+  rd_truth* h_btruth = nullptr;
+  int32_t* h_bstatus = nullptr;
+  std::vector<BatchPlan*> plans;
+  bool batch_forced = false;
+  rd_batch_config batch_force;
+  rd_batch_config batch_last;
 };
 
 namespace {
@@ -226,12 +275,6 @@ void sampling_strides(int d, double r_sp, int* s) {
   }
 }
 
-struct Geometry {
-  FieldDev f;
-  unsigned long long npoints_sampled;  // valid points of sampled blocks
-  int partial;
-};
-
 int make_geometry(rd_context* c, const rd_field* fld, const int* strides_or_null, double r_sp,
                   cudaStream_t s, Geometry* g) {
   if (!fld || fld->ndim < 1 || fld->ndim > 3 || !fld->data) return RD_ERR_INVALID_ARG;
@@ -346,7 +389,7 @@ int issue(rd_context* c, const CallKey& k, const Geometry& g, cudaStream_t s) {
   int hist_mask = ((passes & P_SZ_EST) ? 1 : 0) | ((passes & P_SZ_GT) ? 2 : 0);
   if (hist_mask) {
     if ((rc = launch(c, K_CODE_PREP, s, [&] { return launch_code_prep(ws, hist_mask, s); }))) return rc;
-    if ((rc = launch(c, K_HUFFMAN, s, [&] { return launch_huffman(ws, hist_mask, s); }))) return rc;
+    if ((rc = launch(c, K_HUFFMAN, s, [&] { return launch_huffman(ws, hist_mask, c->xlogx, s); }))) return rc;
   }
   if ((rc = launch(c, K_FINISH, s, [&] {
          return launch_finish(p, ws, passes, zfp_parts, sz_parts, f.N, g.npoints_sampled, s);
@@ -485,6 +528,408 @@ int run(rd_context* c, const rd_field* fld, const rd_params* prm, int passes, in
   return RD_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Batches (rd_select_batch)
+// ---------------------------------------------------------------------------
+void free_plan(BatchPlan* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (const Pending& p : b->events) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  if (b->dbf) cudaFree(b->dbf);
+  if (b->ditems) cudaFree(b->ditems);
+  delete b;
+}
+
+void drop_plans(rd_context* c) {
+  for (BatchPlan* b : c->plans) free_plan(b);
+  c->plans.clear();
+}
+
+void free_batch_buffers(rd_context* c) {
+  drop_plans(c);
+  if (c->bws) cudaFree(c->bws);
+  if (c->d_bres) cudaFree(c->d_bres);
+  if (c->d_btruth) cudaFree(c->d_btruth);
+  if (c->d_bstatus) cudaFree(c->d_bstatus);
+  if (c->h_bres) cudaFreeHost(c->h_bres);
+  if (c->h_btruth) cudaFreeHost(c->h_btruth);
+  if (c->h_bstatus) cudaFreeHost(c->h_bstatus);
+  c->bws = nullptr;
+  c->d_bres = nullptr;
+  c->d_btruth = nullptr;
+  c->d_bstatus = nullptr;
+  c->h_bres = nullptr;
+  c->h_btruth = nullptr;
+  c->h_bstatus = nullptr;
+}
+
+size_t batch_device_bytes(int n) {
+  return (size_t)n * (sizeof(Workspace) + sizeof(rd_result) + sizeof(rd_truth) + sizeof(int32_t));
+}
+
+// One workspace per field and the gathered records, grown to n fields (the
+// cached plans point into them, so growing drops the plans).
+int ensure_batch_capacity(rd_context* c, int n) {
+  if (c->bws_n >= n) return RD_OK;
+  const size_t old = c->bws_n ? batch_device_bytes(c->bws_n) : 0;
+  free_batch_buffers(c);
+  c->held -= old;
+  c->bws_n = 0;
+  const size_t bytes = batch_device_bytes(n);
+  if (c->budget && c->held + bytes > c->budget) return RD_ERR_BUDGET;
+  bool ok = cudaMalloc(&c->bws, (size_t)n * sizeof(Workspace)) == cudaSuccess &&
+            cudaMalloc(&c->d_bres, (size_t)n * sizeof(rd_result)) == cudaSuccess &&
+            cudaMalloc(&c->d_btruth, (size_t)n * sizeof(rd_truth)) == cudaSuccess &&
+            cudaMalloc(&c->d_bstatus, (size_t)n * sizeof(int32_t)) == cudaSuccess &&
+            cudaMallocHost(&c->h_bres, (size_t)n * sizeof(rd_result)) == cudaSuccess &&
+            cudaMallocHost(&c->h_btruth, (size_t)n * sizeof(rd_truth)) == cudaSuccess &&
+            cudaMallocHost(&c->h_bstatus, (size_t)n * sizeof(int32_t)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_batch_buffers(c);
+    return RD_ERR_OOM;
+  }
+  c->bws_n = n;
+  c->held += bytes;
+  return RD_OK;
+}
+
+// Work items of the three item-based passes for one split; counts per field
+// go into the field table.
+void build_items(BatchPlan* b, const rd_batch_config& cfg, std::vector<BatchItem>& items) {
+  items.clear();
+  auto split = [&](int i, long long units, long long per) {
+    long long cnt = units > 0 ? (units + per - 1) / per : 0;
+    for (long long k = 0; k < cnt; k++) {
+      BatchItem it;
+      it.field = i;
+      it.pad = 0;
+      it.begin = k * per;
+      it.end = (k + 1) * per < units ? (k + 1) * per : units;
+      items.push_back(it);
+    }
+    return (uint32_t)cnt;
+  };
+  for (int i = 0; i < b->n; i++) b->hbf[i].items_range = split(i, b->hbf[i].f.N, cfg.range_values);
+  b->n_range = (int)items.size();
+  for (int i = 0; i < b->n; i++) b->hbf[i].items_zfp = split(i, b->hbf[i].f.nsampled, cfg.zfp_blocks);
+  b->n_zfp = (int)items.size() - b->n_range;
+  for (int i = 0; i < b->n; i++) {
+    const FieldDev& f = b->hbf[i].f;
+    split(i, f.nsampled * (1ll << (2 * f.d)), cfg.sz_points);
+  }
+  b->n_sz = (int)items.size() - b->n_range - b->n_zfp;
+}
+
+// Upload the tables of a split (the item buffer holds the largest count,
+// that of the smallest candidate work items).
+int upload_plan(BatchPlan* b, const rd_batch_config& cfg) {
+  std::vector<BatchItem> items;
+  build_items(b, cfg, items);
+  if (!b->dbf && cudaMalloc(&b->dbf, b->hbf.size() * sizeof(BatchField)) != cudaSuccess) return RD_ERR_OOM;
+  if (!b->ditems) {
+    rd_batch_config small = cfg;
+    small.range_values = kRangeValues[0] < cfg.range_values ? kRangeValues[0] : cfg.range_values;
+    small.zfp_blocks = kZfpBlocks[0] < cfg.zfp_blocks ? kZfpBlocks[0] : cfg.zfp_blocks;
+    small.sz_points = kSzPoints[0] < cfg.sz_points ? kSzPoints[0] : cfg.sz_points;
+    std::vector<BatchItem> most;
+    std::vector<BatchField> keep = b->hbf;
+    build_items(b, small, most);
+    b->hbf = keep;
+    build_items(b, cfg, items);
+    if (cudaMalloc(&b->ditems, most.size() * sizeof(BatchItem)) != cudaSuccess) return RD_ERR_OOM;
+  }
+  if (cudaMemcpy(b->dbf, b->hbf.data(), b->hbf.size() * sizeof(BatchField), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpy(b->ditems, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice) !=
+          cudaSuccess)
+    return RD_ERR_CUDA;
+  b->cfg = cfg;
+  return RD_OK;
+}
+
+rd_batch_config resolve_ctas(const rd_context* c, rd_batch_config cfg) {
+  if (cfg.range_ctas <= 0) cfg.range_ctas = c->b_range_ctas;
+  if (cfg.zfp_ctas <= 0) cfg.zfp_ctas = c->b_zfp_ctas;
+  if (cfg.sz_ctas <= 0) cfg.sz_ctas = c->b_sz_ctas;
+  return cfg;
+}
+
+rd_batch_config split_level(const rd_context* c, int lr, int lz, int ls) {
+  rd_batch_config cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.range_values = kRangeValues[lr];
+  cfg.zfp_blocks = kZfpBlocks[lz];
+  cfg.sz_points = kSzPoints[ls];
+  return resolve_ctas(c, cfg);
+}
+
+// The estimate launches of a batch (reset .. final), optionally with event
+// pairs around the three item-based passes (the autotuner's timing).
+int issue_batch_estimate(rd_context* c, BatchPlan* b, cudaStream_t s, cudaEvent_t* ev) {
+  const int n = b->n;
+  const rd_batch_config& cfg = b->cfg;
+  int rc;
+  if ((rc = launch(c, K_B_RESET, s, [&] { return launch_batch_reset(b->dbf, n, b->need_gt, s); })))
+    return rc;
+  if (ev) cudaEventRecord(ev[0], s);
+  if ((rc = launch(c, K_B_RANGE, s, [&] {
+         return launch_batch_range(b->dbf, b->ditems, b->n_range, cfg.range_ctas, s);
+       })))
+    return rc;
+  if (ev) cudaEventRecord(ev[1], s);
+  if ((rc = launch(c, K_B_ZFP, s, [&] {
+         return launch_batch_zfp_est(b->dbf, b->ditems + b->n_range, b->n_zfp, cfg.zfp_ctas, s);
+       })))
+    return rc;
+  if (ev) cudaEventRecord(ev[2], s);
+  if ((rc = launch(c, K_B_SZ, s, [&] {
+         return launch_batch_sz_est(b->dbf, b->ditems + b->n_range + b->n_zfp, b->n_sz, cfg.sz_ctas, s);
+       })))
+    return rc;
+  if (ev) cudaEventRecord(ev[3], s);
+  if ((rc = launch(c, K_B_PREP, s, [&] { return launch_batch_code_prep(b->dbf, n, s); }))) return rc;
+  return launch(c, K_B_FINAL, s, [&] {
+    return launch_batch_final(b->dbf, n, c->xlogx, c->d_bres, c->d_bstatus, s);
+  });
+}
+
+// The whole launch sequence of a batch call and the copies of its records.
+int issue_batch(rd_context* c, BatchPlan* b, cudaStream_t s) {
+  int rc = issue_batch_estimate(c, b, s, nullptr);
+  if (rc) return rc;
+  const int n = b->n;
+  if (b->need_gt) {
+    // the truth of each field, by the per-field passes on its workspace
+    for (int i = 0; i < n; i++) {
+      const FieldDev& f = b->hbf[i].f;
+      const ParamsDev& p = b->hbf[i].p;
+      Workspace* ws = b->hbf[i].ws;
+      const unsigned long long npts = b->hbf[i].npoints;
+      const int d = f.d;
+      int zparts = 0, sparts = 0;
+      if ((rc = launch(c, K_ZFP, s, [&] {
+             return launch_zfp(f, p, P_ZFP_GT, ws, c->zfp_ctas[d], s, &zparts);
+           })))
+        return rc;
+      if ((rc = launch(c, K_SZ_GT, s, [&] {
+             if (sz_march_supported(f)) return launch_sz_march(f, p, 0, ws, c->num_sms, s, &sparts);
+             return launch_sz_gt(f, p, 0, ws, c->sz_ctas[d], s, &sparts);
+           })))
+        return rc;
+      if ((rc = launch(c, K_CODE_PREP, s, [&] { return launch_code_prep(ws, 2, s); }))) return rc;
+      if ((rc = launch(c, K_HUFFMAN, s, [&] { return launch_huffman(ws, 2, c->xlogx, s); }))) return rc;
+      if ((rc = launch(c, K_FINISH, s, [&] {
+             return launch_finish(p, ws, P_ZFP_GT | P_SZ_GT, zparts, sparts, f.N, npts, s);
+           })))
+        return rc;
+    }
+    if ((rc = launch(c, K_B_TRUTH, s, [&] {
+           return launch_batch_truth(b->dbf, n, c->d_btruth, c->d_bstatus, s);
+         })))
+      return rc;
+  }
+  cudaError_t e = cudaMemcpyAsync(c->h_bres, c->d_bres, n * sizeof(rd_result), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->h_bstatus, c->d_bstatus, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && b->need_gt)
+    e = cudaMemcpyAsync(c->h_btruth, c->d_btruth, n * sizeof(rd_truth), cudaMemcpyDeviceToHost, s);
+  return cuda_status(e);
+}
+
+// Autotuner: run the estimate with the small, middle and large work items
+// of every pass, time each item-based pass with events, and keep the
+// fastest split per pass.  The results do not depend on the split (integer
+// sums, fixed-order floating point), so these are ordinary runs.
+int autotune_plan(rd_context* c, BatchPlan* b, cudaStream_t s) {
+  cudaEvent_t ev[4];
+  for (int i = 0; i < 4; i++)
+    if (cudaEventCreate(&ev[i]) != cudaSuccess) return RD_ERR_CUDA;
+  float best[3] = {1e30f, 1e30f, 1e30f};
+  int lvl[3] = {1, 1, 1};
+  int rc = RD_OK;
+  const bool prof = c->profiling;
+  c->profiling = false;
+  for (int l = 0; l < 3 && rc == RD_OK; l++) {
+    rc = upload_plan(b, split_level(c, l, l, l));
+    if (rc == RD_OK) rc = issue_batch_estimate(c, b, s, ev);
+    if (rc == RD_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = RD_ERR_CUDA;
+    for (int k = 0; k < 3 && rc == RD_OK; k++) {
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) == cudaSuccess && ms < best[k]) {
+        best[k] = ms;
+        lvl[k] = l;
+      }
+    }
+  }
+  c->profiling = prof;
+  for (int i = 0; i < 4; i++) cudaEventDestroy(ev[i]);
+  if (rc) return rc;
+  rd_batch_config cfg = split_level(c, lvl[0], lvl[1], lvl[2]);
+  cfg.tuned = 1;
+  return upload_plan(b, cfg);
+}
+
+BatchPlan* find_plan(rd_context* c, const std::vector<unsigned char>& key) {
+  for (BatchPlan* b : c->plans)
+    if (b->key == key) return b;
+  return nullptr;
+}
+
+// Returns a call-level error (no record written) or, once the records are
+// written (*written set), the status of the first failing field.
+int batch_call(rd_context* c, const rd_field* fields, const rd_params* params, int n,
+               rd_result* results, rd_truth* truths, int32_t* status, cudaStream_t s,
+               bool* written) {
+  const int need_gt = truths ? 1 : 0;
+  std::vector<Geometry> geo((size_t)n);
+  for (int i = 0; i < n; i++) {
+    int rc = check_params(&params[i]);
+    if (rc) return rc;
+    if (fields[i].location != RD_LOC_DEVICE) return RD_ERR_INVALID_ARG;
+    rc = make_geometry(c, &fields[i], nullptr, params[i].r_sp, s, &geo[i]);
+    if (rc) return rc;
+  }
+  int rc = ensure_batch_capacity(c, n);
+  if (rc) return rc;
+  // the plan key: everything the launch sequence depends on
+  std::vector<unsigned char> key;
+  auto put = [&](const void* p, size_t bytes) {
+    const unsigned char* q = static_cast<const unsigned char*>(p);
+    key.insert(key.end(), q, q + bytes);
+  };
+  const int forced = c->batch_forced ? 1 : 0;
+  put(&n, sizeof(n));
+  put(&need_gt, sizeof(need_gt));
+  put(&forced, sizeof(forced));
+  if (forced) put(&c->batch_force, sizeof(rd_batch_config));
+  std::vector<ParamsDev> pdev((size_t)n);
+  for (int i = 0; i < n; i++) {
+    pdev[i] = to_dev(&params[i]);
+    put(&geo[i].f, sizeof(FieldDev));
+    put(&pdev[i], sizeof(ParamsDev));
+  }
+  BatchPlan* b = find_plan(c, key);
+  if (!b) {
+    if (c->plans.size() >= kMaxPlans) {
+      size_t lru = 0;
+      for (size_t i = 1; i < c->plans.size(); i++)
+        if (c->plans[i]->last_use < c->plans[lru]->last_use) lru = i;
+      free_plan(c->plans[lru]);
+      c->plans.erase(c->plans.begin() + lru);
+    }
+    b = new (std::nothrow) BatchPlan();
+    if (!b) return RD_ERR_OOM;
+    b->key = key;
+    b->n = n;
+    b->need_gt = need_gt;
+    b->geo = geo;
+    b->hbf.resize((size_t)n);
+    for (int i = 0; i < n; i++) {
+      BatchField& F = b->hbf[i];
+      memset(&F, 0, sizeof(F));
+      F.f = geo[i].f;
+      F.p = pdev[i];
+      F.ws = c->bws + i;
+      F.ncoeff = (unsigned long long)F.f.nsampled * ec_count(F.f.d, params[i].ec_mode);
+      F.npoints = geo[i].npoints_sampled;
+      F.need_gt = need_gt;
+    }
+    if (forced) {
+      rd_batch_config cfg = c->batch_force;
+      if (cfg.range_values <= 0) cfg.range_values = kRangeValues[1];
+      if (cfg.zfp_blocks <= 0) cfg.zfp_blocks = kZfpBlocks[1];
+      if (cfg.sz_points <= 0) cfg.sz_points = kSzPoints[1];
+      cfg.range_values = (cfg.range_values + 3) / 4 * 4;
+      cfg.tuned = 0;
+      rc = upload_plan(b, resolve_ctas(c, cfg));
+    } else {
+      rc = autotune_plan(c, b, s);
+    }
+    if (rc) {
+      free_plan(b);
+      return rc;
+    }
+    c->plans.push_back(b);
+  }
+  b->last_use = ++c->tick;
+  cudaError_t e = cudaSuccess;
+  if (!b->exec && b->uses >= 1) {
+    // capture the repeat into a graph
+    if (c->cap || cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) == cudaSuccess) {
+      if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        c->capturing = true;
+        c->sink = &b->events;
+        c->cap_kernels = 0;
+        int crc = issue_batch(c, b, c->cap);
+        c->capturing = false;
+        c->sink = nullptr;
+        cudaGraph_t graph = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(c->cap, &graph);
+        if (crc == RD_OK && ce == cudaSuccess) ce = cudaGraphInstantiate(&b->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (crc != RD_OK || ce != cudaSuccess) {
+          cudaGetLastError();
+          b->exec = nullptr;
+          for (const Pending& p : b->events) {
+            cudaEventDestroy(p.a);
+            cudaEventDestroy(p.b);
+          }
+          b->events.clear();
+        } else {
+          b->kernels = c->cap_kernels;
+        }
+      }
+    }
+  }
+  b->uses++;
+  if (b->exec) {
+    e = cudaGraphLaunch(b->exec, s);
+    c->launches += b->kernels;
+    rc = cuda_status(e);
+  } else {
+    rc = issue_batch(c, b, s);
+  }
+  e = cudaStreamSynchronize(s);
+  if (c->profiling) {
+    if (b->exec)
+      add_times(c, b->events);
+    else
+      collect_profile(c);
+  }
+  if (rc != RD_OK) return rc;
+  if (e != cudaSuccess) return cuda_status(e);
+  c->batch_last = b->cfg;
+  *written = true;
+  int first = RD_OK;
+  for (int i = 0; i < n; i++) {
+    const int st = c->h_bstatus[i];
+    if (status) status[i] = st;
+    if (st != RD_OK) {
+      memset(&results[i], 0, sizeof(rd_result));
+      if (truths) memset(&truths[i], 0, sizeof(rd_truth));
+      if (first == RD_OK) first = st;
+      continue;
+    }
+    const FieldDev& f = b->hbf[i].f;
+    rd_result r = c->h_bres[i];
+    for (int k = 0; k < 3; k++) r.strides[k] = k < f.d ? f.s[k] : 0;
+    r.n_blocks = (uint64_t)f.nblocks;
+    if (!(r.flags & RD_F_CONSTANT)) {
+      r.n_sampled_blocks = (uint64_t)f.nsampled;
+      r.r_sp_eff = (double)f.nsampled / (double)f.nblocks;
+      r.zfp_npoints = b->hbf[i].npoints;
+      r.zfp_ncoeff = b->hbf[i].ncoeff;
+    }
+    if (b->geo[i].partial) r.flags |= RD_F_PARTIAL_BLOCKS;
+    results[i] = r;
+    if (truths) truths[i] = c->h_btruth[i];
+  }
+  return first;
+}
+
 }  // namespace
 
 extern "C" {
@@ -506,7 +951,12 @@ int32_t rd_context_create(int32_t device, size_t hbm_budget, rd_context** out) {
     delete c;
     return RD_ERR_OOM;
   }
-  c->held = sizeof(Workspace);
+  if (cudaMalloc(&c->xlogx, kNsym * sizeof(double)) != cudaSuccess) {
+    cudaFree(c->ws);
+    delete c;
+    return RD_ERR_OOM;
+  }
+  c->held = sizeof(Workspace) + kNsym * sizeof(double);
   if (cudaMallocHost(&c->out, sizeof(HostOut)) != cudaSuccess) {
     cudaFree(c->ws);
     delete c;
@@ -514,8 +964,9 @@ int32_t rd_context_create(int32_t device, size_t hbm_budget, rd_context** out) {
   }
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
   if (prepare_code_stats() != cudaSuccess || prepare_sz_march() != cudaSuccess ||
-      launch_init_tables(c->ws, 0) != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess) {
+      launch_init_tables(c->xlogx, 0) != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess) {
     cudaFreeHost(c->out);
+    cudaFree(c->xlogx);
     cudaFree(c->ws);
     delete c;
     return RD_ERR_CUDA;
@@ -525,6 +976,9 @@ int32_t rd_context_create(int32_t device, size_t hbm_budget, rd_context** out) {
     c->zfp_ctas[d] = zfp_occupancy(d, c->num_sms);
     c->sz_ctas[d] = sz_occupancy(d, c->num_sms);
   }
+  c->b_range_ctas = batch_range_occupancy(c->num_sms);
+  c->b_zfp_ctas = batch_zfp_occupancy(c->num_sms);
+  c->b_sz_ctas = batch_sz_occupancy(c->num_sms);
   *out = c;
   return RD_OK;
 }
@@ -539,9 +993,11 @@ int32_t rd_context_destroy(rd_context* c) {
     cudaEventDestroy(p.b);
   }
   for (GraphEntry& g : c->graphs) drop_entry(g);
+  free_batch_buffers(c);
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->staging) cudaFree(c->staging);
   if (c->ws) cudaFree(c->ws);
+  if (c->xlogx) cudaFree(c->xlogx);
   if (c->out) cudaFreeHost(c->out);
   delete c;
   return RD_OK;
@@ -577,6 +1033,41 @@ int32_t rd_evaluate(rd_context* c, const rd_field* f, const rd_params* p, rd_res
                     rd_truth* truth, void* stream) {
   return run(c, f, p, P_ZFP_EST | P_ZFP_GT | P_SZ_EST | P_SZ_GT, DELTA_FROM_MSE, 0.0, est, truth,
              stream);
+}
+
+int32_t rd_select_batch(rd_context* c, const rd_field* fields, const rd_params* params, int32_t n,
+                        rd_result* results, rd_truth* truths, int32_t* status, void* stream) {
+  if (!c || !fields || !params || !results || n < 1) return RD_ERR_INVALID_ARG;
+  CallGuard guard(c->device);
+  bool written = false;
+  int rc = batch_call(c, fields, params, n, results, truths, status, (cudaStream_t)stream, &written);
+  if (!written) {
+    memset(results, 0, sizeof(rd_result) * (size_t)n);
+    if (truths) memset(truths, 0, sizeof(rd_truth) * (size_t)n);
+    if (status)
+      for (int i = 0; i < n; i++) status[i] = rc;
+  }
+  return rc;
+}
+
+int32_t rd_batch_set_config(rd_context* c, const rd_batch_config* cfg) {
+  if (!c) return RD_ERR_INVALID_ARG;
+  if (!cfg) {
+    c->batch_forced = false;
+    return RD_OK;
+  }
+  if (cfg->range_values < 0 || cfg->zfp_blocks < 0 || cfg->sz_points < 0 || cfg->range_ctas < 0 ||
+      cfg->zfp_ctas < 0 || cfg->sz_ctas < 0)
+    return RD_ERR_INVALID_ARG;
+  c->batch_forced = true;
+  c->batch_force = *cfg;
+  return RD_OK;
+}
+
+int32_t rd_batch_get_config(rd_context* c, rd_batch_config* out) {
+  if (!c || !out) return RD_ERR_INVALID_ARG;
+  *out = c->batch_last;
+  return RD_OK;
 }
 
 int32_t rd_copy_histograms(rd_context* c, uint32_t* est_hist, uint32_t* gt_hist) {

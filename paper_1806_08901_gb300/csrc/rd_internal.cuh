@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "rdsel.h"
@@ -28,6 +29,7 @@ struct Scalars {
   int32_t constant;      // value range is zero
   int32_t minexp;        // floor(log2 eb_abs)
   uint32_t min_key, max_key, nonfinite, pad0;
+  uint32_t done[2];       // work items finished (batched passes: last-CTA detection)
   float vmin, vmax, amax;  // amax = max(|vmin|, |vmax|)
   float w, inv, tau;       // SZ quantiser: bin, 1/bin, escape threshold
   double vr, eb_abs, delta, mse_sp;
@@ -47,23 +49,26 @@ struct HuffOut {
   uint32_t pad;
 };
 
+// The arrays are 16-byte aligned: kernels clear and read them as uint4.
 struct Workspace {
   Scalars sc;
-  uint32_t hist[2][kNsym];            // 0 = SZ estimate, 1 = SZ ground truth
-  double ent_part[2][kEntropyCtas];   // partial sums of h log2 h
+  alignas(16) uint32_t hist[2][kNsym];          // 0 = SZ estimate, 1 = SZ ground truth
+  double ent_part[2][kEntropyCtas];             // partial sums of h log2 h
   HuffOut huff[2];
-  double zfp_sse[kMaxGrid];           // per-CTA partial sums (fixed order)
+  double zfp_sse[kMaxGrid];                     // per-CTA partial sums (fixed order)
   double sz_sse[kMaxGrid];
-  uint32_t count_of[2][kNsym];        // multiplicity of each count value below 2^16
-  uint32_t present[2][kNsym / 32];    // bitmap of the count values present
-  uint32_t nbig[2];                   // counts of 2^16 or more
-  uint32_t distinct[2][kNsym];        // sorted distinct counts when there are many
-  double xlogx[kNsym];                // v log2 v, filled once per workspace
-  uint32_t sort_scratch[2][kNsym];    // Huffman leaves when K is large
-  uint32_t node_scratch[2][kNsym];    // counts >= 2^16, then Huffman internal nodes when K is large
+  alignas(16) uint32_t count_of[2][kNsym];      // multiplicity of each count value below 2^16
+  alignas(16) uint32_t present[2][kNsym / 32];  // bitmap of the count values present
+  uint32_t nbig[2];                             // counts of 2^16 or more
+  alignas(16) uint32_t distinct[2][kNsym];      // sorted distinct counts when there are many
+  alignas(16) uint32_t sort_scratch[2][kNsym];  // Huffman leaves when K is large
+  alignas(16) uint32_t node_scratch[2][kNsym];  // counts >= 2^16, then Huffman internal nodes
   rd_result res;
   rd_truth truth;
 };
+static_assert(offsetof(Workspace, hist) % 16 == 0 && offsetof(Workspace, count_of) % 16 == 0 &&
+                  offsetof(Workspace, present) % 16 == 0 && sizeof(Workspace) % 16 == 0,
+              "workspace arrays must be 16-byte aligned");
 
 // Field geometry, passed by value to every kernel.  Axis 0 is the slowest;
 // only the first d entries are meaningful.
@@ -89,6 +94,27 @@ struct ParamsDev {
   double sz_offset;
 };
 
+// One field of a batched call (rd_select_batch), in device memory.
+struct BatchField {
+  FieldDev f;
+  ParamsDev p;
+  Workspace* ws;                 // the field's own workspace
+  unsigned long long ncoeff;     // EC-sampled coefficients (denominator of MSE_sp)
+  unsigned long long npoints;    // valid points of the sampled blocks
+  uint32_t items_range;          // work items of the field in the range pass
+  uint32_t items_zfp;            // ... and in the ZFP estimate pass
+  int32_t need_gt;               // the quantiser is also prepared for the ground truth
+  int32_t pad;
+};
+
+// A work item of a batched pass: units [begin, end) of one field (values,
+// sampled blocks or points of sampled blocks, by pass).
+struct BatchItem {
+  int32_t field;
+  int32_t pad;
+  long long begin, end;
+};
+
 // Grid bounds computed once per context from the occupancy calculator.
 struct LaunchCfg {
   int num_sms;
@@ -110,6 +136,13 @@ enum KernelId {
   K_FINISH,
   K_ZFP_INSPECT,
   K_SZ_INSPECT,
+  K_B_RESET,
+  K_B_RANGE,
+  K_B_ZFP,
+  K_B_SZ,
+  K_B_PREP,
+  K_B_FINAL,
+  K_B_TRUTH,
   K_COUNT
 };
 
@@ -124,8 +157,8 @@ enum PassFlags : int {
 enum DeltaMode { DELTA_FROM_MSE = 0, DELTA_EXPLICIT = 1, DELTA_FROM_EB_SZ = 2 };
 
 // ---- launchers (each returns the cudaError_t of the launch) ----
-// constant tables of a new workspace (once, before its first call)
-cudaError_t launch_init_tables(Workspace* ws, cudaStream_t s);
+// the table v log2 v (v < 2^16) of the entropy sums, kNsym doubles (once)
+cudaError_t launch_init_tables(double* xlogx, cudaStream_t s);
 cudaError_t launch_reset(Workspace* ws, cudaStream_t s);
 cudaError_t launch_range(const FieldDev& f, Workspace* ws, int ctas, cudaStream_t s);
 cudaError_t launch_prepare(const ParamsDev& p, Workspace* ws, cudaStream_t s);
@@ -143,8 +176,8 @@ cudaError_t launch_sz_gt(const FieldDev& f, const ParamsDev& p, int with_est,
 // bit 1 = ground truth); launch_code_stats issues both.  prepare_code_stats()
 // once per device first.
 cudaError_t launch_code_prep(Workspace* ws, int which_mask, cudaStream_t s);
-cudaError_t launch_huffman(Workspace* ws, int which_mask, cudaStream_t s);
-cudaError_t launch_code_stats(Workspace* ws, int which_mask, cudaStream_t s);
+cudaError_t launch_huffman(Workspace* ws, int which_mask, const double* xlogx, cudaStream_t s);
+cudaError_t launch_code_stats(Workspace* ws, int which_mask, const double* xlogx, cudaStream_t s);
 cudaError_t prepare_code_stats();
 cudaError_t launch_finish(const ParamsDev& p, Workspace* ws, int passes,
                           int zfp_parts, int sz_parts, long long npoints_all,
@@ -162,6 +195,29 @@ cudaError_t prepare_sz_march();
 cudaError_t launch_sz_march(const FieldDev& f, const ParamsDev& p, int with_est, Workspace* ws,
                             int num_sms, cudaStream_t s, int* grid_used);
 int zfp_occupancy(int d, int num_sms);
+
+// ---- batched estimate (rd_select_batch): persistent passes over work items
+// of all fields; CTAs stride over the items in order ----
+cudaError_t launch_batch_reset(const BatchField* bf, int n, int need_gt, cudaStream_t s);
+// range + (last item of a field) prepare
+cudaError_t launch_batch_range(const BatchField* bf, const BatchItem* items, int nitems, int ctas,
+                               cudaStream_t s);
+// sampled ZFP blocks + (last item of a field) the bin width delta
+cudaError_t launch_batch_zfp_est(const BatchField* bf, const BatchItem* items, int nitems, int ctas,
+                                 cudaStream_t s);
+cudaError_t launch_batch_sz_est(const BatchField* bf, const BatchItem* items, int nitems, int ctas,
+                                cudaStream_t s);
+cudaError_t launch_batch_code_prep(const BatchField* bf, int n, cudaStream_t s);
+// Huffman cost, entropy and finish of every field; result records and
+// statuses gathered into res[n] and status[n]
+cudaError_t launch_batch_final(const BatchField* bf, int n, const double* xlogx, rd_result* res,
+                               int32_t* status, cudaStream_t s);
+// ground-truth records and final statuses of a batch, gathered
+cudaError_t launch_batch_truth(const BatchField* bf, int n, rd_truth* truth, int32_t* status,
+                               cudaStream_t s);
+int batch_range_occupancy(int num_sms);
+int batch_zfp_occupancy(int num_sms);
+int batch_sz_occupancy(int num_sms);
 int sz_occupancy(int d, int num_sms);
 
 }  // namespace rdk

@@ -5,6 +5,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "rd_delta.cuh"
 #include "rd_device.cuh"
 
 namespace rdk {
@@ -12,15 +13,20 @@ namespace rdk {
 // ---------------------------------------------------------------------------
 // Reset: zero accumulators and histograms of the workspace.
 // ---------------------------------------------------------------------------
-__global__ void k_reset(Workspace* ws) {
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nth = gridDim.x * blockDim.x;
-  uint32_t* h = &ws->hist[0][0];
-  for (int i = tid; i < 2 * kNsym; i += nth) h[i] = 0u;
-  uint32_t* cc = &ws->count_of[0][0];
-  for (int i = tid; i < 2 * kNsym; i += nth) cc[i] = 0u;
-  uint32_t* pr = &ws->present[0][0];
-  for (int i = tid; i < 2 * (kNsym / 32); i += nth) pr[i] = 0u;
+__device__ void reset_ws(Workspace* ws, int tid, int nth, int which_mask) {
+#pragma unroll 1
+  for (int w = 0; w < 2; w++) {
+    if (!((which_mask >> w) & 1)) continue;
+    uint4* h = reinterpret_cast<uint4*>(ws->hist[w]);
+    uint4* cc = reinterpret_cast<uint4*>(ws->count_of[w]);
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = tid; i < kNsym / 4; i += nth) {
+      h[i] = z;
+      cc[i] = z;
+    }
+    uint32_t* pr = ws->present[w];
+    for (int i = tid; i < kNsym / 32; i += nth) pr[i] = 0u;
+  }
   unsigned long long* lo = ws->sc.mse_lo;
   unsigned long long* hi = ws->sc.mse_hi;
   for (int i = tid; i < kMseBins; i += nth) {
@@ -36,6 +42,7 @@ __global__ void k_reset(Workspace* ws) {
     s.min_key = 0xffffffffu;
     s.max_key = 0u;
     s.nonfinite = 0u;
+    s.done[0] = s.done[1] = 0u;
     s.vmin = s.vmax = s.amax = 0.0f;
     s.w = s.inv = s.tau = 0.0f;
     s.vr = s.eb_abs = s.delta = s.mse_sp = 0.0;
@@ -57,6 +64,10 @@ __global__ void k_reset(Workspace* ws) {
   }
 }
 
+__global__ void k_reset(Workspace* ws) {
+  reset_ws(ws, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, 3);
+}
+
 cudaError_t launch_reset(Workspace* ws, cudaStream_t s) {
   k_reset<<<128, 256, 0, s>>>(ws);
   return cudaGetLastError();
@@ -66,50 +77,47 @@ cudaError_t launch_reset(Workspace* ws, cudaStream_t s) {
 // Value range: min / max over every value, with a non-finite test.  Rows are
 // read as float4 where the pointer allows it.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(512) k_range(const float* __restrict__ x, long long n,
-                                               Workspace* ws) {
+struct RangeAcc {
   unsigned kmin = 0xffffffffu, kmax = 0u, bad = 0u;
-  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long nth = (long long)gridDim.x * blockDim.x;
-  // scalar head up to a 16-byte boundary
-  long long head = (long long)((16u - ((uintptr_t)x & 15u)) & 15u) / 4;
+  __device__ __forceinline__ void add(float v) {
+    const unsigned b = __float_as_uint(v);
+    bad |= ((b & 0x7f800000u) == 0x7f800000u);
+    const unsigned k = float_key(v);
+    kmin = min(kmin, k);
+    kmax = max(kmax, k);
+  }
+};
+
+// Values [begin, end) of x, thread tid of nth: a scalar head up to a 16-byte
+// boundary, float4 loads, a scalar tail.
+__device__ __forceinline__ void range_span(const float* __restrict__ x, long long begin,
+                                           long long end, long long tid, long long nth,
+                                           RangeAcc& acc) {
+  const float* xb = x + begin;
+  const long long n = end - begin;
+  long long head = (long long)((16u - ((uintptr_t)xb & 15u)) & 15u) / 4;
   if (head > n) head = n;
-  if (((uintptr_t)x & 3u) != 0) head = n;  // not even 4-byte aligned: all scalar
-  for (long long i = tid; i < head; i += nth) {
-    float v = x[i];
-    unsigned b = __float_as_uint(v);
-    bad |= ((b & 0x7f800000u) == 0x7f800000u);
-    unsigned k = float_key(v);
-    kmin = min(kmin, k);
-    kmax = max(kmax, k);
-  }
+  if (((uintptr_t)xb & 3u) != 0) head = n;  // not even 4-byte aligned: all scalar
+  for (long long i = tid; i < head; i += nth) acc.add(xb[i]);
   const long long nvec = (n - head) / 4;
-  const float4* x4 = reinterpret_cast<const float4*>(x + head);
+  const float4* x4 = reinterpret_cast<const float4*>(xb + head);
   for (long long i = tid; i < nvec; i += nth) {
-    float4 q = __ldg(x4 + i);
-    float v[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-      unsigned b = __float_as_uint(v[j]);
-      bad |= ((b & 0x7f800000u) == 0x7f800000u);
-      unsigned k = float_key(v[j]);
-      kmin = min(kmin, k);
-      kmax = max(kmax, k);
-    }
+    const float4 q = __ldg(x4 + i);
+    acc.add(q.x);
+    acc.add(q.y);
+    acc.add(q.z);
+    acc.add(q.w);
   }
-  for (long long i = head + nvec * 4 + tid; i < n; i += nth) {
-    float v = x[i];
-    unsigned b = __float_as_uint(v);
-    bad |= ((b & 0x7f800000u) == 0x7f800000u);
-    unsigned k = float_key(v);
-    kmin = min(kmin, k);
-    kmax = max(kmax, k);
-  }
-  // warp, then CTA, then one update per CTA of the shared keys
-  __shared__ unsigned s_min[16], s_max[16], s_bad[16];
-  kmin = __reduce_min_sync(0xffffffffu, kmin);
-  kmax = __reduce_max_sync(0xffffffffu, kmax);
-  bad = __reduce_or_sync(0xffffffffu, bad);
+  for (long long i = head + nvec * 4 + tid; i < n; i += nth) acc.add(xb[i]);
+}
+
+// Warp, then CTA, then one update per CTA of the field's shared keys.  All
+// threads of the CTA call it (up to 1024 threads).
+__device__ __forceinline__ void range_commit(RangeAcc acc, Workspace* ws) {
+  __shared__ unsigned s_min[32], s_max[32], s_bad[32];
+  unsigned kmin = __reduce_min_sync(0xffffffffu, acc.kmin);
+  unsigned kmax = __reduce_max_sync(0xffffffffu, acc.kmax);
+  unsigned bad = __reduce_or_sync(0xffffffffu, acc.bad);
   const int wid = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) {
     s_min[wid] = kmin;
@@ -131,6 +139,15 @@ __global__ void __launch_bounds__(512) k_range(const float* __restrict__ x, long
       if (c) atomicOr(&ws->sc.nonfinite, 1u);
     }
   }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(512) k_range(const float* __restrict__ x, long long n,
+                                               Workspace* ws) {
+  RangeAcc acc;
+  range_span(x, 0, n, (long long)blockIdx.x * blockDim.x + threadIdx.x,
+             (long long)gridDim.x * blockDim.x, acc);
+  range_commit(acc, ws);
 }
 
 cudaError_t launch_range(const FieldDev& f, Workspace* ws, int ctas, cudaStream_t s) {
@@ -144,14 +161,14 @@ cudaError_t launch_range(const FieldDev& f, Workspace* ws, int ctas, cudaStream_
 // Prepare: value range VR, eb_abs (Eq. psnr-sz: eb_rel = eb_abs / VR) and
 // floor(log2 eb_abs) for the ZFP precision rule.
 // ---------------------------------------------------------------------------
-__global__ void k_prepare(ParamsDev p, Workspace* ws) {
+__device__ __forceinline__ void prepare_field(const ParamsDev& p, Workspace* ws) {
   Scalars& s = ws->sc;
-  if (s.nonfinite) {
+  if (__ldcg(&s.nonfinite)) {
     s.status = RD_ERR_NONFINITE;
     return;
   }
-  s.vmin = key_float(s.min_key);
-  s.vmax = key_float(s.max_key);
+  s.vmin = key_float(__ldcg(&s.min_key));
+  s.vmax = key_float(__ldcg(&s.max_key));
   s.amax = fmaxf(fabsf(s.vmin), fabsf(s.vmax));
   s.vr = (double)s.vmax - (double)s.vmin;
   s.eb_abs = (p.eb_mode == RD_EB_REL) ? p.eb * s.vr : p.eb;
@@ -174,172 +191,17 @@ __global__ void k_prepare(ParamsDev p, Workspace* ws) {
   ws->res.minexp = s.minexp;
 }
 
+__global__ void k_prepare(ParamsDev p, Workspace* ws) { prepare_field(p, ws); }
+
 cudaError_t launch_prepare(const ParamsDev& p, Workspace* ws, cudaStream_t s) {
   k_prepare<<<1, 1, 0, s>>>(p, ws);
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// Bin width.  MSE_sp is the exact sum of (2^d d)^2 4^(emax-30) over the
-// EC-sampled coefficients, held as 64-bit limbs with the least significant
-// bit at 2^-312 and rounded once to nearest-even; delta = sqrt(12 MSE_sp)
-// (PSNR_sz = PSNR_zfp in Eq. psnr-pdf-linear), clamped to 2 eb_abs.
-// ---------------------------------------------------------------------------
-constexpr int kLimbs = 12;  // 768 bits
-
-// Round the limb integer times 2^-312 to the nearest double (ties to even):
-// the 53 bits below the leading one, a round bit and a sticky bit.  Every
-// limb index is a compile-time constant, so the limbs stay in registers.
-__device__ __forceinline__ double limbs_to_double(const unsigned long long (&a)[kLimbs]) {
-  // rolling window (w2, w1, w0) = limbs i, i-1, i-2 and the OR of the
-  // limbs below it, captured at the highest nonzero limb
-  unsigned long long w2 = 0ull, w1 = 0ull, w0 = 0ull;
-  bool bl = false;
-  unsigned long long h = 0ull, m = 0ull, l = 0ull;
-  bool below = false;
-  int ti = -1;
-#pragma unroll
-  for (int i = 0; i < kLimbs; i++) {
-    bl = bl || (w0 != 0ull);
-    w0 = w1;
-    w1 = w2;
-    w2 = a[i];
-    if (w2) {
-      h = w2;
-      m = w1;
-      l = w0;
-      below = bl;
-      ti = i;
-    }
-  }
-  if (ti < 0) return 0.0;
-  // normalise the 192-bit window h:m:l so that bit 63 of h is the leading one
-  const int lz = __clzll((long long)h);
-  if (lz) {
-    h = (h << lz) | (m >> (64 - lz));
-    m = (m << lz) | (l >> (64 - lz));
-    l <<= lz;
-  }
-  unsigned long long mant = h >> 11;  // 53 bits
-  const bool round = (h >> 10) & 1ull;
-  const bool sticky = (h & 0x3ffull) || m || l || below;
-  if (round && (sticky || (mant & 1ull))) mant += 1ull;  // 2^53 stays exact
-  const int lead = ti * 64 + 63 - lz;  // bit index of the leading one
-  return ldexp((double)mant, lead - 52 - 312);
-}
-
-// Launched with one warp.  Bin i holds a 128-bit sum at bit offset 2i, so
-// the bins of lane l (i = l + 32k) all sit at shift 2l within limb k: each
-// lane adds its bins as one multi-limb integer, shifts it by 2l, and a
-// butterfly adds the 32 integers (exact, so the order does not matter).
-// The logarithms of the PSNRs run in separate lanes.
+// Bin width delta (Algorithm 1 line 7): one warp.
 __global__ void k_delta(ParamsDev p, Workspace* ws, int mode, double arg, int need_quant,
                         int need_gt, unsigned long long ncoeff, unsigned long long npoints) {
-  Scalars& s = ws->sc;
-  if (s.status != RD_OK || s.constant) return;
-  rd_result& r = ws->res;
-  const int lane = threadIdx.x;
-  double delta, mse_sp = 0.0;
-  bool clamped = false;
-  if (mode == DELTA_FROM_MSE) {
-    unsigned long long acc[kLimbs];
-    unsigned long long lo[9], hi[9];
-#pragma unroll
-    for (int k = 0; k < 9; k++) {
-      const int i = lane + 32 * k;
-      lo[k] = i < kMseBins ? s.mse_lo[i] : 0ull;
-      hi[k] = i < kMseBins ? s.mse_hi[i] : 0ull;
-    }
-    unsigned long long carry = 0ull;
-#pragma unroll
-    for (int k = 0; k < 10; k++) {
-      const unsigned long long a0 = k < 9 ? lo[k] : 0ull;
-      const unsigned long long a1 = k >= 1 ? hi[k - 1] : 0ull;
-      const unsigned long long t = a0 + a1;
-      const unsigned long long c1 = t < a0;
-      const unsigned long long u = t + carry;
-      const unsigned long long c2 = u < carry;
-      acc[k] = u;
-      carry = c1 + c2;
-    }
-    acc[10] = carry;
-    acc[11] = 0ull;
-    const int sh = 2 * lane;
-    if (sh) {
-#pragma unroll
-      for (int j = kLimbs - 1; j > 0; j--) acc[j] = (acc[j] << sh) | (acc[j - 1] >> (64 - sh));
-      acc[0] <<= sh;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      unsigned long long c = 0ull;
-#pragma unroll
-      for (int j = 0; j < kLimbs; j++) {
-        const unsigned long long t = __shfl_xor_sync(0xffffffffu, acc[j], o);
-        const unsigned long long u = acc[j] + t;
-        const unsigned long long c1 = u < t;
-        const unsigned long long v = u + c;
-        const unsigned long long c2 = v < c;
-        acc[j] = v;
-        c = c1 + c2;
-      }
-    }
-    mse_sp = limbs_to_double(acc) / (double)ncoeff;
-    if (mse_sp == 0.0) {
-      delta = 2.0 * s.eb_abs;
-    } else {
-      delta = sqrt(12.0 * mse_sp);
-      clamped = delta > 2.0 * s.eb_abs;
-      if (clamped) delta = 2.0 * s.eb_abs;
-    }
-  } else if (mode == DELTA_EXPLICIT) {
-    delta = arg > 0.0 ? arg : 2.0 * s.eb_abs;
-  } else {
-    delta = 2.0 * arg;
-  }
-  // lane 0: log10 VR, lane 1: log10 MSE_sp, lane 2: log10 (VR / delta),
-  // lane 3: log10 12
-  const double larg = lane == 0 ? s.vr : lane == 1 ? mse_sp : lane == 2 ? s.vr / delta : 12.0;
-  const double lg = log10(larg);
-  const double l_vr = __shfl_sync(0xffffffffu, lg, 0);
-  const double l_mse = __shfl_sync(0xffffffffu, lg, 1);
-  const double l_vd = __shfl_sync(0xffffffffu, lg, 2);
-  const double l_12 = __shfl_sync(0xffffffffu, lg, 3);
-  if (lane != 0) return;
-  if (mode == DELTA_FROM_MSE) {
-    s.mse_sp = mse_sp;
-    r.mse_sp = mse_sp;
-    r.zfp_s2 = s.s2;
-    r.br_zfp = (double)s.s2 / (2.0 * (double)npoints);
-    r.psnr_zfp = mse_sp > 0.0 ? 20.0 * l_vr - 10.0 * l_mse : INFINITY;
-    if (mse_sp == 0.0) s.flags |= RD_F_MSE_ZERO;
-    if (clamped) s.flags |= RD_F_DELTA_CLAMPED;
-  }
-  s.delta = delta;
-  r.delta = delta;
-  r.psnr_sz = 20.0 * l_vd + 10.0 * l_12;
-  if (!need_quant) return;
-  // float quantiser: w = float(delta), 1/w, and tau = the largest float not
-  // above (delta / 2)(1 - 2^-23), so that a float |x - xhat| <= tau proves
-  // |x - xhat| <= delta / 2
-  float w = (float)delta;
-  if (!(w >= 1.17549435e-38f) || isinf(w)) {
-    s.status = RD_ERR_RANGE;
-    return;
-  }
-  float inv = __fdiv_rn(1.0f, w);
-  if (isinf(inv) || !(inv >= 1.17549435e-38f)) {
-    s.status = RD_ERR_RANGE;
-    return;
-  }
-  double t = (delta / 2.0) * (1.0 - 1.1920928955078125e-07);
-  float tau = __double2float_rz(t);
-  s.w = w;
-  s.inv = inv;
-  s.tau = tau;
-  if (need_gt) {
-    if (__fmul_rn(s.amax, inv) > 134217728.0f) s.status = RD_ERR_RANGE;
-  }
+  delta_warp(p, ws, mode, arg, need_quant, need_gt, ncoeff, npoints);
 }
 
 cudaError_t launch_delta(const ParamsDev& p, Workspace* ws, int mode, double arg, int need_quant,
@@ -486,15 +348,15 @@ __device__ __forceinline__ void warp_count_below2(const uint32_t* a, uint32_t na
 }
 
 // ---------------------------------------------------------------------------
-// Table of v log2 v for the entropy (v < 2^16), filled once per workspace.
+// Table of v log2 v for the entropy (v < 2^16), filled once per context.
 // ---------------------------------------------------------------------------
-__global__ void k_init_xlogx(Workspace* ws) {
+__global__ void k_init_xlogx(double* xlogx) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v < kNsym) ws->xlogx[v] = v > 1 ? (double)v * log2((double)v) : 0.0;
+  if (v < kNsym) xlogx[v] = v > 1 ? (double)v * log2((double)v) : 0.0;
 }
 
-cudaError_t launch_init_tables(Workspace* ws, cudaStream_t s) {
-  k_init_xlogx<<<kNsym / 256, 256, 0, s>>>(ws);
+cudaError_t launch_init_tables(double* xlogx, cudaStream_t s) {
+  k_init_xlogx<<<kNsym / 256, 256, 0, s>>>(xlogx);
   return cudaGetLastError();
 }
 
@@ -505,12 +367,9 @@ cudaError_t launch_init_tables(Workspace* ws, cudaStream_t s) {
 // count values present, and the counts of 2^16 or more (at most N / 2^16 of
 // them) appended to a list, with their share c log2 c of the entropy sum.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kPrepThreads) k_code_prep(Workspace* ws, int which_mask) {
+__device__ __forceinline__ void code_prep_slice(Workspace* ws, int which, int slice) {
   __shared__ double part[kPrepThreads / 32];
   if (ws->sc.status != RD_OK || ws->sc.constant) return;
-  const int first = (which_mask & 1) ? 0 : 1;
-  const int which = first + blockIdx.x / kEntropyCtas;
-  const int slice = blockIdx.x % kEntropyCtas;
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   uint32_t* cc = ws->count_of[which];
@@ -548,6 +407,11 @@ __global__ void __launch_bounds__(kPrepThreads) k_code_prep(Workspace* ws, int w
     const double t = warp_sum(threadIdx.x < kPrepThreads / 32 ? part[threadIdx.x] : 0.0);
     if (threadIdx.x == 0) ws->ent_part[which][slice] = t;
   }
+}
+
+__global__ void __launch_bounds__(kPrepThreads) k_code_prep(Workspace* ws, int which_mask) {
+  const int first = (which_mask & 1) ? 0 : 1;
+  code_prep_slice(ws, first + blockIdx.x / kEntropyCtas, blockIdx.x % kEntropyCtas);
 }
 
 // Block-wide scans and sums for kHuffThreads threads (32 warps); s_w holds
@@ -639,13 +503,12 @@ __device__ double block_sum_f64(double v, double* s_w) {
 //     contiguous runs of the merged order (nodes are written only above the
 //     queue tail, which no thread reads until the next barrier).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kHuffThreads) k_huffman(Workspace* ws, int which0) {
+__device__ void huffman_cta(Workspace* ws, int which, const double* __restrict__ xlogx) {
   extern __shared__ uint32_t s_dyn[];
   __shared__ uint32_t s_w[32];
   __shared__ unsigned long long s_w64[32];
   __shared__ double s_wd[32];
   if (ws->sc.status != RD_OK || ws->sc.constant) return;
-  const int which = which0 + blockIdx.x;
   const int tid = threadIdx.x;
   const uint32_t* cc = ws->count_of[which];
 
@@ -676,7 +539,7 @@ __global__ void __launch_bounds__(kHuffThreads) k_huffman(Workspace* ws, int whi
     for (int u = 0; u < 4; u++) {
       const uint32_t d = d0 + (uint32_t)u * kHuffThreads;
       mm[u] = d < D ? cc[vv[u]] : 0u;
-      xl[u] = d < D ? ws->xlogx[vv[u]] : 0.0;
+      xl[u] = d < D ? xlogx[vv[u]] : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < 4; u++) {
@@ -806,28 +669,40 @@ __global__ void __launch_bounds__(kHuffThreads) k_huffman(Workspace* ws, int whi
   }
 }
 
+__global__ void __launch_bounds__(kHuffThreads) k_huffman(Workspace* ws, int which0,
+                                                          const double* xlogx) {
+  huffman_cta(ws, which0 + blockIdx.x, xlogx);
+}
+
 cudaError_t launch_code_prep(Workspace* ws, int which_mask, cudaStream_t s) {
   const int nh = (which_mask == 3) ? 2 : 1;
   k_code_prep<<<nh * kEntropyCtas, kPrepThreads, 0, s>>>(ws, which_mask);
   return cudaGetLastError();
 }
 
-cudaError_t launch_huffman(Workspace* ws, int which_mask, cudaStream_t s) {
+cudaError_t launch_huffman(Workspace* ws, int which_mask, const double* xlogx, cudaStream_t s) {
   const int smem = 2 * kHuffSmemKeys * (int)sizeof(uint32_t);
   const int nh = (which_mask == 3) ? 2 : 1;
-  k_huffman<<<nh, kHuffThreads, smem, s>>>(ws, (which_mask & 1) ? 0 : 1);
+  k_huffman<<<nh, kHuffThreads, smem, s>>>(ws, (which_mask & 1) ? 0 : 1, xlogx);
   return cudaGetLastError();
 }
 
-cudaError_t launch_code_stats(Workspace* ws, int which_mask, cudaStream_t s) {
+cudaError_t launch_code_stats(Workspace* ws, int which_mask, const double* xlogx, cudaStream_t s) {
   cudaError_t e = launch_code_prep(ws, which_mask, s);
-  if (e == cudaSuccess) e = launch_huffman(ws, which_mask, s);
+  if (e == cudaSuccess) e = launch_huffman(ws, which_mask, xlogx, s);
   return e;
 }
 
+__global__ void __launch_bounds__(kHuffThreads) k_batch_final(const BatchField* __restrict__ bf,
+                                                              const double* __restrict__ xlogx,
+                                                              rd_result* res, int32_t* status);
+
 cudaError_t prepare_code_stats() {
   const int smem = 2 * kHuffSmemKeys * (int)sizeof(uint32_t);
-  return cudaFuncSetAttribute(k_huffman, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(k_huffman, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_batch_final, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return e;
 }
 
 // ---------------------------------------------------------------------------
@@ -852,11 +727,9 @@ __device__ double block_sum_parts(const double* a, int n, double* red) {
   return t;
 }
 
-__global__ void __launch_bounds__(kFinishThreads) k_finish(ParamsDev p, Workspace* ws, int passes,
-                                                           int zfp_parts, int sz_parts,
-                                                           long long npoints_all,
-                                                           unsigned long long zfp_npoints) {
-  __shared__ double red[kFinishThreads / 32];
+__device__ void finish_cta(const ParamsDev& p, Workspace* ws, int passes, int zfp_parts,
+                           int sz_parts, long long npoints_all, unsigned long long zfp_npoints) {
+  __shared__ double red[32];
   Scalars& s = ws->sc;
   if (s.status != RD_OK) return;
   rd_result& r = ws->res;
@@ -950,10 +823,123 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(ParamsDev p, Workspac
   t.flags = s.flags & (RD_F_DELTA_CLAMPED | RD_F_MSE_ZERO | RD_F_CONSTANT);
 }
 
+__global__ void __launch_bounds__(kFinishThreads) k_finish(ParamsDev p, Workspace* ws, int passes,
+                                                           int zfp_parts, int sz_parts,
+                                                           long long npoints_all,
+                                                           unsigned long long zfp_npoints) {
+  finish_cta(p, ws, passes, zfp_parts, sz_parts, npoints_all, zfp_npoints);
+}
+
 cudaError_t launch_finish(const ParamsDev& p, Workspace* ws, int passes, int zfp_parts,
                           int sz_parts, long long npoints_all, unsigned long long zfp_npoints,
                           cudaStream_t s) {
   k_finish<<<1, kFinishThreads, 0, s>>>(p, ws, passes, zfp_parts, sz_parts, npoints_all, zfp_npoints);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Batched estimate (rd_select_batch): the passes of this file over many
+// fields.  Range work items are runs of values of one field; the CTA that
+// finishes a field's last item (a counter in the field's workspace, with
+// fences on both sides) computes VR, eb_abs and the precision exponent.
+// The final pass runs one CTA per field: Huffman cost and entropy, then the
+// rates, PSNRs and selection, and gathers the field's record and status.
+// ---------------------------------------------------------------------------
+constexpr int kBatchRangeThreads = 512;
+
+__global__ void k_batch_reset(const BatchField* __restrict__ bf, int need_gt) {
+  const BatchField& F = bf[blockIdx.x];
+  reset_ws(F.ws, blockIdx.y * blockDim.x + threadIdx.x, gridDim.y * blockDim.x, need_gt ? 3 : 1);
+}
+
+cudaError_t launch_batch_reset(const BatchField* bf, int n, int need_gt, cudaStream_t s) {
+  k_batch_reset<<<dim3(n, 8), 256, 0, s>>>(bf, need_gt);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kBatchRangeThreads) k_batch_range(const BatchField* __restrict__ bf,
+                                                                    const BatchItem* __restrict__ items,
+                                                                    int nitems) {
+  __shared__ int s_last;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const BatchItem item = items[it];
+    const BatchField& F = bf[item.field];
+    RangeAcc acc;
+    range_span(F.f.x, item.begin, item.end, threadIdx.x, blockDim.x, acc);
+    range_commit(acc, F.ws);
+    if (threadIdx.x == 0) {
+      __threadfence();
+      s_last = atomicAdd(&F.ws->sc.done[0], 1u) == F.items_range - 1u;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+      __threadfence();
+      prepare_field(F.p, F.ws);
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_batch_range(const BatchField* bf, const BatchItem* items, int nitems, int ctas,
+                               cudaStream_t s) {
+  int g = nitems < ctas ? nitems : ctas;
+  if (g < 1) g = 1;
+  k_batch_range<<<g, kBatchRangeThreads, 0, s>>>(bf, items, nitems);
+  return cudaGetLastError();
+}
+
+int batch_range_occupancy(int num_sms) {
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void*)k_batch_range, kBatchRangeThreads,
+                                                    0) != cudaSuccess ||
+      per < 1)
+    per = 1;
+  return per * num_sms;
+}
+
+__global__ void __launch_bounds__(kPrepThreads) k_batch_code_prep(const BatchField* __restrict__ bf) {
+  code_prep_slice(bf[blockIdx.x / kEntropyCtas].ws, 0, blockIdx.x % kEntropyCtas);
+}
+
+cudaError_t launch_batch_code_prep(const BatchField* bf, int n, cudaStream_t s) {
+  k_batch_code_prep<<<n * kEntropyCtas, kPrepThreads, 0, s>>>(bf);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kHuffThreads) k_batch_final(const BatchField* __restrict__ bf,
+                                                              const double* __restrict__ xlogx,
+                                                              rd_result* res, int32_t* status) {
+  const BatchField& F = bf[blockIdx.x];
+  Workspace* ws = F.ws;
+  huffman_cta(ws, 0, xlogx);
+  __syncthreads();
+  finish_cta(F.p, ws, P_ZFP_EST | P_SZ_EST, 0, 0, F.f.N, F.npoints);
+  __syncthreads();
+  // gather the record (word-wise) and the status
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(&ws->res);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(&res[blockIdx.x]);
+  for (int i = threadIdx.x; i < (int)(sizeof(rd_result) / 4); i += blockDim.x) dst[i] = src[i];
+  if (threadIdx.x == 0) status[blockIdx.x] = ws->sc.status;
+}
+
+cudaError_t launch_batch_final(const BatchField* bf, int n, const double* xlogx, rd_result* res,
+                               int32_t* status, cudaStream_t s) {
+  const int smem = 2 * kHuffSmemKeys * (int)sizeof(uint32_t);
+  k_batch_final<<<n, kHuffThreads, smem, s>>>(bf, xlogx, res, status);
+  return cudaGetLastError();
+}
+
+__global__ void k_batch_truth(const BatchField* __restrict__ bf, rd_truth* truth, int32_t* status) {
+  const Workspace* ws = bf[blockIdx.x].ws;
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(&ws->truth);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(&truth[blockIdx.x]);
+  for (int i = threadIdx.x; i < (int)(sizeof(rd_truth) / 4); i += blockDim.x) dst[i] = src[i];
+  if (threadIdx.x == 0) status[blockIdx.x] = ws->sc.status;
+}
+
+cudaError_t launch_batch_truth(const BatchField* bf, int n, rd_truth* truth, int32_t* status,
+                               cudaStream_t s) {
+  k_batch_truth<<<n, 64, 0, s>>>(bf, truth, status);
   return cudaGetLastError();
 }
 

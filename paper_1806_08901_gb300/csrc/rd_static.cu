@@ -27,18 +27,21 @@ using namespace rdk;
 
 namespace {
 
-// Stated maximum of the fixed scratch: 3.25 MiB per device, held for the
-// life of the process by every GPU that loads the library.
-constexpr size_t kStaticScratchBytes = 3407872;
+// Stated maximum of the fixed scratch: 2.75 MiB per device (plus the 0.5 MiB
+// entropy table), held for the life of the process by every GPU that loads
+// the library.
+constexpr size_t kStaticScratchBytes = 2883584;
 static_assert(sizeof(Workspace) <= kStaticScratchBytes, "workspace exceeds the static scratch");
 
 static __device__ __align__(256) unsigned char g_select_scratch[kStaticScratchBytes];
+static __device__ double g_xlogx[kNsym];  // v log2 v table of the entropy sums
 
 constexpr int kMaxDevices = 64;
 
 struct DeviceSlot {
   bool ready;
   Workspace* ws;  // device address of g_select_scratch on that device
+  double* xlogx;  // device address of g_xlogx
   int range_ctas;
   int zfp_ctas[4];
   int sz_ctas[4];
@@ -57,11 +60,14 @@ int setup_device(int dev, DeviceSlot** out) {
   if (!s.ready) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_select_scratch) != cudaSuccess || !p) return RD_ERR_CUDA;
+    void* tx = nullptr;
+    if (cudaGetSymbolAddress(&tx, g_xlogx) != cudaSuccess || !tx) return RD_ERR_CUDA;
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return RD_ERR_CUDA;
     if (prepare_code_stats() != cudaSuccess) return RD_ERR_CUDA;
     s.ws = static_cast<Workspace*>(p);
-    if (launch_init_tables(s.ws, 0) != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess)
+    s.xlogx = static_cast<double*>(tx);
+    if (launch_init_tables(s.xlogx, 0) != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess)
       return RD_ERR_CUDA;
     s.range_ctas = sms * 4;
     for (int d = 1; d <= 3; d++) {
@@ -174,7 +180,7 @@ extern "C" int32_t rd_select_static(const rd_field* fld, const rd_params* prm, r
   if (e == cudaSuccess) e = launch_zfp(f, p, P_ZFP_EST, ws, slot->zfp_ctas[d], s, &zparts);
   if (e == cudaSuccess) e = launch_delta(p, ws, DELTA_FROM_MSE, 0.0, 1, 0, ncoeff, npts, s);
   if (e == cudaSuccess) e = launch_sz_est(f, p, ws, slot->sz_ctas[d], s);
-  if (e == cudaSuccess) e = launch_code_stats(ws, 1, s);
+  if (e == cudaSuccess) e = launch_code_stats(ws, 1, slot->xlogx, s);
   if (e == cudaSuccess) e = launch_finish(p, ws, passes, zparts, 0, f.N, npts, s);
   rd_result r;
   int32_t status = RD_OK;

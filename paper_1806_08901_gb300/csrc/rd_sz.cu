@@ -99,6 +99,27 @@ __device__ __forceinline__ bool in_sampled_block(const FieldDev& f, const int* g
 // ---------------------------------------------------------------------------
 // Estimator over the points of sampled blocks only.
 // ---------------------------------------------------------------------------
+// Point u of the sampled blocks (u / 4^D = sampled block in lattice order,
+// u % 4^D = offset in the block, last axis fastest): its coordinates, and
+// whether it lies inside the field.
+template <int D>
+__device__ __forceinline__ bool sampled_point(const FieldDev& f, long long u, int* g) {
+  constexpr int NB = 1 << (2 * D);
+  const long long sb = u / NB;
+  const int t = (int)(u % NB);
+  long long r = sb;
+  bool ok = true;
+#pragma unroll
+  for (int k = D - 1; k >= 0; k--) {
+    int l = (int)(r % f.L[k]);
+    r /= f.L[k];
+    int tk = (t >> (2 * (D - 1 - k))) & 3;
+    g[k] = 4 * l * f.s[k] + tk;
+    ok = ok && g[k] < f.n[k];
+  }
+  return ok;
+}
+
 template <int D>
 __global__ void __launch_bounds__(kSzThreads) k_sz_est(FieldDev f, ParamsDev p, Workspace* ws) {
   constexpr int NB = 1 << (2 * D);
@@ -112,21 +133,8 @@ __global__ void __launch_bounds__(kSzThreads) k_sz_est(FieldDev f, ParamsDev p, 
   for (long long u0 = (long long)blockIdx.x * blockDim.x; u0 < units;
        u0 += (long long)gridDim.x * blockDim.x) {
     const long long u = u0 + threadIdx.x;
-    bool ok = u < units;
     int g[3] = {0, 0, 0};
-    if (ok) {
-      long long sb = u / NB;
-      int t = (int)(u % NB);
-      long long r = sb;
-#pragma unroll
-      for (int k = D - 1; k >= 0; k--) {
-        int l = (int)(r % f.L[k]);
-        r /= f.L[k];
-        int tk = (t >> (2 * (D - 1 - k))) & 3;
-        g[k] = 4 * l * f.s[k] + tk;
-        ok = ok && g[k] < f.n[k];
-      }
-    }
+    const bool ok = u < units && sampled_point<D>(f, u, g);
     const unsigned mask = __ballot_sync(0xffffffffu, ok);
     if (ok) {
       Nbr c = gather_cell<D>(f, g);
@@ -257,6 +265,66 @@ int sz_occupancy(int d, int num_sms) {
     per = 1;
   long long g = (long long)per * num_sms;
   return (int)(g > kMaxGrid ? kMaxGrid : g);
+}
+
+// ---------------------------------------------------------------------------
+// Batched estimate: points of the sampled blocks of many fields.  Each work
+// item is a run of points of one field; its histogram window lives in
+// shared memory and is added to the field's histogram when the item ends.
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ void sz_est_item(const FieldDev& f, int R, float inv, uint32_t* g_hist,
+                                            long long u0, long long u1, uint32_t* s_win) {
+  for (long long b0 = u0; b0 < u1; b0 += blockDim.x) {
+    const long long u = b0 + threadIdx.x;
+    int g[3] = {0, 0, 0};
+    const bool ok = u < u1 && sampled_point<D>(f, u, g);
+    const unsigned mask = __ballot_sync(0xffffffffu, ok);
+    if (ok) {
+      Nbr c = gather_cell<D>(f, g);
+      hist_add(s_win, g_hist, est_symbol(est_residual<D>(c), inv, R), mask);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kSzThreads) k_batch_sz_est(const BatchField* __restrict__ bf,
+                                                             const BatchItem* __restrict__ items,
+                                                             int nitems) {
+  __shared__ uint32_t s_win[kHistWin];
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const BatchItem item = items[it];
+    const BatchField& F = bf[item.field];
+    Workspace* ws = F.ws;
+    if (ws->sc.status != RD_OK || ws->sc.constant) continue;  // uniform over the CTA
+    for (int i = threadIdx.x; i < kHistWin; i += blockDim.x) s_win[i] = 0u;
+    __syncthreads();
+    const float inv = ws->sc.inv;
+    switch (F.f.d) {
+      case 1: sz_est_item<1>(F.f, F.p.R, inv, ws->hist[0], item.begin, item.end, s_win); break;
+      case 2: sz_est_item<2>(F.f, F.p.R, inv, ws->hist[0], item.begin, item.end, s_win); break;
+      default: sz_est_item<3>(F.f, F.p.R, inv, ws->hist[0], item.begin, item.end, s_win); break;
+    }
+    __syncthreads();
+    hist_flush(s_win, ws->hist[0]);
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_batch_sz_est(const BatchField* bf, const BatchItem* items, int nitems, int ctas,
+                                cudaStream_t s) {
+  int g = nitems < ctas ? nitems : ctas;
+  if (g < 1) g = 1;
+  k_batch_sz_est<<<g, kSzThreads, 0, s>>>(bf, items, nitems);
+  return cudaGetLastError();
+}
+
+int batch_sz_occupancy(int num_sms) {
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void*)k_batch_sz_est, kSzThreads, 0) !=
+          cudaSuccess ||
+      per < 1)
+    per = 1;
+  return per * num_sms;
 }
 
 // ---------------------------------------------------------------------------

@@ -10,6 +10,7 @@
 //     truncation, inverse transform, reconstruction, SSE and max error.
 #include <stdint.h>
 
+#include "rd_delta.cuh"
 #include "rd_device.cuh"
 
 namespace rdk {
@@ -194,6 +195,60 @@ __device__ __forceinline__ void decode_block(const FieldDev& f, long long u, boo
   }
 }
 
+// Estimator terms of one sampled block (Alg. 1 lines 4-6): the doubled
+// interpolated n_sb sum into s2, and the exact squared truncation errors at
+// the EC-sampled coefficients into the 128-bit bin of the block exponent.
+template <int D>
+__device__ __forceinline__ void zfp_est_accumulate(const BlockWork<D>& w, bool ec_all,
+                                                   unsigned long long& my_s2,
+                                                   unsigned long long* s_lo,
+                                                   unsigned long long* s_hi) {
+  constexpr int NB = 1 << (2 * D);
+  constexpr EcPositions<D> EC{};
+  // n_sb at the sampled positions, interpolated in sequency index
+  auto nsb = [&](int q) {
+    int bb = 31 - __clz((int)w.u[q]);
+    return bb >= w.bi.kmin ? bb - w.bi.kmin + 1 : 0;
+  };
+  long long s2 = 0;
+  unsigned long long lo = 0ull, hi = 0ull;
+  const unsigned keep = w.keep_mask();
+  if (ec_all) {
+#pragma unroll
+    for (int q = 0; q < NB; q++) {
+      s2 += 2 * nsb(q);
+      long long d = (long long)from_negabinary(w.u[q]) - (long long)from_negabinary(w.u[q] & keep);
+      unsigned long long ad = (unsigned long long)(d < 0 ? -d : d);
+      unsigned long long sq = ad * ad;  // |d| < 2^32
+      lo += sq;
+      hi += (lo < sq);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < EcPositions<D>::M; j++) {
+      const int q = EC.pos[j];
+      if (j + 1 < EcPositions<D>::M) {
+        const int L = EC.pos[j + 1] - q;
+        s2 += (long long)(L + 1) * nsb(q) + (long long)(L - 1) * nsb(EC.pos[j + 1]);
+      } else {
+        s2 += 2 * nsb(q);
+      }
+      long long d = (long long)from_negabinary(w.u[q]) - (long long)from_negabinary(w.u[q] & keep);
+      unsigned long long ad = (unsigned long long)(d < 0 ? -d : d);
+      unsigned long long sq = ad * ad;  // |d| < 2^32
+      lo += sq;
+      hi += (lo < sq);
+    }
+  }
+  my_s2 += (unsigned long long)s2;
+  if (!w.bi.all_zero && (lo | hi)) {
+    const int bin = w.bi.emax + D + 126;  // exponent of the 2^d-rescaled error
+    unsigned long long old = atomicAdd(&s_lo[bin], lo);
+    unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+    if (hi + carry) atomicAdd(&s_hi[bin], hi + carry);
+  }
+}
+
 template <int D, bool GT, bool EST>
 __global__ void __launch_bounds__(kZfpThreads) k_zfp(FieldDev f, ParamsDev p, Workspace* ws) {
   constexpr int NB = 1 << (2 * D);
@@ -217,7 +272,6 @@ __global__ void __launch_bounds__(kZfpThreads) k_zfp(FieldDev f, ParamsDev p, Wo
   unsigned long long my_s2 = 0ull, my_bits = 0ull;
   double my_sse = 0.0;
   float my_max = 0.0f;
-  constexpr EcPositions<D> EC{};
   const bool ec_all = p.ec_mode == RD_EC_ALL;
 
   for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < units;
@@ -234,50 +288,7 @@ __global__ void __launch_bounds__(kZfpThreads) k_zfp(FieldDev f, ParamsDev p, Wo
     BlockWork<D> w;
     w.forward(v, minexp);
 
-    if (EST && sampled) {
-      // n_sb at the sampled positions, interpolated in sequency index
-      auto nsb = [&](int q) {
-        int bb = 31 - __clz((int)w.u[q]);
-        return bb >= w.bi.kmin ? bb - w.bi.kmin + 1 : 0;
-      };
-      long long s2 = 0;
-      unsigned long long lo = 0ull, hi = 0ull;
-      const unsigned keep = w.keep_mask();
-      if (ec_all) {
-#pragma unroll
-        for (int q = 0; q < NB; q++) {
-          s2 += 2 * nsb(q);
-          long long d = (long long)from_negabinary(w.u[q]) - (long long)from_negabinary(w.u[q] & keep);
-          unsigned long long ad = (unsigned long long)(d < 0 ? -d : d);
-          unsigned long long sq = ad * ad;  // |d| < 2^32
-          lo += sq;
-          hi += (lo < sq);
-        }
-      } else {
-#pragma unroll
-        for (int j = 0; j < EcPositions<D>::M; j++) {
-          const int q = EC.pos[j];
-          if (j + 1 < EcPositions<D>::M) {
-            const int L = EC.pos[j + 1] - q;
-            s2 += (long long)(L + 1) * nsb(q) + (long long)(L - 1) * nsb(EC.pos[j + 1]);
-          } else {
-            s2 += 2 * nsb(q);
-          }
-          long long d = (long long)from_negabinary(w.u[q]) - (long long)from_negabinary(w.u[q] & keep);
-          unsigned long long ad = (unsigned long long)(d < 0 ? -d : d);
-          unsigned long long sq = ad * ad;  // |d| < 2^32
-          lo += sq;
-          hi += (lo < sq);
-        }
-      }
-      my_s2 += (unsigned long long)s2;
-      if (!w.bi.all_zero && (lo | hi)) {
-        const int bin = w.bi.emax + D + 126;  // exponent of the 2^d-rescaled error
-        unsigned long long old = atomicAdd(&s_lo[bin], lo);
-        unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
-        if (hi + carry) atomicAdd(&s_hi[bin], hi + carry);
-      }
-    }
+    if (EST && sampled) zfp_est_accumulate<D>(w, ec_all, my_s2, s_lo, s_hi);
 
     if (GT) {
       my_bits += w.bits();
@@ -409,6 +420,95 @@ int zfp_occupancy(int d, int num_sms) {
     per = 1;
   long long g = (long long)per * num_sms;
   return (int)(g > kMaxGrid ? kMaxGrid : g);
+}
+
+// ---------------------------------------------------------------------------
+// Batched estimate: sampled blocks of many fields.  Each work item is a run
+// of sampled blocks of one field, accumulated in shared memory and added to
+// the field's exact sums when the item ends; the CTA that finishes a field's
+// last item then derives the bin width delta of that field (one warp).
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ void zfp_est_item(const FieldDev& f, const ParamsDev& p, int minexp,
+                                             long long u0, long long u1,
+                                             unsigned long long& my_s2, unsigned long long* s_lo,
+                                             unsigned long long* s_hi) {
+  constexpr int NB = 1 << (2 * D);
+  const bool ec_all = p.ec_mode == RD_EC_ALL;
+  for (long long u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
+    int b[3] = {0, 0, 0};
+    decode_block<D>(f, u, true, b);
+    float v[NB];
+    load_block<D>(f, b, v);
+    BlockWork<D> w;
+    w.forward(v, minexp);
+    zfp_est_accumulate<D>(w, ec_all, my_s2, s_lo, s_hi);
+  }
+}
+
+__global__ void __launch_bounds__(kZfpThreads) k_batch_zfp_est(const BatchField* __restrict__ bf,
+                                                               const BatchItem* __restrict__ items,
+                                                               int nitems) {
+  __shared__ unsigned long long s_lo[kMseBins], s_hi[kMseBins];
+  __shared__ unsigned long long s_s2;
+  __shared__ int s_last;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const BatchItem item = items[it];
+    const BatchField& F = bf[item.field];
+    Workspace* ws = F.ws;
+    const bool live = ws->sc.status == RD_OK && !ws->sc.constant;
+    for (int i = threadIdx.x; i < kMseBins; i += blockDim.x) {
+      s_lo[i] = 0ull;
+      s_hi[i] = 0ull;
+    }
+    if (threadIdx.x == 0) s_s2 = 0ull;
+    __syncthreads();
+    if (live) {
+      unsigned long long my_s2 = 0ull;
+      const int minexp = ws->sc.minexp;
+      switch (F.f.d) {
+        case 1: zfp_est_item<1>(F.f, F.p, minexp, item.begin, item.end, my_s2, s_lo, s_hi); break;
+        case 2: zfp_est_item<2>(F.f, F.p, minexp, item.begin, item.end, my_s2, s_lo, s_hi); break;
+        default: zfp_est_item<3>(F.f, F.p, minexp, item.begin, item.end, my_s2, s_lo, s_hi); break;
+      }
+      my_s2 = warp_sum(my_s2);
+      if ((threadIdx.x & 31) == 0 && my_s2) atomicAdd(&s_s2, my_s2);
+    }
+    __syncthreads();
+    if (live) {
+      if (threadIdx.x == 0 && s_s2) atomicAdd(&ws->sc.s2, s_s2);
+      for (int i = threadIdx.x; i < kMseBins; i += blockDim.x)
+        if (s_lo[i] | s_hi[i]) atomic_add_u128(&ws->sc.mse_lo[i], &ws->sc.mse_hi[i], s_lo[i], s_hi[i]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      s_last = atomicAdd(&ws->sc.done[1], 1u) == F.items_zfp - 1u;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x < 32) {
+      __threadfence();
+      delta_warp(F.p, ws, DELTA_FROM_MSE, 0.0, 1, F.need_gt, F.ncoeff, F.npoints);
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_batch_zfp_est(const BatchField* bf, const BatchItem* items, int nitems, int ctas,
+                                 cudaStream_t s) {
+  int g = nitems < ctas ? nitems : ctas;
+  if (g < 1) g = 1;
+  k_batch_zfp_est<<<g, kZfpThreads, 0, s>>>(bf, items, nitems);
+  return cudaGetLastError();
+}
+
+int batch_zfp_occupancy(int num_sms) {
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void*)k_batch_zfp_est, kZfpThreads, 0) !=
+          cudaSuccess ||
+      per < 1)
+    per = 1;
+  return per * num_sms;
 }
 
 // ---------------------------------------------------------------------------

@@ -76,6 +76,12 @@ class rd_truth(C.Structure):
     ]
 
 
+class rd_batch_config(C.Structure):
+    _fields_ = [("range_values", C.c_int64), ("zfp_blocks", C.c_int32), ("sz_points", C.c_int32),
+                ("range_ctas", C.c_int32), ("zfp_ctas", C.c_int32), ("sz_ctas", C.c_int32),
+                ("tuned", C.c_int32)]
+
+
 # Every symbol include/rdsel.h declares, with its ctypes signature.
 _P = C.POINTER
 _SIGNATURES = {
@@ -90,6 +96,10 @@ _SIGNATURES = {
     "rd_evaluate": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), _P(rd_result),
                                 _P(rd_truth), C.c_void_p]),
     "rd_select_static": (C.c_int32, [_P(rd_field), _P(rd_params), _P(rd_result), C.c_void_p]),
+    "rd_select_batch": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), C.c_int32,
+                                    _P(rd_result), _P(rd_truth), _P(C.c_int32), C.c_void_p]),
+    "rd_batch_set_config": (C.c_int32, [C.c_void_p, _P(rd_batch_config)]),
+    "rd_batch_get_config": (C.c_int32, [C.c_void_p, _P(rd_batch_config)]),
     "rd_copy_histograms": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "rd_zfp_blocks": (C.c_int32, [C.c_void_p, _P(rd_field), C.c_double, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -260,6 +270,51 @@ def rd_evaluate(ctx, field, prm: rd_params, stream=None) -> tuple:
     return _todict(r), _todict(t)
 
 
+def rd_select_batch(ctx, fields, prms, truth: bool = False, stream=None, check: bool = True):
+    """Estimates (and, with truth=True, ground truths) of many device fields
+    in one batched call.  prms: one rd_params for all fields or a list.
+    Returns (results, truths or None, statuses); raises on a call-level
+    error, and on a per-field error when check is true."""
+    n = len(fields)
+    if isinstance(prms, rd_params):
+        prms = [prms] * n
+    if len(prms) != n or n < 1:
+        raise ValueError("one rd_params per field")
+    fs = (rd_field * n)()
+    keep = []
+    for i, x in enumerate(fields):
+        f, k = make_field(x)
+        fs[i] = f
+        keep.append(k)
+    ps = (rd_params * n)(*prms)
+    rs = (rd_result * n)()
+    ts = (rd_truth * n)() if truth else None
+    st = (C.c_int32 * n)()
+    rc = lib().rd_select_batch(ctx, fs, ps, n, rs, ts, st, _stream(stream))
+    statuses = list(st)
+    if rc != RD_OK and (check or all(v == rc for v in statuses)):
+        raise RdselError(rc, "rd_select_batch", status_string(rc))
+    return ([_todict(r) for r in rs], [_todict(t) for t in ts] if truth else None, statuses)
+
+
+def rd_batch_set_config(ctx, cfg=None) -> None:
+    """Force the work split of later batch calls (a dict of rd_batch_config
+    fields, zeros = defaults), or None for the autotuner."""
+    if cfg is None:
+        _check(lib().rd_batch_set_config(ctx, None), "rd_batch_set_config")
+        return
+    c = rd_batch_config()
+    for k, v in cfg.items():
+        setattr(c, k, int(v))
+    _check(lib().rd_batch_set_config(ctx, C.byref(c)), "rd_batch_set_config")
+
+
+def rd_batch_get_config(ctx) -> dict:
+    c = rd_batch_config()
+    _check(lib().rd_batch_get_config(ctx, C.byref(c)), "rd_batch_get_config")
+    return _todict(c)
+
+
 def rd_copy_histograms(ctx) -> tuple:
     est = np.zeros(RD_NSYM, np.uint32)
     gt = np.zeros(RD_NSYM, np.uint32)
@@ -370,6 +425,15 @@ class Context:
 
     def evaluate(self, x, p, stream=None):
         return rd_evaluate(self.h, x, p, stream)
+
+    def select_batch(self, fields, prms, truth=False, stream=None, check=True):
+        return rd_select_batch(self.h, fields, prms, truth, stream, check)
+
+    def batch_set_config(self, cfg=None):
+        rd_batch_set_config(self.h, cfg)
+
+    def batch_get_config(self):
+        return rd_batch_get_config(self.h)
 
     def histograms(self):
         return rd_copy_histograms(self.h)

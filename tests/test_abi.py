@@ -46,7 +46,8 @@ def test_struct_layout_matches_header(rdsel, tmp_path):
     """Compile a probe against include/rdsel.h with the host compiler and
     compare sizeof / offsetof with the ctypes mirrors."""
     structs = {"rd_field": rdsel.rd_field, "rd_params": rdsel.rd_params,
-               "rd_result": rdsel.rd_result, "rd_truth": rdsel.rd_truth}
+               "rd_result": rdsel.rd_result, "rd_truth": rdsel.rd_truth,
+               "rd_batch_config": rdsel.rd_batch_config}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rdsel.h"', "int main(void){"]
     for sname, cls in structs.items():
         lines.append(f'printf("{sname} sizeof %zu\\n", sizeof({sname}));')
