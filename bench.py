@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-planes", type=int, default=100,
                     help="planes of the field in the CPU-baseline sample")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched-snapshot measurement")
+    ap.add_argument("--batch-steps", type=int, default=20)
     return ap.parse_args()
 
 
@@ -142,6 +145,106 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+SNAPSHOT = "snapshot_79x1800x3600_13x100x500x500_6x512^3_f32"
+
+
+def snapshot_alg_bytes(fields, r_sp: float) -> float:
+    """Algorithmic bytes of the estimate: one read of every value (range), the
+    sampled ZFP blocks and the sampled SZ points with their one-cell halo,
+    4 + 4 r + 4 r (5/4)^d bytes per value."""
+    tot = 0.0
+    for x in fields:
+        d = x.dim()
+        tot += x.numel() * (4.0 + 4.0 * r_sp + 4.0 * r_sp * (1.25 ** d))
+    return tot
+
+
+def bench_snapshot(R, ctx, stream, steps: int, peak: float, peak_kind: str):
+    """The batched estimate of a whole snapshot (79 2D 1800x3600, 13
+    100x500x500 and 6 512^3 fields, 6.57 GB, far larger than L2) in one
+    rd_select_batch call, against the same fields through per-field rd_select
+    calls, both timed with CUDA events on the stream."""
+    import ctypes as C
+
+    import torch
+
+    import synth
+
+    specs = synth.snapshot_specs()
+    fields = [synth.make_field_torch(sp) for sp in specs]
+    torch.cuda.synchronize()
+    prms = [R.params(eb=sp["eb_rel"], r_sp=R_SP) for sp in specs]
+    nbytes = sum(4 * x.numel() for x in fields)
+    call = ctx.batch_call(fields, prms)
+    for _ in range(3):  # autotune, capture, replay
+        rc = call.run(stream)
+        if rc != 0:
+            raise R.RdselError(rc, "rd_select_batch", R.status_string(rc))
+    cfg = ctx.batch_get_config()
+    n0 = ctx.launch_count()
+    ms = []
+    for _ in range(steps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        call.run(stream)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    launches = (ctx.launch_count() - n0) / steps
+    batch_ms = statistics.median(ms)
+    res = call.results()
+    # per-kernel device times of the batched launches (a separate profiled plan)
+    ctx.set_profiling(True)
+    for _ in range(3):
+        call.run(stream)
+    ctx.reset_profile()
+    for _ in range(5):
+        call.run(stream)
+    kstats = {k: v[0] / v[1] for k, v in ctx.kernel_stats().items() if v[1] and k.startswith("batch")}
+    ctx.set_profiling(False)
+    # plain: one rd_select per field, arguments marshalled beforehand
+    L = R.lib()
+    recs = []
+    for x, p in zip(fields, prms):
+        f, keep = R.make_field(x)
+        recs.append((f, p, R.rd_result(), keep))
+    sp = R._stream(stream)
+    for _ in range(2):
+        for f, p, r, _k in recs:
+            L.rd_select(ctx.h, C.byref(f), C.byref(p), C.byref(r), sp)
+    pms = []
+    for _ in range(max(3, steps // 4)):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for f, p, r, _k in recs:
+            L.rd_select(ctx.h, C.byref(f), C.byref(p), C.byref(r), sp)
+        b.record(stream)
+        b.synchronize()
+        pms.append(a.elapsed_time(b))
+    plain_ms = statistics.median(pms)
+    same = all(R._todict(r) == g for (_f, _p, r, _k), g in zip(recs, res))
+    alg = snapshot_alg_bytes(fields, R_SP)
+    achieved = alg / (batch_ms / 1e3) / 1e9
+    out = {
+        "workload": SNAPSHOT, "fields": len(fields), "field_bytes": nbytes, "r_sp": R_SP,
+        "eb_rel": "per field from {1e-3,1e-4,1e-5}", "l2": "inputs 6.6 GB, larger than L2",
+        "ms": batch_ms, "value": nbytes / (batch_ms / 1e3) / 1e9, "unit": "GB/s",
+        "plain_ms": plain_ms, "plain_value": nbytes / (plain_ms / 1e3) / 1e9,
+        "speedup_vs_plain": plain_ms / batch_ms, "gpu_launches": launches,
+        "records_equal_plain": same, "split": cfg,
+        "kernel_ms": kstats,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+                     "unit": "GB/s", "frac": achieved / peak, "alg_bytes": alg},
+        "selections": {"sz": sum(1 for r in res if r["selection"] == 0),
+                       "zfp": sum(1 for r in res if r["selection"] == 1)},
+    }
+    del fields, call, recs
+    torch.cuda.empty_cache()
+    return out
 
 
 def cpu_baseline(x_host, planes: int, steps: int = 1):
@@ -325,6 +428,8 @@ def main():
                    "br_sz_gt": truth_ref["br_sz_gt"], "br_zfp_gt": truth_ref["br_zfp_gt"],
                    "psnr_zfp": est_ref["psnr_zfp"], "psnr_zfp_gt": truth_ref["psnr_zfp_gt"]},
     }
+    if not args.no_batch and world == 1:
+        line["batched"] = bench_snapshot(R, ctx, stream, args.batch_steps, peak, peak_kind)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(x.cpu().numpy(), args.cpu_planes, 1)
     if rank == 0:

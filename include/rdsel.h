@@ -199,7 +199,7 @@ int32_t rd_select_static(const rd_field* field, const rd_params* params,
 typedef struct {
   int64_t range_values; /* values per work item of the range pass (multiple of 4) */
   int32_t zfp_blocks;   /* sampled ZFP blocks per work item */
-  int32_t sz_points;    /* points of sampled blocks per SZ work item */
+  int32_t sz_blocks;    /* sampled SZ blocks per work item */
   int32_t range_ctas;   /* persistent grids; 0 = every CTA the SMs hold at once */
   int32_t zfp_ctas;
   int32_t sz_ctas;

@@ -91,7 +91,7 @@ constexpr size_t kMaxPlans = 8;
 // Candidate work splits of the autotuner (small, middle, large).
 constexpr long long kRangeValues[3] = {1ll << 16, 1ll << 18, 1ll << 20};
 constexpr int kZfpBlocks[3] = {256, 1024, 4096};
-constexpr int kSzPoints[3] = {4096, 16384, 65536};
+constexpr int kSzBlocks[3] = {256, 1024, 4096};
 
 }  // namespace
 
@@ -616,10 +616,7 @@ void build_items(BatchPlan* b, const rd_batch_config& cfg, std::vector<BatchItem
   b->n_range = (int)items.size();
   for (int i = 0; i < b->n; i++) b->hbf[i].items_zfp = split(i, b->hbf[i].f.nsampled, cfg.zfp_blocks);
   b->n_zfp = (int)items.size() - b->n_range;
-  for (int i = 0; i < b->n; i++) {
-    const FieldDev& f = b->hbf[i].f;
-    split(i, f.nsampled * (1ll << (2 * f.d)), cfg.sz_points);
-  }
+  for (int i = 0; i < b->n; i++) split(i, b->hbf[i].f.nsampled, cfg.sz_blocks);
   b->n_sz = (int)items.size() - b->n_range - b->n_zfp;
 }
 
@@ -633,7 +630,7 @@ int upload_plan(BatchPlan* b, const rd_batch_config& cfg) {
     rd_batch_config small = cfg;
     small.range_values = kRangeValues[0] < cfg.range_values ? kRangeValues[0] : cfg.range_values;
     small.zfp_blocks = kZfpBlocks[0] < cfg.zfp_blocks ? kZfpBlocks[0] : cfg.zfp_blocks;
-    small.sz_points = kSzPoints[0] < cfg.sz_points ? kSzPoints[0] : cfg.sz_points;
+    small.sz_blocks = kSzBlocks[0] < cfg.sz_blocks ? kSzBlocks[0] : cfg.sz_blocks;
     std::vector<BatchItem> most;
     std::vector<BatchField> keep = b->hbf;
     build_items(b, small, most);
@@ -662,7 +659,7 @@ rd_batch_config split_level(const rd_context* c, int lr, int lz, int ls) {
   memset(&cfg, 0, sizeof(cfg));
   cfg.range_values = kRangeValues[lr];
   cfg.zfp_blocks = kZfpBlocks[lz];
-  cfg.sz_points = kSzPoints[ls];
+  cfg.sz_blocks = kSzBlocks[ls];
   return resolve_ctas(c, cfg);
 }
 
@@ -801,8 +798,10 @@ int batch_call(rd_context* c, const rd_field* fields, const rd_params* params, i
     key.insert(key.end(), q, q + bytes);
   };
   const int forced = c->batch_forced ? 1 : 0;
+  const int prof = c->profiling ? 1 : 0;  // a plan's graph records events only if captured so
   put(&n, sizeof(n));
   put(&need_gt, sizeof(need_gt));
+  put(&prof, sizeof(prof));
   put(&forced, sizeof(forced));
   if (forced) put(&c->batch_force, sizeof(rd_batch_config));
   std::vector<ParamsDev> pdev((size_t)n);
@@ -841,7 +840,7 @@ int batch_call(rd_context* c, const rd_field* fields, const rd_params* params, i
       rd_batch_config cfg = c->batch_force;
       if (cfg.range_values <= 0) cfg.range_values = kRangeValues[1];
       if (cfg.zfp_blocks <= 0) cfg.zfp_blocks = kZfpBlocks[1];
-      if (cfg.sz_points <= 0) cfg.sz_points = kSzPoints[1];
+      if (cfg.sz_blocks <= 0) cfg.sz_blocks = kSzBlocks[1];
       cfg.range_values = (cfg.range_values + 3) / 4 * 4;
       cfg.tuned = 0;
       rc = upload_plan(b, resolve_ctas(c, cfg));
@@ -1056,7 +1055,7 @@ int32_t rd_batch_set_config(rd_context* c, const rd_batch_config* cfg) {
     c->batch_forced = false;
     return RD_OK;
   }
-  if (cfg->range_values < 0 || cfg->zfp_blocks < 0 || cfg->sz_points < 0 || cfg->range_ctas < 0 ||
+  if (cfg->range_values < 0 || cfg->zfp_blocks < 0 || cfg->sz_blocks < 0 || cfg->range_ctas < 0 ||
       cfg->zfp_ctas < 0 || cfg->sz_ctas < 0)
     return RD_ERR_INVALID_ARG;
   c->batch_forced = true;

@@ -101,7 +101,21 @@ __device__ __forceinline__ void range_span(const float* __restrict__ x, long lon
   for (long long i = tid; i < head; i += nth) acc.add(xb[i]);
   const long long nvec = (n - head) / 4;
   const float4* x4 = reinterpret_cast<const float4*>(xb + head);
-  for (long long i = tid; i < nvec; i += nth) {
+  long long i = tid;
+  // four independent 16-byte loads in flight per thread
+  for (; i + 3 * nth < nvec; i += 4 * nth) {
+    float4 q[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) q[u] = __ldg(x4 + i + u * nth);
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      acc.add(q[u].x);
+      acc.add(q[u].y);
+      acc.add(q[u].z);
+      acc.add(q[u].w);
+    }
+  }
+  for (; i < nvec; i += nth) {
     const float4 q = __ldg(x4 + i);
     acc.add(q.x);
     acc.add(q.y);

@@ -97,49 +97,121 @@ __device__ __forceinline__ bool in_sampled_block(const FieldDev& f, const int* g
 }
 
 // ---------------------------------------------------------------------------
-// Estimator over the points of sampled blocks only.
+// Estimator over the points of sampled blocks only: one thread per sampled
+// block.  The thread reads the block with its one-cell halo on the low side
+// ((4+1)^d values, zero outside the domain), a plane at a time: the 2D
+// nested difference of each of the 16 points of a plane, minus that of the
+// plane behind, is the 3D residual, in the same float32 operations and
+// order as est_residual.
 // ---------------------------------------------------------------------------
-// Point u of the sampled blocks (u / 4^D = sampled block in lattice order,
-// u % 4^D = offset in the block, last axis fastest): its coordinates, and
-// whether it lies inside the field.
+// Row y of plane z, values x0-1 .. x0+3 (zero outside the domain; values past
+// the far edges feed no valid point and read as zero).
+__device__ __forceinline__ void load_halo_row(const FieldDev& f, long long row, bool row_ok, int x0,
+                                              float* v) {
+  const int nx = f.n[f.d - 1];
+  if (!row_ok) {
+#pragma unroll
+    for (int k = 0; k < 5; k++) v[k] = 0.0f;
+    return;
+  }
+  const float* __restrict__ p = f.x + row * nx;
+  v[0] = x0 > 0 ? __ldg(p + x0 - 1) : 0.0f;
+  if (f.vec_ok && x0 + 4 <= nx) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p + x0));
+    v[1] = q.x;
+    v[2] = q.y;
+    v[3] = q.z;
+    v[4] = q.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; k++) v[k + 1] = x0 + k < nx ? __ldg(p + x0 + k) : 0.0f;
+  }
+}
+
+// Lattice index of a sampled block -> its first point per axis.
 template <int D>
-__device__ __forceinline__ bool sampled_point(const FieldDev& f, long long u, int* g) {
-  constexpr int NB = 1 << (2 * D);
-  const long long sb = u / NB;
-  const int t = (int)(u % NB);
+__device__ __forceinline__ void sampled_block_origin(const FieldDev& f, long long sb, int* o) {
   long long r = sb;
-  bool ok = true;
 #pragma unroll
   for (int k = D - 1; k >= 0; k--) {
-    int l = (int)(r % f.L[k]);
+    const int l = (int)(r % f.L[k]);
     r /= f.L[k];
-    int tk = (t >> (2 * (D - 1 - k))) & 3;
-    g[k] = 4 * l * f.s[k] + tk;
-    ok = ok && g[k] < f.n[k];
+    o[k] = 4 * l * f.s[k];
   }
-  return ok;
+}
+
+template <int D>
+__device__ __forceinline__ void sz_est_block(const FieldDev& f, long long sb, bool active, float inv,
+                                             int R, uint32_t* s_win, uint32_t* g_hist) {
+  int o[3] = {0, 0, 0};
+  if (active) sampled_block_origin<D>(f, sb, o);
+  if constexpr (D == 1) {
+    float v[5];
+    load_halo_row(f, 0, active, o[0], v);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const bool ok = active && o[0] + k < f.n[0];
+      const unsigned mask = __ballot_sync(0xffffffffu, ok);
+      if (ok) hist_add(s_win, g_hist, est_symbol(__fsub_rn(v[k + 1], v[k]), inv, R), mask);
+    }
+  } else {
+    const int ny = f.n[D - 2], nx = f.n[D - 1];
+    const int y0 = o[D - 2], x0 = o[D - 1];
+    // 2D nested differences of the 16 points of plane z (rows y0-1 .. y0+3)
+    auto plane = [&](int z, bool z_ok, float* d2) {
+      float v[5][5];
+#pragma unroll
+      for (int r = 0; r < 5; r++) {
+        const int y = y0 - 1 + r;
+        const bool ok = z_ok && y >= 0 && y < ny;
+        const long long row = (D == 3 ? (long long)z * ny : 0ll) + y;
+        load_halo_row(f, row, ok, x0, v[r]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; j++)
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+          d2[4 * j + k] = __fsub_rn(__fsub_rn(v[j + 1][k + 1], v[j + 1][k]),
+                                    __fsub_rn(v[j][k + 1], v[j][k]));
+    };
+    float prev[16];
+    const int nz = D == 3 ? f.n[0] : 1;
+    const int z0 = D == 3 ? o[0] : 0;
+    if (D == 3) plane(z0 - 1, active && z0 > 0, prev);
+#pragma unroll 1
+    for (int i = 0; i < (D == 3 ? 4 : 1); i++) {
+      const int z = z0 + i;
+      const bool z_ok = active && z < nz;
+      float cur[16];
+      plane(z, z_ok, cur);
+#pragma unroll
+      for (int t = 0; t < 16; t++) {
+        const int j = t >> 2, k = t & 3;
+        const bool ok = z_ok && y0 + j < ny && x0 + k < nx;
+        const unsigned mask = __ballot_sync(0xffffffffu, ok);
+        const float r = D == 3 ? __fsub_rn(cur[t], prev[t]) : cur[t];
+        if (ok) hist_add(s_win, g_hist, est_symbol(r, inv, R), mask);
+      }
+      if (D == 3) {
+#pragma unroll
+        for (int t = 0; t < 16; t++) prev[t] = cur[t];
+      }
+    }
+  }
 }
 
 template <int D>
 __global__ void __launch_bounds__(kSzThreads) k_sz_est(FieldDev f, ParamsDev p, Workspace* ws) {
-  constexpr int NB = 1 << (2 * D);
   __shared__ uint32_t s_win[kHistWin];
   const Scalars& sc = ws->sc;
   if (sc.status != RD_OK || sc.constant) return;
   for (int i = threadIdx.x; i < kHistWin; i += blockDim.x) s_win[i] = 0u;
   __syncthreads();
   const float inv = sc.inv;
-  const long long units = f.nsampled * NB;
-  for (long long u0 = (long long)blockIdx.x * blockDim.x; u0 < units;
-       u0 += (long long)gridDim.x * blockDim.x) {
-    const long long u = u0 + threadIdx.x;
-    int g[3] = {0, 0, 0};
-    const bool ok = u < units && sampled_point<D>(f, u, g);
-    const unsigned mask = __ballot_sync(0xffffffffu, ok);
-    if (ok) {
-      Nbr c = gather_cell<D>(f, g);
-      hist_add(s_win, ws->hist[0], est_symbol(est_residual<D>(c), inv, p.R), mask);
-    }
+  for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < f.nsampled;
+       b0 += (long long)gridDim.x * blockDim.x) {
+    const long long sb = b0 + threadIdx.x;
+    sz_est_block<D>(f, sb, sb < f.nsampled, inv, p.R, s_win, ws->hist[0]);
   }
   __syncthreads();
   hist_flush(s_win, ws->hist[0]);
@@ -219,8 +291,7 @@ __global__ void __launch_bounds__(kSzThreads) k_sz_gt(FieldDev f, ParamsDev p, W
 template <int D>
 static cudaError_t launch_est_d(const FieldDev& f, const ParamsDev& p, Workspace* ws, int ctas,
                                 cudaStream_t s) {
-  constexpr int NB = 1 << (2 * D);
-  long long want = (f.nsampled * NB + kSzThreads - 1) / kSzThreads;
+  long long want = (f.nsampled + kSzThreads - 1) / kSzThreads;
   int g = (int)(want < ctas ? (want < 1 ? 1 : want) : ctas);
   k_sz_est<D><<<g, kSzThreads, 0, s>>>(f, p, ws);
   return cudaGetLastError();
@@ -268,22 +339,16 @@ int sz_occupancy(int d, int num_sms) {
 }
 
 // ---------------------------------------------------------------------------
-// Batched estimate: points of the sampled blocks of many fields.  Each work
-// item is a run of points of one field; its histogram window lives in
-// shared memory and is added to the field's histogram when the item ends.
+// Batched estimate: the sampled blocks of many fields.  Each work item is a
+// run of sampled blocks of one field; its histogram window lives in shared
+// memory and is added to the field's histogram when the item ends.
 // ---------------------------------------------------------------------------
 template <int D>
 __device__ __forceinline__ void sz_est_item(const FieldDev& f, int R, float inv, uint32_t* g_hist,
                                             long long u0, long long u1, uint32_t* s_win) {
   for (long long b0 = u0; b0 < u1; b0 += blockDim.x) {
-    const long long u = b0 + threadIdx.x;
-    int g[3] = {0, 0, 0};
-    const bool ok = u < u1 && sampled_point<D>(f, u, g);
-    const unsigned mask = __ballot_sync(0xffffffffu, ok);
-    if (ok) {
-      Nbr c = gather_cell<D>(f, g);
-      hist_add(s_win, g_hist, est_symbol(est_residual<D>(c), inv, R), mask);
-    }
+    const long long sb = b0 + threadIdx.x;
+    sz_est_block<D>(f, sb, sb < u1, inv, R, s_win, g_hist);
   }
 }
 

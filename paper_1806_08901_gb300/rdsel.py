@@ -77,7 +77,7 @@ class rd_truth(C.Structure):
 
 
 class rd_batch_config(C.Structure):
-    _fields_ = [("range_values", C.c_int64), ("zfp_blocks", C.c_int32), ("sz_points", C.c_int32),
+    _fields_ = [("range_values", C.c_int64), ("zfp_blocks", C.c_int32), ("sz_blocks", C.c_int32),
                 ("range_ctas", C.c_int32), ("zfp_ctas", C.c_int32), ("sz_ctas", C.c_int32),
                 ("tuned", C.c_int32)]
 
@@ -297,6 +297,35 @@ def rd_select_batch(ctx, fields, prms, truth: bool = False, stream=None, check: 
     return ([_todict(r) for r in rs], [_todict(t) for t in ts] if truth else None, statuses)
 
 
+class BatchCall:
+    """A batch call marshalled once (fields, parameters and output arrays), to
+    be issued repeatedly with run(); for timing loops that must not pay the
+    per-call marshalling."""
+
+    def __init__(self, ctx, fields, prms, truth: bool = False):
+        n = len(fields)
+        if isinstance(prms, rd_params):
+            prms = [prms] * n
+        self.ctx, self.n = ctx, n
+        self.fs = (rd_field * n)()
+        self.keep = []
+        for i, x in enumerate(fields):
+            f, k = make_field(x)
+            self.fs[i] = f
+            self.keep.append(k)
+        self.ps = (rd_params * n)(*prms)
+        self.rs = (rd_result * n)()
+        self.ts = (rd_truth * n)() if truth else None
+        self.st = (C.c_int32 * n)()
+
+    def run(self, stream=None) -> int:
+        return lib().rd_select_batch(self.ctx, self.fs, self.ps, self.n, self.rs, self.ts,
+                                     self.st, _stream(stream))
+
+    def results(self) -> list:
+        return [_todict(r) for r in self.rs]
+
+
 def rd_batch_set_config(ctx, cfg=None) -> None:
     """Force the work split of later batch calls (a dict of rd_batch_config
     fields, zeros = defaults), or None for the autotuner."""
@@ -428,6 +457,9 @@ class Context:
 
     def select_batch(self, fields, prms, truth=False, stream=None, check=True):
         return rd_select_batch(self.h, fields, prms, truth, stream, check)
+
+    def batch_call(self, fields, prms, truth=False):
+        return BatchCall(self.h, fields, prms, truth)
 
     def batch_set_config(self, cfg=None):
         rd_batch_set_config(self.h, cfg)
