@@ -195,24 +195,24 @@ int32_t rd_select_static(const rd_field* field, const rd_params* params,
 
 /* ---- batched estimate ------------------------------------------------ */
 
-/* Work split of the batched passes.  The results do not depend on it. */
+/* Work split of the batched estimate.  The results do not depend on it. */
 typedef struct {
-  int64_t range_values; /* values per work item of the range pass (multiple of 4) */
+  int64_t range_values; /* values per range work item (rounded up to a multiple of 4) */
   int32_t zfp_blocks;   /* sampled ZFP blocks per work item */
   int32_t sz_blocks;    /* sampled SZ blocks per work item */
-  int32_t range_ctas;   /* persistent grids; 0 = every CTA the SMs hold at once */
-  int32_t zfp_ctas;
-  int32_t sz_ctas;
+  int32_t ctas;         /* cap on each pass's CTAs; 0 = every CTA the SMs hold at once */
   int32_t tuned;        /* output: 1 when the autotuner chose this split */
 } rd_batch_config;
 
 /* Algorithm 1 lines 2-12 for n fields at once, e.g. every field of a
  * simulation snapshot, of uneven 2D/3D sizes (the paper's algorithm loops
- * over the fields of a snapshot).  Six persistent launches cover all fields:
- * reset; value range (the CTA that ends a field's last work item also
- * derives VR and eb_abs); sampled ZFP blocks (the CTA that ends a field's
- * last item also derives delta); sampled SZ points; count-of-counts; one CTA
- * per field for the Huffman cost, entropy, rates, PSNRs and selection.
+ * over the fields of a snapshot).  Six launches cover all fields: a reset;
+ * three persistent passes over work items of every field (runs of a field's
+ * values for the range, runs of its sampled blocks for the ZFP and the SZ
+ * estimates; the CTA that ends a field's last range item derives VR and
+ * eb_abs, the one that ends its last ZFP item derives delta); the
+ * count-of-counts; one CTA per field for the Huffman cost, entropy, rates,
+ * PSNRs and selection.
  *  - fields[i]: DEVICE memory only (RD_ERR_INVALID_ARG otherwise);
  *    params[i]: the parameters of field i.  n >= 1.
  *  - results[n] is required; truths[n] may be NULL, else each field's ground
@@ -224,9 +224,9 @@ typedef struct {
  *    record zeroed.
  *  - The context holds one workspace per field (about 2.6 MB each) and caches
  *    a plan per distinct set of fields and parameters: the plan's first call
- *    runs the autotuner (three work splits, each pass timed, the fastest
- *    split per pass kept) unless rd_batch_set_config forced one; its second
- *    call captures a CUDA graph that later calls replay.
+ *    runs the autotuner (three work-item sizes, the passes timed, the fastest
+ *    kept) unless rd_batch_set_config forced a split; its second call
+ *    captures a CUDA graph that later calls replay.
  *  - Each field's records equal those of rd_select (and of rd_evaluate for
  *    the truth) on that field alone. */
 int32_t rd_select_batch(rd_context* ctx, const rd_field* fields,

@@ -7,7 +7,9 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "rd_internal.cuh"
@@ -77,7 +79,7 @@ struct BatchPlan {
   std::vector<BatchField> hbf;
   std::vector<Geometry> geo;
   BatchField* dbf = nullptr;
-  BatchItem* ditems = nullptr;
+  BatchItem* ditems = nullptr;  // range items, then ZFP items, then SZ items
   int n_range = 0, n_zfp = 0, n_sz = 0;
   cudaGraphExec_t exec = nullptr;
   std::vector<Pending> events;
@@ -596,12 +598,14 @@ int ensure_batch_capacity(rd_context* c, int n) {
   return RD_OK;
 }
 
-// Work items of the three item-based passes for one split; counts per field
-// go into the field table.
+// Work items of the three passes for one split: range items (runs of
+// range_values values), then ZFP items and SZ items (runs of zfp_blocks /
+// sz_blocks sampled blocks), each list in field order.  Per-field item
+// counts go into the field table.
 void build_items(BatchPlan* b, const rd_batch_config& cfg, std::vector<BatchItem>& items) {
   items.clear();
   auto split = [&](int i, long long units, long long per) {
-    long long cnt = units > 0 ? (units + per - 1) / per : 0;
+    const long long cnt = units > 0 ? (units + per - 1) / per : 0;
     for (long long k = 0; k < cnt; k++) {
       BatchItem it;
       it.field = i;
@@ -624,20 +628,16 @@ void build_items(BatchPlan* b, const rd_batch_config& cfg, std::vector<BatchItem
 // that of the smallest candidate work items).
 int upload_plan(BatchPlan* b, const rd_batch_config& cfg) {
   std::vector<BatchItem> items;
-  build_items(b, cfg, items);
   if (!b->dbf && cudaMalloc(&b->dbf, b->hbf.size() * sizeof(BatchField)) != cudaSuccess) return RD_ERR_OOM;
   if (!b->ditems) {
     rd_batch_config small = cfg;
     small.range_values = kRangeValues[0] < cfg.range_values ? kRangeValues[0] : cfg.range_values;
     small.zfp_blocks = kZfpBlocks[0] < cfg.zfp_blocks ? kZfpBlocks[0] : cfg.zfp_blocks;
     small.sz_blocks = kSzBlocks[0] < cfg.sz_blocks ? kSzBlocks[0] : cfg.sz_blocks;
-    std::vector<BatchItem> most;
-    std::vector<BatchField> keep = b->hbf;
-    build_items(b, small, most);
-    b->hbf = keep;
-    build_items(b, cfg, items);
-    if (cudaMalloc(&b->ditems, most.size() * sizeof(BatchItem)) != cudaSuccess) return RD_ERR_OOM;
+    build_items(b, small, items);
+    if (cudaMalloc(&b->ditems, items.size() * sizeof(BatchItem)) != cudaSuccess) return RD_ERR_OOM;
   }
+  build_items(b, cfg, items);
   if (cudaMemcpy(b->dbf, b->hbf.data(), b->hbf.size() * sizeof(BatchField), cudaMemcpyHostToDevice) !=
           cudaSuccess ||
       cudaMemcpy(b->ditems, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice) !=
@@ -647,46 +647,49 @@ int upload_plan(BatchPlan* b, const rd_batch_config& cfg) {
   return RD_OK;
 }
 
+// A forced grid caps every pass's grid; 0 keeps each pass's resident count.
 rd_batch_config resolve_ctas(const rd_context* c, rd_batch_config cfg) {
-  if (cfg.range_ctas <= 0) cfg.range_ctas = c->b_range_ctas;
-  if (cfg.zfp_ctas <= 0) cfg.zfp_ctas = c->b_zfp_ctas;
-  if (cfg.sz_ctas <= 0) cfg.sz_ctas = c->b_sz_ctas;
+  (void)c;
+  if (cfg.ctas < 0) cfg.ctas = 0;
   return cfg;
 }
 
-rd_batch_config split_level(const rd_context* c, int lr, int lz, int ls) {
+int pass_ctas(int resident, int cap) { return cap > 0 && cap < resident ? cap : resident; }
+
+rd_batch_config split_level(const rd_context* c, int level, int ctas) {
   rd_batch_config cfg;
   memset(&cfg, 0, sizeof(cfg));
-  cfg.range_values = kRangeValues[lr];
-  cfg.zfp_blocks = kZfpBlocks[lz];
-  cfg.sz_blocks = kSzBlocks[ls];
+  cfg.range_values = kRangeValues[level];
+  cfg.zfp_blocks = kZfpBlocks[level];
+  cfg.sz_blocks = kSzBlocks[level];
+  cfg.ctas = ctas;
   return resolve_ctas(c, cfg);
 }
 
-// The estimate launches of a batch (reset .. final), optionally with event
-// pairs around the three item-based passes (the autotuner's timing).
+// The estimate launches of a batch (reset .. final), optionally with an
+// event pair around the three item-based passes (the autotuner's timing).
 int issue_batch_estimate(rd_context* c, BatchPlan* b, cudaStream_t s, cudaEvent_t* ev) {
   const int n = b->n;
-  const rd_batch_config& cfg = b->cfg;
+  const int cap = b->cfg.ctas;
   int rc;
   if ((rc = launch(c, K_B_RESET, s, [&] { return launch_batch_reset(b->dbf, n, b->need_gt, s); })))
     return rc;
   if (ev) cudaEventRecord(ev[0], s);
   if ((rc = launch(c, K_B_RANGE, s, [&] {
-         return launch_batch_range(b->dbf, b->ditems, b->n_range, cfg.range_ctas, s);
+         return launch_batch_range(b->dbf, b->ditems, b->n_range, pass_ctas(c->b_range_ctas, cap), s);
+       })))
+    return rc;
+  if ((rc = launch(c, K_B_ZFP, s, [&] {
+         return launch_batch_zfp_est(b->dbf, b->ditems + b->n_range, b->n_zfp,
+                                     pass_ctas(c->b_zfp_ctas, cap), s);
+       })))
+    return rc;
+  if ((rc = launch(c, K_B_SZ, s, [&] {
+         return launch_batch_sz_est(b->dbf, b->ditems + b->n_range + b->n_zfp, b->n_sz,
+                                    pass_ctas(c->b_sz_ctas, cap), s);
        })))
     return rc;
   if (ev) cudaEventRecord(ev[1], s);
-  if ((rc = launch(c, K_B_ZFP, s, [&] {
-         return launch_batch_zfp_est(b->dbf, b->ditems + b->n_range, b->n_zfp, cfg.zfp_ctas, s);
-       })))
-    return rc;
-  if (ev) cudaEventRecord(ev[2], s);
-  if ((rc = launch(c, K_B_SZ, s, [&] {
-         return launch_batch_sz_est(b->dbf, b->ditems + b->n_range + b->n_zfp, b->n_sz, cfg.sz_ctas, s);
-       })))
-    return rc;
-  if (ev) cudaEventRecord(ev[3], s);
   if ((rc = launch(c, K_B_PREP, s, [&] { return launch_batch_code_prep(b->dbf, n, s); }))) return rc;
   return launch(c, K_B_FINAL, s, [&] {
     return launch_batch_final(b->dbf, n, c->xlogx, c->d_bres, c->d_bstatus, s);
@@ -737,36 +740,34 @@ int issue_batch(rd_context* c, BatchPlan* b, cudaStream_t s) {
 }
 
 // Autotuner: run the estimate with the small, middle and large work items
-// of every pass, time each item-based pass with events, and keep the
-// fastest split per pass.  The results do not depend on the split (integer
-// sums, fixed-order floating point), so these are ordinary runs.
+// of every pass, time the three item-based passes together with events, and
+// keep the fastest.  The results do not depend on the split (integer sums,
+// fixed-order floating point), so these are ordinary runs.
 int autotune_plan(rd_context* c, BatchPlan* b, cudaStream_t s) {
-  cudaEvent_t ev[4];
-  for (int i = 0; i < 4; i++)
+  cudaEvent_t ev[2];
+  for (int i = 0; i < 2; i++)
     if (cudaEventCreate(&ev[i]) != cudaSuccess) return RD_ERR_CUDA;
-  float best[3] = {1e30f, 1e30f, 1e30f};
-  int lvl[3] = {1, 1, 1};
+  float best = 1e30f;
+  rd_batch_config pick = split_level(c, 1, 0);
   int rc = RD_OK;
   const bool prof = c->profiling;
   c->profiling = false;
   for (int l = 0; l < 3 && rc == RD_OK; l++) {
-    rc = upload_plan(b, split_level(c, l, l, l));
+    const rd_batch_config cfg = split_level(c, l, 0);
+    rc = upload_plan(b, cfg);
     if (rc == RD_OK) rc = issue_batch_estimate(c, b, s, ev);
     if (rc == RD_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = RD_ERR_CUDA;
-    for (int k = 0; k < 3 && rc == RD_OK; k++) {
-      float ms = 0.0f;
-      if (cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) == cudaSuccess && ms < best[k]) {
-        best[k] = ms;
-        lvl[k] = l;
-      }
+    float ms = 0.0f;
+    if (rc == RD_OK && cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess && ms < best) {
+      best = ms;
+      pick = cfg;
     }
   }
   c->profiling = prof;
-  for (int i = 0; i < 4; i++) cudaEventDestroy(ev[i]);
+  for (int i = 0; i < 2; i++) cudaEventDestroy(ev[i]);
   if (rc) return rc;
-  rd_batch_config cfg = split_level(c, lvl[0], lvl[1], lvl[2]);
-  cfg.tuned = 1;
-  return upload_plan(b, cfg);
+  pick.tuned = 1;
+  return upload_plan(b, pick);
 }
 
 BatchPlan* find_plan(rd_context* c, const std::vector<unsigned char>& key) {
@@ -975,9 +976,7 @@ int32_t rd_context_create(int32_t device, size_t hbm_budget, rd_context** out) {
     c->zfp_ctas[d] = zfp_occupancy(d, c->num_sms);
     c->sz_ctas[d] = sz_occupancy(d, c->num_sms);
   }
-  c->b_range_ctas = batch_range_occupancy(c->num_sms);
-  c->b_zfp_ctas = batch_zfp_occupancy(c->num_sms);
-  c->b_sz_ctas = batch_sz_occupancy(c->num_sms);
+  batch_occupancy(c->num_sms, &c->b_range_ctas, &c->b_zfp_ctas, &c->b_sz_ctas);
   *out = c;
   return RD_OK;
 }
@@ -1055,8 +1054,7 @@ int32_t rd_batch_set_config(rd_context* c, const rd_batch_config* cfg) {
     c->batch_forced = false;
     return RD_OK;
   }
-  if (cfg->range_values < 0 || cfg->zfp_blocks < 0 || cfg->sz_blocks < 0 || cfg->range_ctas < 0 ||
-      cfg->zfp_ctas < 0 || cfg->sz_ctas < 0)
+  if (cfg->range_values < 0 || cfg->zfp_blocks < 0 || cfg->sz_blocks < 0 || cfg->ctas < 0)
     return RD_ERR_INVALID_ARG;
   c->batch_forced = true;
   c->batch_force = *cfg;

@@ -29,7 +29,7 @@ struct Scalars {
   int32_t constant;      // value range is zero
   int32_t minexp;        // floor(log2 eb_abs)
   uint32_t min_key, max_key, nonfinite, pad0;
-  uint32_t done[2];       // work items finished (batched passes: last-CTA detection)
+  uint32_t done[2];       // batched passes: range / ZFP work items finished (last-CTA detection)
   float vmin, vmax, amax;  // amax = max(|vmin|, |vmax|)
   float w, inv, tau;       // SZ quantiser: bin, 1/bin, escape threshold
   double vr, eb_abs, delta, mse_sp;
@@ -101,14 +101,14 @@ struct BatchField {
   Workspace* ws;                 // the field's own workspace
   unsigned long long ncoeff;     // EC-sampled coefficients (denominator of MSE_sp)
   unsigned long long npoints;    // valid points of the sampled blocks
-  uint32_t items_range;          // work items of the field in the range pass
-  uint32_t items_zfp;            // ... and in the ZFP estimate pass
+  uint32_t items_range;          // range work items of the field
+  uint32_t items_zfp;            // ZFP estimate work items of the field
   int32_t need_gt;               // the quantiser is also prepared for the ground truth
   int32_t pad;
 };
 
-// A work item of a batched pass: units [begin, end) of one field (values,
-// sampled blocks or points of sampled blocks, by pass).
+// A work item of a batched pass: units [begin, end) of one field (values
+// for the range pass, sampled blocks for the estimates).
 struct BatchItem {
   int32_t field;
   int32_t pad;
@@ -196,17 +196,18 @@ cudaError_t launch_sz_march(const FieldDev& f, const ParamsDev& p, int with_est,
                             int num_sms, cudaStream_t s, int* grid_used);
 int zfp_occupancy(int d, int num_sms);
 
-// ---- batched estimate (rd_select_batch): persistent passes over work items
-// of all fields; CTAs stride over the items in order ----
+// ---- batched estimate (rd_select_batch) ----
 cudaError_t launch_batch_reset(const BatchField* bf, int n, int need_gt, cudaStream_t s);
-// range + (last item of a field) prepare
+// range; the CTA ending a field's last item derives VR, eb_abs, minexp
 cudaError_t launch_batch_range(const BatchField* bf, const BatchItem* items, int nitems, int ctas,
                                cudaStream_t s);
-// sampled ZFP blocks + (last item of a field) the bin width delta
+// sampled ZFP blocks; the CTA ending a field's last item derives delta
 cudaError_t launch_batch_zfp_est(const BatchField* bf, const BatchItem* items, int nitems, int ctas,
                                  cudaStream_t s);
 cudaError_t launch_batch_sz_est(const BatchField* bf, const BatchItem* items, int nitems, int ctas,
                                 cudaStream_t s);
+// resident CTAs of the three passes
+void batch_occupancy(int num_sms, int* range_ctas, int* zfp_ctas, int* sz_ctas);
 cudaError_t launch_batch_code_prep(const BatchField* bf, int n, cudaStream_t s);
 // Huffman cost, entropy and finish of every field; result records and
 // statuses gathered into res[n] and status[n]
@@ -215,9 +216,7 @@ cudaError_t launch_batch_final(const BatchField* bf, int n, const double* xlogx,
 // ground-truth records and final statuses of a batch, gathered
 cudaError_t launch_batch_truth(const BatchField* bf, int n, rd_truth* truth, int32_t* status,
                                cudaStream_t s);
-int batch_range_occupancy(int num_sms);
-int batch_zfp_occupancy(int num_sms);
-int batch_sz_occupancy(int num_sms);
+
 int sz_occupancy(int d, int num_sms);
 
 }  // namespace rdk

@@ -7,6 +7,7 @@
 
 #include "rd_delta.cuh"
 #include "rd_device.cuh"
+#include "rd_range_dev.cuh"
 
 namespace rdk {
 
@@ -77,85 +78,6 @@ cudaError_t launch_reset(Workspace* ws, cudaStream_t s) {
 // Value range: min / max over every value, with a non-finite test.  Rows are
 // read as float4 where the pointer allows it.
 // ---------------------------------------------------------------------------
-struct RangeAcc {
-  unsigned kmin = 0xffffffffu, kmax = 0u, bad = 0u;
-  __device__ __forceinline__ void add(float v) {
-    const unsigned b = __float_as_uint(v);
-    bad |= ((b & 0x7f800000u) == 0x7f800000u);
-    const unsigned k = float_key(v);
-    kmin = min(kmin, k);
-    kmax = max(kmax, k);
-  }
-};
-
-// Values [begin, end) of x, thread tid of nth: a scalar head up to a 16-byte
-// boundary, float4 loads, a scalar tail.
-__device__ __forceinline__ void range_span(const float* __restrict__ x, long long begin,
-                                           long long end, long long tid, long long nth,
-                                           RangeAcc& acc) {
-  const float* xb = x + begin;
-  const long long n = end - begin;
-  long long head = (long long)((16u - ((uintptr_t)xb & 15u)) & 15u) / 4;
-  if (head > n) head = n;
-  if (((uintptr_t)xb & 3u) != 0) head = n;  // not even 4-byte aligned: all scalar
-  for (long long i = tid; i < head; i += nth) acc.add(xb[i]);
-  const long long nvec = (n - head) / 4;
-  const float4* x4 = reinterpret_cast<const float4*>(xb + head);
-  long long i = tid;
-  // four independent 16-byte loads in flight per thread
-  for (; i + 3 * nth < nvec; i += 4 * nth) {
-    float4 q[4];
-#pragma unroll
-    for (int u = 0; u < 4; u++) q[u] = __ldg(x4 + i + u * nth);
-#pragma unroll
-    for (int u = 0; u < 4; u++) {
-      acc.add(q[u].x);
-      acc.add(q[u].y);
-      acc.add(q[u].z);
-      acc.add(q[u].w);
-    }
-  }
-  for (; i < nvec; i += nth) {
-    const float4 q = __ldg(x4 + i);
-    acc.add(q.x);
-    acc.add(q.y);
-    acc.add(q.z);
-    acc.add(q.w);
-  }
-  for (long long i = head + nvec * 4 + tid; i < n; i += nth) acc.add(xb[i]);
-}
-
-// Warp, then CTA, then one update per CTA of the field's shared keys.  All
-// threads of the CTA call it (up to 1024 threads).
-__device__ __forceinline__ void range_commit(RangeAcc acc, Workspace* ws) {
-  __shared__ unsigned s_min[32], s_max[32], s_bad[32];
-  unsigned kmin = __reduce_min_sync(0xffffffffu, acc.kmin);
-  unsigned kmax = __reduce_max_sync(0xffffffffu, acc.kmax);
-  unsigned bad = __reduce_or_sync(0xffffffffu, acc.bad);
-  const int wid = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) {
-    s_min[wid] = kmin;
-    s_max[wid] = kmax;
-    s_bad[wid] = bad;
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    const int nw = blockDim.x >> 5;
-    unsigned a = threadIdx.x < nw ? s_min[threadIdx.x] : 0xffffffffu;
-    unsigned b = threadIdx.x < nw ? s_max[threadIdx.x] : 0u;
-    unsigned c = threadIdx.x < nw ? s_bad[threadIdx.x] : 0u;
-    a = __reduce_min_sync(0xffffffffu, a);
-    b = __reduce_max_sync(0xffffffffu, b);
-    c = __reduce_or_sync(0xffffffffu, c);
-    if (threadIdx.x == 0) {
-      atomicMin(&ws->sc.min_key, a);
-      atomicMax(&ws->sc.max_key, b);
-      if (c) atomicOr(&ws->sc.nonfinite, 1u);
-    }
-  }
-  __syncthreads();
-}
-
 __global__ void __launch_bounds__(512) k_range(const float* __restrict__ x, long long n,
                                                Workspace* ws) {
   RangeAcc acc;
@@ -169,40 +91,6 @@ cudaError_t launch_range(const FieldDev& f, Workspace* ws, int ctas, cudaStream_
   int g = (int)(want < ctas ? (want < 1 ? 1 : want) : ctas);
   k_range<<<g, 512, 0, s>>>(f.x, f.N, ws);
   return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// Prepare: value range VR, eb_abs (Eq. psnr-sz: eb_rel = eb_abs / VR) and
-// floor(log2 eb_abs) for the ZFP precision rule.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void prepare_field(const ParamsDev& p, Workspace* ws) {
-  Scalars& s = ws->sc;
-  if (__ldcg(&s.nonfinite)) {
-    s.status = RD_ERR_NONFINITE;
-    return;
-  }
-  s.vmin = key_float(__ldcg(&s.min_key));
-  s.vmax = key_float(__ldcg(&s.max_key));
-  s.amax = fmaxf(fabsf(s.vmin), fabsf(s.vmax));
-  s.vr = (double)s.vmax - (double)s.vmin;
-  s.eb_abs = (p.eb_mode == RD_EB_REL) ? p.eb * s.vr : p.eb;
-  ws->res.vmin = s.vmin;
-  ws->res.vmax = s.vmax;
-  ws->res.vr = s.vr;
-  ws->res.eb_abs = s.eb_abs;
-  if (s.vr == 0.0) {
-    s.constant = 1;
-    s.flags |= RD_F_CONSTANT;
-    return;
-  }
-  if (!(s.eb_abs > 0.0) || !isfinite(s.eb_abs)) {
-    s.status = RD_ERR_INVALID_ARG;
-    return;
-  }
-  int e;
-  frexp(s.eb_abs, &e);
-  s.minexp = e - 1;
-  ws->res.minexp = s.minexp;
 }
 
 __global__ void k_prepare(ParamsDev p, Workspace* ws) { prepare_field(p, ws); }
@@ -852,15 +740,11 @@ cudaError_t launch_finish(const ParamsDev& p, Workspace* ws, int passes, int zfp
 }
 
 // ---------------------------------------------------------------------------
-// Batched estimate (rd_select_batch): the passes of this file over many
-// fields.  Range work items are runs of values of one field; the CTA that
-// finishes a field's last item (a counter in the field's workspace, with
-// fences on both sides) computes VR, eb_abs and the precision exponent.
-// The final pass runs one CTA per field: Huffman cost and entropy, then the
-// rates, PSNRs and selection, and gathers the field's record and status.
+// Batched estimate (rd_select_batch): the reset, the count-of-counts of every
+// field, and the final pass (one CTA per field: Huffman cost and entropy,
+// then the rates, PSNRs and selection; the field's record and status are
+// gathered).
 // ---------------------------------------------------------------------------
-constexpr int kBatchRangeThreads = 512;
-
 __global__ void k_batch_reset(const BatchField* __restrict__ bf, int need_gt) {
   const BatchField& F = bf[blockIdx.x];
   reset_ws(F.ws, blockIdx.y * blockDim.x + threadIdx.x, gridDim.y * blockDim.x, need_gt ? 3 : 1);
@@ -869,46 +753,6 @@ __global__ void k_batch_reset(const BatchField* __restrict__ bf, int need_gt) {
 cudaError_t launch_batch_reset(const BatchField* bf, int n, int need_gt, cudaStream_t s) {
   k_batch_reset<<<dim3(n, 8), 256, 0, s>>>(bf, need_gt);
   return cudaGetLastError();
-}
-
-__global__ void __launch_bounds__(kBatchRangeThreads) k_batch_range(const BatchField* __restrict__ bf,
-                                                                    const BatchItem* __restrict__ items,
-                                                                    int nitems) {
-  __shared__ int s_last;
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const BatchItem item = items[it];
-    const BatchField& F = bf[item.field];
-    RangeAcc acc;
-    range_span(F.f.x, item.begin, item.end, threadIdx.x, blockDim.x, acc);
-    range_commit(acc, F.ws);
-    if (threadIdx.x == 0) {
-      __threadfence();
-      s_last = atomicAdd(&F.ws->sc.done[0], 1u) == F.items_range - 1u;
-    }
-    __syncthreads();
-    if (s_last && threadIdx.x == 0) {
-      __threadfence();
-      prepare_field(F.p, F.ws);
-    }
-    __syncthreads();
-  }
-}
-
-cudaError_t launch_batch_range(const BatchField* bf, const BatchItem* items, int nitems, int ctas,
-                               cudaStream_t s) {
-  int g = nitems < ctas ? nitems : ctas;
-  if (g < 1) g = 1;
-  k_batch_range<<<g, kBatchRangeThreads, 0, s>>>(bf, items, nitems);
-  return cudaGetLastError();
-}
-
-int batch_range_occupancy(int num_sms) {
-  int per = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void*)k_batch_range, kBatchRangeThreads,
-                                                    0) != cudaSuccess ||
-      per < 1)
-    per = 1;
-  return per * num_sms;
 }
 
 __global__ void __launch_bounds__(kPrepThreads) k_batch_code_prep(const BatchField* __restrict__ bf) {

@@ -11,195 +11,11 @@
 //     histogram of residual symbols, SSE and max error.
 #include <stdint.h>
 
-#include "rd_device.cuh"
+#include "rd_sz_dev.cuh"
 
 namespace rdk {
 
-constexpr int kSzThreads = 256;
-
-struct Nbr {
-  // the 2^D corner values of the Lorenzo cell ending at a point; index bit k
-  // set = one step back along axis D-1-k (bit 0 = fastest axis)
-  float v[8];
-};
-
-template <int D>
-__device__ __forceinline__ Nbr gather_cell(const FieldDev& f, const int* g) {
-  Nbr c;
-  constexpr int NC = 1 << D;
-#pragma unroll
-  for (int m = 0; m < NC; m++) {
-    long long idx = 0;
-    bool inside = true;
-#pragma unroll
-    for (int k = 0; k < D; k++) {
-      int back = (m >> (D - 1 - k)) & 1;
-      int gk = g[k] - back;
-      inside = inside && gk >= 0;
-      idx = idx * f.n[k] + gk;
-    }
-    c.v[m] = inside ? __ldg(f.x + idx) : 0.0f;
-  }
-  return c;
-}
-
-// x - Lorenzo(x) as nested float32 differences, last axis first:
-//   1D: v0 - v1
-//   2D: (v00 - v01) - (v10 - v11)
-//   3D: 2D form on the current plane minus the 2D form on the plane behind.
-template <int D>
-__device__ __forceinline__ float est_residual(const Nbr& c) {
-  if constexpr (D == 1) {
-    return __fsub_rn(c.v[0], c.v[1]);
-  } else if constexpr (D == 2) {
-    return __fsub_rn(__fsub_rn(c.v[0], c.v[1]), __fsub_rn(c.v[2], c.v[3]));
-  } else {
-    float p0 = __fsub_rn(__fsub_rn(c.v[0], c.v[1]), __fsub_rn(c.v[2], c.v[3]));
-    float p1 = __fsub_rn(__fsub_rn(c.v[4], c.v[5]), __fsub_rn(c.v[6], c.v[7]));
-    return __fsub_rn(p0, p1);
-  }
-}
-
-__device__ __forceinline__ int est_symbol(float r, float inv, int R) {
-  float q = rintf(__fmul_rn(r, inv));
-  return fabsf(q) < (float)R ? (int)q + kCenter : 0;
-}
-
-// Integer Lorenzo residual of the prequantised codes: sum over the cell's
-// corners of (-1)^(steps back) Q.
-template <int D>
-__device__ __forceinline__ int gt_residual(const Nbr& c, float inv) {
-  int r = 0;
-#pragma unroll
-  for (int m = 0; m < (1 << D); m++) {
-    int q = __float2int_rn(__fmul_rn(c.v[m], inv));
-    r += (__popc(m) & 1) ? -q : q;
-  }
-  return r;
-}
-
-template <int D>
-__device__ __forceinline__ void point_coords(const FieldDev& f, long long u, int* g) {
-  long long r = u;
-#pragma unroll
-  for (int k = D - 1; k >= 0; k--) {
-    g[k] = (int)(r % f.n[k]);
-    r /= f.n[k];
-  }
-}
-
-template <int D>
-__device__ __forceinline__ bool in_sampled_block(const FieldDev& f, const int* g) {
-  bool s = true;
-#pragma unroll
-  for (int k = 0; k < D; k++) s = s && (((g[k] >> 2) % f.s[k]) == 0);
-  return s;
-}
-
-// ---------------------------------------------------------------------------
-// Estimator over the points of sampled blocks only: one thread per sampled
-// block.  The thread reads the block with its one-cell halo on the low side
-// ((4+1)^d values, zero outside the domain), a plane at a time: the 2D
-// nested difference of each of the 16 points of a plane, minus that of the
-// plane behind, is the 3D residual, in the same float32 operations and
-// order as est_residual.
-// ---------------------------------------------------------------------------
-// Row y of plane z, values x0-1 .. x0+3 (zero outside the domain; values past
-// the far edges feed no valid point and read as zero).
-__device__ __forceinline__ void load_halo_row(const FieldDev& f, long long row, bool row_ok, int x0,
-                                              float* v) {
-  const int nx = f.n[f.d - 1];
-  if (!row_ok) {
-#pragma unroll
-    for (int k = 0; k < 5; k++) v[k] = 0.0f;
-    return;
-  }
-  const float* __restrict__ p = f.x + row * nx;
-  v[0] = x0 > 0 ? __ldg(p + x0 - 1) : 0.0f;
-  if (f.vec_ok && x0 + 4 <= nx) {
-    const float4 q = __ldg(reinterpret_cast<const float4*>(p + x0));
-    v[1] = q.x;
-    v[2] = q.y;
-    v[3] = q.z;
-    v[4] = q.w;
-  } else {
-#pragma unroll
-    for (int k = 0; k < 4; k++) v[k + 1] = x0 + k < nx ? __ldg(p + x0 + k) : 0.0f;
-  }
-}
-
-// Lattice index of a sampled block -> its first point per axis.
-template <int D>
-__device__ __forceinline__ void sampled_block_origin(const FieldDev& f, long long sb, int* o) {
-  long long r = sb;
-#pragma unroll
-  for (int k = D - 1; k >= 0; k--) {
-    const int l = (int)(r % f.L[k]);
-    r /= f.L[k];
-    o[k] = 4 * l * f.s[k];
-  }
-}
-
-template <int D>
-__device__ __forceinline__ void sz_est_block(const FieldDev& f, long long sb, bool active, float inv,
-                                             int R, uint32_t* s_win, uint32_t* g_hist) {
-  int o[3] = {0, 0, 0};
-  if (active) sampled_block_origin<D>(f, sb, o);
-  if constexpr (D == 1) {
-    float v[5];
-    load_halo_row(f, 0, active, o[0], v);
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-      const bool ok = active && o[0] + k < f.n[0];
-      const unsigned mask = __ballot_sync(0xffffffffu, ok);
-      if (ok) hist_add(s_win, g_hist, est_symbol(__fsub_rn(v[k + 1], v[k]), inv, R), mask);
-    }
-  } else {
-    const int ny = f.n[D - 2], nx = f.n[D - 1];
-    const int y0 = o[D - 2], x0 = o[D - 1];
-    // 2D nested differences of the 16 points of plane z (rows y0-1 .. y0+3)
-    auto plane = [&](int z, bool z_ok, float* d2) {
-      float v[5][5];
-#pragma unroll
-      for (int r = 0; r < 5; r++) {
-        const int y = y0 - 1 + r;
-        const bool ok = z_ok && y >= 0 && y < ny;
-        const long long row = (D == 3 ? (long long)z * ny : 0ll) + y;
-        load_halo_row(f, row, ok, x0, v[r]);
-      }
-#pragma unroll
-      for (int j = 0; j < 4; j++)
-#pragma unroll
-        for (int k = 0; k < 4; k++)
-          d2[4 * j + k] = __fsub_rn(__fsub_rn(v[j + 1][k + 1], v[j + 1][k]),
-                                    __fsub_rn(v[j][k + 1], v[j][k]));
-    };
-    float prev[16];
-    const int nz = D == 3 ? f.n[0] : 1;
-    const int z0 = D == 3 ? o[0] : 0;
-    if (D == 3) plane(z0 - 1, active && z0 > 0, prev);
-#pragma unroll 1
-    for (int i = 0; i < (D == 3 ? 4 : 1); i++) {
-      const int z = z0 + i;
-      const bool z_ok = active && z < nz;
-      float cur[16];
-      plane(z, z_ok, cur);
-#pragma unroll
-      for (int t = 0; t < 16; t++) {
-        const int j = t >> 2, k = t & 3;
-        const bool ok = z_ok && y0 + j < ny && x0 + k < nx;
-        const unsigned mask = __ballot_sync(0xffffffffu, ok);
-        const float r = D == 3 ? __fsub_rn(cur[t], prev[t]) : cur[t];
-        if (ok) hist_add(s_win, g_hist, est_symbol(r, inv, R), mask);
-      }
-      if (D == 3) {
-#pragma unroll
-        for (int t = 0; t < 16; t++) prev[t] = cur[t];
-      }
-    }
-  }
-}
-
+// Estimator: one thread per sampled block (sz_est_block), grid-strided.
 template <int D>
 __global__ void __launch_bounds__(kSzThreads) k_sz_est(FieldDev f, ParamsDev p, Workspace* ws) {
   __shared__ uint32_t s_win[kHistWin];
@@ -336,60 +152,6 @@ int sz_occupancy(int d, int num_sms) {
     per = 1;
   long long g = (long long)per * num_sms;
   return (int)(g > kMaxGrid ? kMaxGrid : g);
-}
-
-// ---------------------------------------------------------------------------
-// Batched estimate: the sampled blocks of many fields.  Each work item is a
-// run of sampled blocks of one field; its histogram window lives in shared
-// memory and is added to the field's histogram when the item ends.
-// ---------------------------------------------------------------------------
-template <int D>
-__device__ __forceinline__ void sz_est_item(const FieldDev& f, int R, float inv, uint32_t* g_hist,
-                                            long long u0, long long u1, uint32_t* s_win) {
-  for (long long b0 = u0; b0 < u1; b0 += blockDim.x) {
-    const long long sb = b0 + threadIdx.x;
-    sz_est_block<D>(f, sb, sb < u1, inv, R, s_win, g_hist);
-  }
-}
-
-__global__ void __launch_bounds__(kSzThreads) k_batch_sz_est(const BatchField* __restrict__ bf,
-                                                             const BatchItem* __restrict__ items,
-                                                             int nitems) {
-  __shared__ uint32_t s_win[kHistWin];
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const BatchItem item = items[it];
-    const BatchField& F = bf[item.field];
-    Workspace* ws = F.ws;
-    if (ws->sc.status != RD_OK || ws->sc.constant) continue;  // uniform over the CTA
-    for (int i = threadIdx.x; i < kHistWin; i += blockDim.x) s_win[i] = 0u;
-    __syncthreads();
-    const float inv = ws->sc.inv;
-    switch (F.f.d) {
-      case 1: sz_est_item<1>(F.f, F.p.R, inv, ws->hist[0], item.begin, item.end, s_win); break;
-      case 2: sz_est_item<2>(F.f, F.p.R, inv, ws->hist[0], item.begin, item.end, s_win); break;
-      default: sz_est_item<3>(F.f, F.p.R, inv, ws->hist[0], item.begin, item.end, s_win); break;
-    }
-    __syncthreads();
-    hist_flush(s_win, ws->hist[0]);
-    __syncthreads();
-  }
-}
-
-cudaError_t launch_batch_sz_est(const BatchField* bf, const BatchItem* items, int nitems, int ctas,
-                                cudaStream_t s) {
-  int g = nitems < ctas ? nitems : ctas;
-  if (g < 1) g = 1;
-  k_batch_sz_est<<<g, kSzThreads, 0, s>>>(bf, items, nitems);
-  return cudaGetLastError();
-}
-
-int batch_sz_occupancy(int num_sms) {
-  int per = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void*)k_batch_sz_est, kSzThreads, 0) !=
-          cudaSuccess ||
-      per < 1)
-    per = 1;
-  return per * num_sms;
 }
 
 // ---------------------------------------------------------------------------

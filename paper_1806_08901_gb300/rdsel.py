@@ -78,8 +78,7 @@ class rd_truth(C.Structure):
 
 class rd_batch_config(C.Structure):
     _fields_ = [("range_values", C.c_int64), ("zfp_blocks", C.c_int32), ("sz_blocks", C.c_int32),
-                ("range_ctas", C.c_int32), ("zfp_ctas", C.c_int32), ("sz_ctas", C.c_int32),
-                ("tuned", C.c_int32)]
+                ("ctas", C.c_int32), ("tuned", C.c_int32)]
 
 
 # Every symbol include/rdsel.h declares, with its ctypes signature.

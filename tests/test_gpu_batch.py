@@ -114,14 +114,14 @@ def test_autotuner_picks_a_candidate_split(R, ctx, dev_fields):
     assert cfg["range_values"] in (1 << 16, 1 << 18, 1 << 20)
     assert cfg["zfp_blocks"] in (256, 1024, 4096)
     assert cfg["sz_blocks"] in (256, 1024, 4096)
-    assert min(cfg["range_ctas"], cfg["zfp_ctas"], cfg["sz_ctas"]) >= 1
+    assert cfg["ctas"] == 0
 
 
 @pytest.mark.parametrize("cfg", [
     {"range_values": 1 << 12, "zfp_blocks": 32, "sz_blocks": 8},
     {"range_values": 1 << 22, "zfp_blocks": 1 << 14, "sz_blocks": 1 << 14},
-    {"range_values": 4100, "zfp_blocks": 77, "sz_blocks": 45, "range_ctas": 7, "zfp_ctas": 3,
-     "sz_ctas": 5},
+    {"range_values": 4100, "zfp_blocks": 77, "sz_blocks": 45, "ctas": 7},
+    {"range_values": 1 << 16, "zfp_blocks": 1024, "sz_blocks": 1024, "ctas": 1},
 ])
 def test_work_split_and_graph_replay_change_nothing(R, ctx, dev_fields, singles, cfg):
     ctx.batch_set_config(cfg)
