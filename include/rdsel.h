@@ -238,6 +238,64 @@ int32_t rd_batch_set_config(rd_context* ctx, const rd_batch_config* cfg);
 /* The work split of the last batch call. */
 int32_t rd_batch_get_config(rd_context* ctx, rd_batch_config* out);
 
+/* ---- serving loop ----------------------------------------------------- */
+
+/* An in-situ request loop: per-field selection requests (rd_select on one
+ * field each) arrive at any time and are served by `slots` host threads,
+ * each with its own context and CUDA stream, so that the work of requests
+ * in different slots overlaps on the device.  A free slot takes the first
+ * admissible request among the first `window` pending ones (continuous
+ * admission).  A request on a HOST field keeps a device copy of its field
+ * resident under the caller's field key: it is admitted when the key is
+ * resident (a hit), or when the HBM budget has room after evicting unpinned
+ * resident fields, least recently used first; key 0 makes the copy
+ * transient.  A request on a DEVICE field uses the caller's memory and does
+ * not count against the budget.  The paper has no serving loop; this is the
+ * in-situ deployment of its selection. */
+typedef struct rd_server rd_server;
+
+typedef struct {
+  int32_t device;
+  int32_t slots;        /* concurrent requests on the device, 1..64 */
+  int32_t window;       /* pending requests a free slot considers, >= 1 */
+  int32_t pad;
+  uint64_t hbm_budget;  /* bytes of resident host fields; 0 = no bound */
+} rd_server_config;
+
+typedef struct {
+  uint64_t request_id, tag;
+  int32_t status;        /* RD_OK or the rd_select / copy error of the request */
+  int32_t resident_hit;  /* 1: the field was already resident */
+  double queue_ms;       /* submission to start of service */
+  double service_ms;     /* start of service to completion (copy + estimate) */
+  double latency_ms;     /* submission to completion */
+  rd_result result;
+} rd_server_completion;
+
+typedef struct {
+  uint64_t submitted, completed, rejected, pending;
+  uint64_t resident_hits, evictions, resident_fields, resident_bytes;
+  double p50_ms, p99_ms, mean_ms, max_ms;  /* latency of completed requests */
+} rd_server_stats;
+
+/* Start the slots.  Errors: RD_ERR_INVALID_ARG, RD_ERR_CUDA, RD_ERR_OOM. */
+int32_t rd_server_create(const rd_server_config* cfg, rd_server** out);
+/* Queue a request.  The field memory (host or device) must stay valid and
+ * unchanged until the request completes; field_key != 0 names a host field
+ * whose device copy may stay resident (the same key must mean the same
+ * values).  RD_ERR_BUDGET: a host field larger than the whole budget. */
+int32_t rd_server_submit(rd_server* srv, const rd_field* field,
+                         const rd_params* params, uint64_t field_key,
+                         uint64_t tag, uint64_t* request_id);
+/* Take up to max completions (waiting up to wait_ms for the first). */
+int32_t rd_server_poll(rd_server* srv, rd_server_completion* out,
+                       int32_t max, int32_t wait_ms, int32_t* n);
+/* Counters and latency percentiles (nearest rank) since the last reset. */
+int32_t rd_server_get_stats(rd_server* srv, rd_server_stats* out);
+int32_t rd_server_reset_stats(rd_server* srv);
+/* Serve every pending request, stop the slots, free resident copies. */
+int32_t rd_server_destroy(rd_server* srv);
+
 /* ---- inspection (same kernels, per-element outputs) ------------------ */
 
 /* Copy the histograms of the last SZ estimate / SZ ground truth run on this

@@ -81,6 +81,25 @@ class rd_batch_config(C.Structure):
                 ("ctas", C.c_int32), ("tuned", C.c_int32)]
 
 
+class rd_server_config(C.Structure):
+    _fields_ = [("device", C.c_int32), ("slots", C.c_int32), ("window", C.c_int32),
+                ("pad", C.c_int32), ("hbm_budget", C.c_uint64)]
+
+
+class rd_server_completion(C.Structure):
+    _fields_ = [("request_id", C.c_uint64), ("tag", C.c_uint64), ("status", C.c_int32),
+                ("resident_hit", C.c_int32), ("queue_ms", C.c_double), ("service_ms", C.c_double),
+                ("latency_ms", C.c_double), ("result", rd_result)]
+
+
+class rd_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("rejected", C.c_uint64),
+                ("pending", C.c_uint64), ("resident_hits", C.c_uint64), ("evictions", C.c_uint64),
+                ("resident_fields", C.c_uint64), ("resident_bytes", C.c_uint64),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double),
+                ("max_ms", C.c_double)]
+
+
 # Every symbol include/rdsel.h declares, with its ctypes signature.
 _P = C.POINTER
 _SIGNATURES = {
@@ -99,6 +118,14 @@ _SIGNATURES = {
                                     _P(rd_result), _P(rd_truth), _P(C.c_int32), C.c_void_p]),
     "rd_batch_set_config": (C.c_int32, [C.c_void_p, _P(rd_batch_config)]),
     "rd_batch_get_config": (C.c_int32, [C.c_void_p, _P(rd_batch_config)]),
+    "rd_server_create": (C.c_int32, [_P(rd_server_config), _P(C.c_void_p)]),
+    "rd_server_submit": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), C.c_uint64,
+                                     C.c_uint64, _P(C.c_uint64)]),
+    "rd_server_poll": (C.c_int32, [C.c_void_p, _P(rd_server_completion), C.c_int32, C.c_int32,
+                                   _P(C.c_int32)]),
+    "rd_server_get_stats": (C.c_int32, [C.c_void_p, _P(rd_server_stats)]),
+    "rd_server_reset_stats": (C.c_int32, [C.c_void_p]),
+    "rd_server_destroy": (C.c_int32, [C.c_void_p]),
     "rd_copy_histograms": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "rd_zfp_blocks": (C.c_int32, [C.c_void_p, _P(rd_field), C.c_double, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -414,6 +441,67 @@ def rd_kernel_stats(ctx) -> dict:
 
 def rd_launch_count(ctx) -> int:
     return int(lib().rd_launch_count(ctx))
+
+
+class Server:
+    """Owns one rd_server (the serving loop).  submit() keeps a reference to
+    the field until its completion has been polled, since the library reads
+    the field's memory while the request is pending or running."""
+
+    def __init__(self, device: int = 0, slots: int = 4, window: int = 8, hbm_budget: int = 0):
+        cfg = rd_server_config(int(device), int(slots), int(window), 0, int(hbm_budget))
+        h = C.c_void_p()
+        _check(lib().rd_server_create(C.byref(cfg), C.byref(h)), "rd_server_create")
+        self.h = h
+        self._keep = {}
+
+    def submit(self, x, prm: rd_params, key: int = 0, tag: int = 0) -> int:
+        f, keep = make_field(x)
+        rid = C.c_uint64()
+        _check(lib().rd_server_submit(self.h, C.byref(f), C.byref(prm), int(key), int(tag),
+                                      C.byref(rid)), "rd_server_submit")
+        self._keep[rid.value] = (keep, prm)
+        return rid.value
+
+    def poll(self, max_n: int = 256, wait_ms: int = 0) -> list:
+        buf = (rd_server_completion * max_n)()
+        n = C.c_int32()
+        _check(lib().rd_server_poll(self.h, buf, int(max_n), int(wait_ms), C.byref(n)),
+               "rd_server_poll")
+        out = []
+        for i in range(n.value):
+            c = buf[i]
+            self._keep.pop(c.request_id, None)
+            d = {k: getattr(c, k) for k, _ in rd_server_completion._fields_ if k != "result"}
+            d["result"] = _todict(c.result)
+            out.append(d)
+        return out
+
+    def stats(self) -> dict:
+        st = rd_server_stats()
+        _check(lib().rd_server_get_stats(self.h, C.byref(st)), "rd_server_get_stats")
+        return _todict(st)
+
+    def reset_stats(self) -> None:
+        _check(lib().rd_server_reset_stats(self.h), "rd_server_reset_stats")
+
+    def close(self):
+        if self.h:
+            _check(lib().rd_server_destroy(self.h), "rd_server_destroy")
+            self.h = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Context:

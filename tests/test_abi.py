@@ -47,7 +47,10 @@ def test_struct_layout_matches_header(rdsel, tmp_path):
     compare sizeof / offsetof with the ctypes mirrors."""
     structs = {"rd_field": rdsel.rd_field, "rd_params": rdsel.rd_params,
                "rd_result": rdsel.rd_result, "rd_truth": rdsel.rd_truth,
-               "rd_batch_config": rdsel.rd_batch_config}
+               "rd_batch_config": rdsel.rd_batch_config,
+               "rd_server_config": rdsel.rd_server_config,
+               "rd_server_completion": rdsel.rd_server_completion,
+               "rd_server_stats": rdsel.rd_server_stats}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rdsel.h"', "int main(void){"]
     for sname, cls in structs.items():
         lines.append(f'printf("{sname} sizeof %zu\\n", sizeof({sname}));')
