@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched-snapshot measurement")
     ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--serve-population", type=int, default=64)
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-rates", default="100,500,2000")
     return ap.parse_args()
 
 
@@ -247,6 +251,73 @@ def bench_snapshot(R, ctx, stream, steps: int, peak: float, peak_kind: str):
     return out
 
 
+SERVE_WORKLOAD = "serving_poisson_2d512-1800x3600_3d64-512cubed_f32"
+
+
+def bench_serving(R, population: int, n_req: int, rates, budget: int = 120 << 30):
+    """The serving loop under Poisson arrivals: requests name fields of a
+    population held in pinned host memory (2D ny ~ logU[512, 1800], nx ~
+    logU[512, 3600], or 3D cubes with side ~ logU[64, 512]; spectra k^a, a ~
+    U[-4, -2]) and an error bound from {1e-2 .. 1e-6}; each field stays
+    resident on the device after its first request (120 GB budget).  Every
+    field is requested once before the timed rates."""
+    import time
+
+    import torch
+
+    import synth
+
+    specs = synth.serving_population(seed=synth.seed_for(5), population=population)
+    fields = []
+    for sp in specs:
+        g = synth.grf_torch(tuple(sp["shape"]), sp["alpha"], sp["seed"])
+        h = torch.empty(g.shape, dtype=torch.float32, pin_memory=True)
+        h.copy_(g)
+        fields.append(h)
+        del g
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    prm = {eb: R.params(eb=eb, r_sp=R_SP) for eb in (1e-2, 1e-3, 1e-4, 1e-5, 1e-6)}
+    out = {"workload": SERVE_WORKLOAD, "population": population, "hbm_budget_bytes": budget,
+           "population_bytes": sum(4 * f.numel() for f in fields), "slots": 4, "rates": []}
+    with R.Server(0, slots=4, window=16, hbm_budget=budget) as srv:
+        for i, f in enumerate(fields):  # first touch: copy in
+            srv.submit(f, prm[1e-4], key=1 + i, tag=i)
+        got = 0
+        while got < len(fields):
+            got += len(srv.poll(256, wait_ms=5000))
+        for k, rate in enumerate(rates):
+            reqs = synth.serving_requests(rate, n_req, seed=synth.seed_for(5, 100 + k),
+                                          population=population)
+            srv.reset_stats()
+            done = 0
+            nbytes = 0
+            t0 = time.perf_counter()
+            for i, r in enumerate(reqs):
+                while True:
+                    now = time.perf_counter() - t0
+                    if now >= r["t"]:
+                        break
+                    if r["t"] - now > 2e-3:
+                        time.sleep(r["t"] - now - 1e-3)
+                eb = min(prm, key=lambda e: abs(e - r["eb_rel"]))
+                srv.submit(fields[r["field"]], prm[eb], key=1 + r["field"], tag=i)
+                nbytes += 4 * fields[r["field"]].numel()
+                done += len(srv.poll(256, wait_ms=0))
+            while done < len(reqs):
+                done += len(srv.poll(256, wait_ms=5000))
+            wall = time.perf_counter() - t0
+            st = srv.stats()
+            out["rates"].append({
+                "rate_req_s": rate, "requests": len(reqs), "wall_s": wall,
+                "throughput_req_s": len(reqs) / wall, "throughput_GB_s": nbytes / wall / 1e9,
+                "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+                "max_ms": st["max_ms"], "resident_hits": st["resident_hits"],
+                "evictions": st["evictions"]})
+    del fields
+    return out
+
+
 def cpu_baseline(x_host, planes: int, steps: int = 1):
     """Time the oracle (select + ground truth) on the first `planes` planes."""
     import oracle as O
@@ -430,6 +501,9 @@ def main():
     }
     if not args.no_batch and world == 1:
         line["batched"] = bench_snapshot(R, ctx, stream, args.batch_steps, peak, peak_kind)
+    if not args.no_serve and world == 1:
+        rates = [float(v) for v in args.serve_rates.split(",") if v]
+        line["serving"] = bench_serving(R, args.serve_population, args.serve_requests, rates)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(x.cpu().numpy(), args.cpu_planes, 1)
     if rank == 0:
