@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched-snapshot measurement")
     ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--batch-subset", default="all", choices=["all", "small"],
+                    help="small: 20 ATM + 2 Hurricane + 1 512^3 fields (1.3 GB), for profiling")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
     ap.add_argument("--serve-population", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=400)
@@ -165,7 +167,7 @@ def snapshot_alg_bytes(fields, r_sp: float) -> float:
     return tot
 
 
-def bench_snapshot(R, ctx, stream, steps: int, peak: float, peak_kind: str):
+def bench_snapshot(R, ctx, stream, steps: int, peak: float, peak_kind: str, subset: str = "all"):
     """The batched estimate of a whole snapshot (79 2D 1800x3600, 13
     100x500x500 and 6 512^3 fields, 6.57 GB, far larger than L2) in one
     rd_select_batch call, against the same fields through per-field rd_select
@@ -177,6 +179,8 @@ def bench_snapshot(R, ctx, stream, steps: int, peak: float, peak_kind: str):
     import synth
 
     specs = synth.snapshot_specs()
+    if subset == "small":
+        specs = specs[:20] + specs[79:81] + specs[92:93]
     fields = [synth.make_field_torch(sp) for sp in specs]
     torch.cuda.synchronize()
     prms = [R.params(eb=sp["eb_rel"], r_sp=R_SP) for sp in specs]
@@ -234,7 +238,8 @@ def bench_snapshot(R, ctx, stream, steps: int, peak: float, peak_kind: str):
     alg = snapshot_alg_bytes(fields, R_SP)
     achieved = alg / (batch_ms / 1e3) / 1e9
     out = {
-        "workload": SNAPSHOT, "fields": len(fields), "field_bytes": nbytes, "r_sp": R_SP,
+        "workload": SNAPSHOT if subset == "all" else SNAPSHOT + "_subset20+2+1", "fields": len(fields),
+        "field_bytes": nbytes, "r_sp": R_SP,
         "eb_rel": "per field from {1e-3,1e-4,1e-5}", "l2": "inputs 6.6 GB, larger than L2",
         "ms": batch_ms, "value": nbytes / (batch_ms / 1e3) / 1e9, "unit": "GB/s",
         "plain_ms": plain_ms, "plain_value": nbytes / (plain_ms / 1e3) / 1e9,
@@ -517,7 +522,8 @@ def main():
                    "psnr_zfp": est_ref["psnr_zfp"], "psnr_zfp_gt": truth_ref["psnr_zfp_gt"]},
     }
     if not args.no_batch and world == 1:
-        line["batched"] = bench_snapshot(R, ctx, stream, args.batch_steps, peak, peak_kind)
+        line["batched"] = bench_snapshot(R, ctx, stream, args.batch_steps, peak, peak_kind,
+                                         args.batch_subset)
     if not args.no_serve and world == 1:
         rates = [float(v) for v in args.serve_rates.split(",") if v]
         line["serving"] = bench_serving(R, args.serve_population, args.serve_requests, rates)
