@@ -198,8 +198,8 @@ int32_t rd_select_static(const rd_field* field, const rd_params* params,
 /* Work split of the batched estimate.  The results do not depend on it. */
 typedef struct {
   int64_t range_values; /* values per range work item (rounded up to a multiple of 4) */
-  int32_t zfp_blocks;   /* sampled ZFP blocks per work item */
-  int32_t sz_blocks;    /* sampled SZ blocks per work item */
+  int32_t zfp_blocks;   /* sampled blocks per work item of the block pass */
+  int32_t sz_blocks;    /* sampled blocks per work item of the SZ histogram */
   int32_t ctas;         /* cap on each pass's CTAs; 0 = every CTA the SMs hold at once */
   int32_t tuned;        /* output: 1 when the autotuner chose this split */
 } rd_batch_config;
@@ -208,11 +208,12 @@ typedef struct {
  * simulation snapshot, of uneven 2D/3D sizes (the paper's algorithm loops
  * over the fields of a snapshot).  Six launches cover all fields: a reset;
  * three persistent passes over work items of every field (runs of a field's
- * values for the range, runs of its sampled blocks for the ZFP and the SZ
- * estimates; the CTA that ends a field's last range item derives VR and
- * eb_abs, the one that ends its last ZFP item derives delta); the
- * count-of-counts; one CTA per field for the Huffman cost, entropy, rates,
- * PSNRs and selection.
+ * values for the range; runs of its sampled blocks, read once for both
+ * estimators, for the ZFP estimate and the SZ residuals; the stored
+ * residuals for the SZ histogram; the CTA that ends a field's last range
+ * item derives VR and eb_abs, the one that ends its last block item derives
+ * delta); the count-of-counts; one CTA per field for the Huffman cost,
+ * entropy, rates, PSNRs and selection.
  *  - fields[i]: DEVICE memory only (RD_ERR_INVALID_ARG otherwise);
  *    params[i]: the parameters of field i.  n >= 1.
  *  - results[n] is required; truths[n] may be NULL, else each field's ground

@@ -21,7 +21,7 @@ namespace {
 const char* kKernelNames[K_COUNT] = {
     "reset", "range", "prepare", "zfp_pass", "delta", "sz_est", "sz_pass",
     "code_prep", "huffman", "finish", "zfp_inspect", "sz_inspect",
-    "batch_reset", "batch_range", "batch_zfp_est", "batch_sz_est", "batch_code_prep",
+    "batch_reset", "batch_range", "batch_blocks", "batch_sz_hist", "batch_code_prep",
     "batch_final", "batch_truth"};
 
 struct KStat {
@@ -79,7 +79,9 @@ struct BatchPlan {
   std::vector<BatchField> hbf;
   std::vector<Geometry> geo;
   BatchField* dbf = nullptr;
-  BatchItem* ditems = nullptr;  // range items, then ZFP items, then SZ items
+  BatchItem* ditems = nullptr;  // range items, then sampled-block items, then SZ items
+  float* dres = nullptr;        // SZ residuals of every field's sampled blocks
+  size_t res_bytes = 0;
   int n_range = 0, n_zfp = 0, n_sz = 0;
   cudaGraphExec_t exec = nullptr;
   std::vector<Pending> events;
@@ -541,11 +543,15 @@ void free_plan(BatchPlan* b) {
   }
   if (b->dbf) cudaFree(b->dbf);
   if (b->ditems) cudaFree(b->ditems);
+  if (b->dres) cudaFree(b->dres);
   delete b;
 }
 
 void drop_plans(rd_context* c) {
-  for (BatchPlan* b : c->plans) free_plan(b);
+  for (BatchPlan* b : c->plans) {
+    c->held -= b->res_bytes;
+    free_plan(b);
+  }
   c->plans.clear();
 }
 
@@ -680,13 +686,13 @@ int issue_batch_estimate(rd_context* c, BatchPlan* b, cudaStream_t s, cudaEvent_
        })))
     return rc;
   if ((rc = launch(c, K_B_ZFP, s, [&] {
-         return launch_batch_zfp_est(b->dbf, b->ditems + b->n_range, b->n_zfp,
-                                     pass_ctas(c->b_zfp_ctas, cap), s);
+         return launch_batch_blocks(b->dbf, b->ditems + b->n_range, b->n_zfp,
+                                    pass_ctas(c->b_zfp_ctas, cap), s);
        })))
     return rc;
   if ((rc = launch(c, K_B_SZ, s, [&] {
-         return launch_batch_sz_est(b->dbf, b->ditems + b->n_range + b->n_zfp, b->n_sz,
-                                    pass_ctas(c->b_sz_ctas, cap), s);
+         return launch_batch_sz_hist(b->dbf, b->ditems + b->n_range + b->n_zfp, b->n_sz,
+                                     pass_ctas(c->b_sz_ctas, cap), s);
        })))
     return rc;
   if (ev) cudaEventRecord(ev[1], s);
@@ -817,6 +823,7 @@ int batch_call(rd_context* c, const rd_field* fields, const rd_params* params, i
       size_t lru = 0;
       for (size_t i = 1; i < c->plans.size(); i++)
         if (c->plans[i]->last_use < c->plans[lru]->last_use) lru = i;
+      c->held -= c->plans[lru]->res_bytes;
       free_plan(c->plans[lru]);
       c->plans.erase(c->plans.begin() + lru);
     }
@@ -827,6 +834,21 @@ int batch_call(rd_context* c, const rd_field* fields, const rd_params* params, i
     b->need_gt = need_gt;
     b->geo = geo;
     b->hbf.resize((size_t)n);
+    // the SZ residuals of every field's sampled blocks (4^d floats each)
+    size_t res_floats = 0;
+    for (int i = 0; i < n; i++) res_floats += (size_t)geo[i].f.nsampled << (2 * geo[i].f.d);
+    b->res_bytes = res_floats * sizeof(float);
+    if (c->budget && c->held + b->res_bytes > c->budget) {
+      delete b;
+      return RD_ERR_BUDGET;
+    }
+    if (cudaMalloc(&b->dres, b->res_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      delete b;
+      return RD_ERR_OOM;
+    }
+    c->held += b->res_bytes;
+    size_t roff = 0;
     for (int i = 0; i < n; i++) {
       BatchField& F = b->hbf[i];
       memset(&F, 0, sizeof(F));
@@ -836,6 +858,8 @@ int batch_call(rd_context* c, const rd_field* fields, const rd_params* params, i
       F.ncoeff = (unsigned long long)F.f.nsampled * ec_count(F.f.d, params[i].ec_mode);
       F.npoints = geo[i].npoints_sampled;
       F.need_gt = need_gt;
+      F.res = b->dres + roff;
+      roff += (size_t)F.f.nsampled << (2 * F.f.d);
     }
     if (forced) {
       rd_batch_config cfg = c->batch_force;
@@ -849,6 +873,7 @@ int batch_call(rd_context* c, const rd_field* fields, const rd_params* params, i
       rc = autotune_plan(c, b, s);
     }
     if (rc) {
+      c->held -= b->res_bytes;
       free_plan(b);
       return rc;
     }

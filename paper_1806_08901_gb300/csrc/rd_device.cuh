@@ -222,6 +222,83 @@ __device__ __forceinline__ void hist_add(uint32_t* s_win, uint32_t* g_hist, int 
   }
 }
 
+// Warp-aggregated histogram insert without warp matching (whose unit runs it
+// at a low rate on this GPU): the warp sorts its 32 symbols with a bitonic
+// network of shuffles, and the first lane of every run of equal symbols adds
+// the run's length with one atomic (shared window [win_lo, win_lo + win),
+// else the global histogram).  Every lane of the warp calls; lanes with
+// ok == false contribute nothing.
+__device__ __forceinline__ void hist_add_sorted(uint32_t* s_win, int win_lo, int win,
+                                                uint32_t* g_hist, int sym, bool ok) {
+  const int lane = threadIdx.x & 31;
+  int key = ok ? sym : 0x7fffffff;
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const int other = __shfl_xor_sync(0xffffffffu, key, j);
+      const bool up = (lane & k) == 0;
+      const bool low = (lane & j) == 0;
+      key = (low == up) ? min(key, other) : max(key, other);
+    }
+  }
+  const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+  const bool head = lane == 0 || key != prev;
+  const unsigned heads = __ballot_sync(0xffffffffu, head);
+  if (head && key != 0x7fffffff) {
+    const unsigned later = heads & ~((2u << lane) - 1u);  // heads after this lane
+    const int next = later ? __ffs(later) - 1 : 32;
+    const unsigned cnt = (unsigned)(next - lane);
+    const int wi = key - win_lo;
+    if ((unsigned)wi < (unsigned)win)
+      atomicAdd(&s_win[wi], cnt);
+    else
+      atomicAdd(&g_hist[key], cnt);
+  }
+}
+
+// Per-thread register counters of the 2H+1 symbols around the centre, where
+// nearly every code of a smooth field falls: counting them costs a few
+// predicated adds and no atomics (contended shared-memory atomics on a few
+// hot bins, or warp matching, would set the pace).  Other symbols take a
+// plain atomic on the shared window (or the global histogram outside it).
+template <int H>
+struct HotBins {
+  uint32_t c[2 * H + 1];
+  __device__ __forceinline__ void clear() {
+#pragma unroll
+    for (int k = 0; k < 2 * H + 1; k++) c[k] = 0u;
+  }
+  // d = symbol - kCenter; true when counted here
+  __device__ __forceinline__ bool take(int d) {
+#pragma unroll
+    for (int k = 0; k < 2 * H + 1; k++) c[k] += d == k - H ? 1u : 0u;
+    return (unsigned)(d + H) <= (unsigned)(2 * H);
+  }
+  // count symbol sym: a hot bin, else the window at win_lo (width win), else
+  // the global histogram
+  __device__ __forceinline__ void add(int sym, uint32_t* s_win, int win_lo, int win,
+                                      uint32_t* g_hist) {
+    if (take(sym - kCenter)) return;
+    const int wi = sym - win_lo;
+    if ((unsigned)wi < (unsigned)win)
+      atomicAdd(&s_win[wi], 1u);
+    else
+      atomicAdd(&g_hist[sym], 1u);
+  }
+  // add the warp's counters to the window; every lane of the warp calls
+  __device__ __forceinline__ void flush_warp(uint32_t* s_win, int win_lo) {
+#pragma unroll
+    for (int k = 0; k < 2 * H + 1; k++) {
+      uint32_t v = c[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_win[kCenter - H + k - win_lo], v);
+    }
+    clear();
+  }
+};
+
 __device__ __forceinline__ void hist_flush(const uint32_t* s_win, uint32_t* g_hist) {
   for (int i = threadIdx.x; i < kHistWin; i += blockDim.x) {
     uint32_t c = s_win[i];

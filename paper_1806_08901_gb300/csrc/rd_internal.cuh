@@ -99,10 +99,11 @@ struct BatchField {
   FieldDev f;
   ParamsDev p;
   Workspace* ws;                 // the field's own workspace
+  float* res;                    // SZ residuals of the sampled blocks' points (4^d per block)
   unsigned long long ncoeff;     // EC-sampled coefficients (denominator of MSE_sp)
   unsigned long long npoints;    // valid points of the sampled blocks
   uint32_t items_range;          // range work items of the field
-  uint32_t items_zfp;            // ZFP estimate work items of the field
+  uint32_t items_zfp;            // sampled-block work items of the field
   int32_t need_gt;               // the quantiser is also prepared for the ground truth
   int32_t pad;
 };
@@ -201,11 +202,13 @@ cudaError_t launch_batch_reset(const BatchField* bf, int n, int need_gt, cudaStr
 // range; the CTA ending a field's last item derives VR, eb_abs, minexp
 cudaError_t launch_batch_range(const BatchField* bf, const BatchItem* items, int nitems, int ctas,
                                cudaStream_t s);
-// sampled ZFP blocks; the CTA ending a field's last item derives delta
-cudaError_t launch_batch_zfp_est(const BatchField* bf, const BatchItem* items, int nitems, int ctas,
-                                 cudaStream_t s);
-cudaError_t launch_batch_sz_est(const BatchField* bf, const BatchItem* items, int nitems, int ctas,
+// sampled blocks (ZFP estimate, stored SZ residuals); the CTA ending a
+// field's last item derives delta
+cudaError_t launch_batch_blocks(const BatchField* bf, const BatchItem* items, int nitems, int ctas,
                                 cudaStream_t s);
+// SZ histogram of the stored residuals
+cudaError_t launch_batch_sz_hist(const BatchField* bf, const BatchItem* items, int nitems, int ctas,
+                                 cudaStream_t s);
 // resident CTAs of the three passes
 void batch_occupancy(int num_sms, int* range_ctas, int* zfp_ctas, int* sz_ctas);
 cudaError_t launch_batch_code_prep(const BatchField* bf, int n, cudaStream_t s);

@@ -24,11 +24,14 @@ __global__ void __launch_bounds__(kSzThreads) k_sz_est(FieldDev f, ParamsDev p, 
   for (int i = threadIdx.x; i < kHistWin; i += blockDim.x) s_win[i] = 0u;
   __syncthreads();
   const float inv = sc.inv;
+  HotBins<2> hot;
+  hot.clear();
   for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < f.nsampled;
        b0 += (long long)gridDim.x * blockDim.x) {
     const long long sb = b0 + threadIdx.x;
-    sz_est_block<D>(f, sb, sb < f.nsampled, inv, p.R, s_win, ws->hist[0]);
+    sz_est_block<D>(f, sb, sb < f.nsampled, inv, p.R, s_win, ws->hist[0], hot);
   }
+  hot.flush_warp(s_win, kHistWinLo);
   __syncthreads();
   hist_flush(s_win, ws->hist[0]);
 }

@@ -136,7 +136,8 @@ __device__ __forceinline__ void sampled_block_origin(const FieldDev& f, long lon
 
 template <int D>
 __device__ __forceinline__ void sz_est_block(const FieldDev& f, long long sb, bool active, float inv,
-                                             int R, uint32_t* s_win, uint32_t* g_hist) {
+                                             int R, uint32_t* s_win, uint32_t* g_hist,
+                                             HotBins<2>& hot) {
   int o[3] = {0, 0, 0};
   if (active) sampled_block_origin<D>(f, sb, o);
   if constexpr (D == 1) {
@@ -145,8 +146,7 @@ __device__ __forceinline__ void sz_est_block(const FieldDev& f, long long sb, bo
 #pragma unroll
     for (int k = 0; k < 4; k++) {
       const bool ok = active && o[0] + k < f.n[0];
-      const unsigned mask = __ballot_sync(0xffffffffu, ok);
-      if (ok) hist_add(s_win, g_hist, est_symbol(__fsub_rn(v[k + 1], v[k]), inv, R), mask);
+      if (ok) hot.add(est_symbol(__fsub_rn(v[k + 1], v[k]), inv, R), s_win, kHistWinLo, kHistWin, g_hist);
     }
   } else {
     const int ny = f.n[D - 2], nx = f.n[D - 1];
@@ -182,25 +182,14 @@ __device__ __forceinline__ void sz_est_block(const FieldDev& f, long long sb, bo
       for (int t = 0; t < 16; t++) {
         const int j = t >> 2, k = t & 3;
         const bool ok = z_ok && y0 + j < ny && x0 + k < nx;
-        const unsigned mask = __ballot_sync(0xffffffffu, ok);
         const float r = D == 3 ? __fsub_rn(cur[t], prev[t]) : cur[t];
-        if (ok) hist_add(s_win, g_hist, est_symbol(r, inv, R), mask);
+        if (ok) hot.add(est_symbol(r, inv, R), s_win, kHistWinLo, kHistWin, g_hist);
       }
       if (D == 3) {
 #pragma unroll
         for (int t = 0; t < 16; t++) prev[t] = cur[t];
       }
     }
-  }
-}
-
-// Sampled blocks [u0, u1) of one field, one per thread.
-template <int D>
-__device__ __forceinline__ void sz_est_item(const FieldDev& f, int R, float inv, uint32_t* g_hist,
-                                            long long u0, long long u1, uint32_t* s_win) {
-  for (long long b0 = u0; b0 < u1; b0 += blockDim.x) {
-    const long long sb = b0 + threadIdx.x;
-    sz_est_block<D>(f, sb, sb < u1, inv, R, s_win, g_hist);
   }
 }
 
