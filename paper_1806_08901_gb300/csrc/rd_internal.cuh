@@ -18,7 +18,7 @@ constexpr int kMaxGrid = 4096;       // upper bound of CTAs of a reducing pass
 constexpr int kHistWin = 4096;       // shared-memory window of histogram bins
 constexpr int kHistWinLo = kCenter - kHistWin / 2;
 constexpr int kEntropyCtas = kNsym / 1024;
-constexpr int kHuffSmemKeys = 24576; // Huffman in shared memory up to this many symbols
+constexpr int kHuffSmemKeys = 28672; // Huffman with linear queues in shared memory up to this many symbols
 
 // Scalars produced and consumed on the device within one call: nothing
 // data-dependent (value range, bin width, error flags) leaves the device

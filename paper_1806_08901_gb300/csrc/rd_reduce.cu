@@ -162,8 +162,9 @@ __device__ void bitonic_sort(uint32_t* a, int n) {
 // the predicate A[i] <= B[d-1-i] holds for a prefix of i in [lo, hi].  A
 // 4-way search (three probes per step, loaded together) shortens the chain
 // of dependent loads, then binary steps finish.
-__device__ __forceinline__ uint32_t merge_split(const uint32_t* A, uint32_t na, const uint32_t* B,
-                                                uint32_t nb, uint32_t d) {
+template <class VA, class VB>
+__device__ __forceinline__ uint32_t merge_split(const VA& A, uint32_t na, const VB& B, uint32_t nb,
+                                                uint32_t d) {
   uint32_t lo = d > nb ? d - nb : 0u, hi = d < na ? d : na;
   while (hi - lo > 3u) {
     const uint32_t q = (hi - lo) >> 2;
@@ -200,8 +201,8 @@ constexpr uint32_t kMinPairs = 1;   // fewest pairs per thread in a Huffman phas
 // range still wider than 32 and keeps the gap holding the answer; a range of
 // at most 32 is answered by one ballot.  T < 2^33; a T of 2^32 or more
 // exceeds every 32-bit element.
-__device__ __forceinline__ void warp_count_below2(const uint32_t* a, uint32_t na,
-                                                  const uint32_t* b, uint32_t nb,
+template <class VA, class VB>
+__device__ __forceinline__ void warp_count_below2(const VA& a, uint32_t na, const VB& b, uint32_t nb,
                                                   unsigned long long T, uint32_t& ra,
                                                   uint32_t& rb) {
   if (T > 0xffffffffull) {
@@ -247,6 +248,59 @@ __device__ __forceinline__ void warp_count_below2(const uint32_t* a, uint32_t na
       }
     }
   }
+}
+
+// The internal-node queue of the run-length form (below) as a ring of cap
+// words: element k of the queue from position off.
+struct RingView {
+  const uint32_t* q;
+  uint32_t off, cap;
+  __device__ __forceinline__ uint32_t operator[](uint32_t k) const {
+    const uint32_t p = off + k;  // off < cap and k < cap
+    return q[p >= cap ? p - cap : p];
+  }
+};
+
+// The run holding leaf o: the last r with rs[r] <= o (rs[0] = 0).
+__device__ __forceinline__ uint32_t run_of(const uint32_t* rs, uint32_t R, uint32_t o) {
+  uint32_t lo = 0u, hi = R;
+  while (hi - lo > 1u) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (rs[mid] <= o) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// merge_split with the leaves in run-length form: A[i] is leaf lh + i, run r
+// holding leaves rs[r] .. rs[r+1]-1, all of weight rv[r].  The predicate
+// A[i] <= B[d-1-i] is tested first at the starts of runs, then inside the
+// one run where it turns false.  Returns the split and, in run, the run of
+// leaf lh + split.
+template <class VB>
+__device__ __forceinline__ uint32_t merge_split_runs(const uint32_t* rv, const uint32_t* rs,
+                                                     uint32_t R, uint32_t lh, uint32_t na,
+                                                     const VB& B, uint32_t nb, uint32_t d,
+                                                     uint32_t& run) {
+  const uint32_t lo = d > nb ? d - nb : 0u, hi = d < na ? d : na;
+  const uint32_t r0 = run_of(rs, R, lh + lo);
+  run = r0;
+  if (lo == hi || rv[r0] > B[d - 1 - lo]) return lo;
+  // the last run whose first leaf in [lo, hi) still satisfies the predicate
+  uint32_t a = r0, b = R;
+  while (b - a > 1u) {
+    const uint32_t mid = (a + b) >> 1;
+    const uint32_t s = rs[mid] - lh;  // > lo: mid is past the run of lo
+    if (s < hi && rv[mid] <= B[d - 1 - s]) a = mid; else b = mid;
+  }
+  const uint32_t v = rv[a];
+  const uint32_t end = rs[a + 1] - lh;
+  uint32_t l2 = (a == r0 ? lo : rs[a] - lh) + 1u, h2 = end < hi ? end : hi;
+  while (l2 < h2) {
+    const uint32_t mid = (l2 + h2) >> 1;
+    if (v <= B[d - 1 - mid]) l2 = mid + 1u; else h2 = mid;
+  }
+  run = l2 < end ? a : a + 1u;
+  return l2;
 }
 
 // ---------------------------------------------------------------------------
@@ -391,6 +445,131 @@ __device__ double block_sum_f64(double v, double* s_w) {
   return t;
 }
 
+// Phases of the two-queue merge with the leaves in run-length form, for
+// alphabets past the linear shared-memory form: the ascending leaves are
+// runs of equal weight (rv[r], first leaf rs[r]; the D distinct small
+// counts, then the large counts one run each), and the internal nodes live
+// in a ring of C words.  Before a phase the L live nodes are disjoint
+// subtrees of at least two leaves each, so L <= lh / 2 and the phase's new
+// nodes np <= ((K - lh) + L) / 2; L + np <= 3K/4 < C, so new nodes never
+// overwrite a node still to be read.  Returns this thread's share of the
+// cost.
+__device__ unsigned long long huffman_runs(const uint32_t* dv, uint32_t D, const uint32_t* big,
+                                           uint32_t nbig, uint32_t nsmall, uint32_t K,
+                                           uint32_t* s_dyn, uint32_t* s_w) {
+  const uint32_t tid = threadIdx.x;
+  const uint32_t R = D + nbig;
+  const uint32_t C = (3u * K + 3u) / 4u + 1u;
+  uint32_t* rv = s_dyn;
+  uint32_t* rs = s_dyn + R;
+  uint32_t* ring = s_dyn + 2u * R + 1u;
+  {
+    const uint32_t Cd = (D + kHuffThreads - 1) / kHuffThreads;
+    const uint32_t e0 = min(D, tid * Cd), e1 = min(D, e0 + Cd);
+    uint32_t mloc = 0u;
+    for (uint32_t d = e0; d < e1; d++) mloc += (dv[d] & 0xffffu) + 1u;
+    uint32_t tot;
+    uint32_t start = block_excl_sum(mloc, s_w, &tot);
+    for (uint32_t d = e0; d < e1; d++) {
+      const uint32_t q = dv[d];
+      rv[d] = q >> 16;
+      rs[d] = start;
+      start += (q & 0xffffu) + 1u;
+    }
+    for (uint32_t i = tid; i < nbig; i += kHuffThreads) rv[D + i] = big[i];
+    __syncthreads();
+    bitonic_sort(rv + D, (int)nbig);
+    for (uint32_t i = tid; i < nbig; i += kHuffThreads) rs[D + i] = nsmall + i;
+    if (tid == 0) rs[R] = K;
+    __syncthreads();
+  }
+  unsigned long long cost = 0ull;
+  uint32_t lh = 0u, ih = 0u, it = 0u;  // leaf head, node head, node tail
+  uint32_t ihr = 0u, itr = 0u;         // ring positions of ih and it
+  for (;;) {
+    if ((K - lh) + (it - ih) <= 1u) break;
+    if (tid < 32) {
+      const RingView B{ring, ihr, C};
+      unsigned long long c4[4] = {~0ull, ~0ull, ~0ull, ~0ull};
+      if (lh < K) {
+        const uint32_t r = run_of(rs, R, lh);
+        c4[0] = rv[r];
+        if (lh + 1u < K) c4[1] = lh + 1u < rs[r + 1u] ? rv[r] : rv[r + 1u];
+      }
+      if (ih < it) c4[2] = B[0];
+      if (ih + 1u < it) c4[3] = B[1];
+      const unsigned long long m01 = min(c4[0], c4[1]), x01 = max(c4[0], c4[1]);
+      const unsigned long long m23 = min(c4[2], c4[3]), x23 = max(c4[2], c4[3]);
+      const unsigned long long a0 = min(m01, m23);
+      const unsigned long long a1 = m01 < m23 ? min(x01, m23) : min(x23, m01);
+      // runs of weight below T end at leaf rs[rc]
+      uint32_t rc, mi;
+      warp_count_below2(rv, R, B, it - ih, a0 + a1, rc, mi);
+      const uint32_t first = rs[rc];
+      const uint32_t ml = first > lh ? first - lh : 0u;
+      uint32_t cl = ml;
+      if ((ml + mi) & 1u) {
+        if (mi == 0u || (ml > 0u && rv[rc - 1u] > B[mi - 1u])) cl = ml - 1u;
+      }
+      if (tid == 0) {
+        s_w[0] = ml;
+        s_w[1] = mi;
+        s_w[2] = cl;
+      }
+    }
+    __syncthreads();
+    const uint32_t ml = s_w[0], mi = s_w[1], cl = s_w[2];
+    const uint32_t np = (ml + mi) >> 1;
+    const uint32_t per_t = max(kMinPairs, (np + kHuffThreads - 1) / kHuffThreads);
+    const uint32_t j0 = tid * per_t;
+    const uint32_t j1 = min(np, j0 + per_t);
+    if (j0 < j1) {
+      const RingView B{ring, ihr, C};
+      uint32_t r;
+      uint32_t i = merge_split_runs(rv, rs, R, lh, ml, B, mi, 2u * j0, r);
+      uint32_t k = 2u * j0 - i;
+      uint32_t vA = r < R ? rv[r] : 0u;
+      uint32_t endA = r < R ? rs[r + 1u] - lh : 0xffffffffu;
+      uint32_t bp = ihr + k;
+      if (bp >= C) bp -= C;
+      uint32_t wp = itr + j0;
+      if (wp >= C) wp -= C;
+      for (uint32_t j = j0; j < j1; j++) {
+        uint32_t e[2];
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+          if (i < ml && (k >= mi || vA <= ring[bp])) {
+            e[u] = vA;
+            if (++i == endA) {
+              r++;
+              vA = r < R ? rv[r] : 0u;
+              endA = r < R ? rs[r + 1u] - lh : 0xffffffffu;
+            }
+          } else {
+            e[u] = ring[bp];
+            k++;
+            if (++bp == C) bp = 0u;
+          }
+        }
+        const uint32_t sum = e[0] + e[1];
+        ring[wp] = sum;
+        if (++wp == C) wp = 0u;
+        cost += sum;
+      }
+    }
+    __syncthreads();
+    const uint32_t used = 2u * np - cl;  // nodes consumed
+    lh += cl;
+    ih += used;
+    ihr += used;
+    if (ihr >= C) ihr -= C;
+    it += np;
+    itr += np;
+    if (itr >= C) itr -= C;
+  }
+  return cost;
+}
+
 // ---------------------------------------------------------------------------
 // Huffman cost and entropy sum (one CTA per histogram).
 //  1. The bitmap of present count values gives each its rank d in ascending
@@ -404,6 +583,10 @@ __device__ double block_sum_f64(double v, double* s_w) {
 //     the numbers of leaves and nodes below it, then the threads pair
 //     contiguous runs of the merged order (nodes are written only above the
 //     queue tail, which no thread reads until the next barrier).
+// Up to kHuffSmemKeys symbols both queues are linear in shared memory.
+// Larger alphabets keep the leaves as runs of equal weight and the nodes in
+// a ring, in shared memory (huffman_runs), when the runs fit; otherwise the
+// linear queues live in the workspace in global memory.
 // ---------------------------------------------------------------------------
 __device__ void huffman_cta(Workspace* ws, int which, const double* __restrict__ xlogx) {
   extern __shared__ uint32_t s_dyn[];
@@ -462,104 +645,111 @@ __device__ void huffman_cta(Workspace* ws, int which, const double* __restrict__
   const double plogp = block_sum_f64(ent, s_wd);
   const uint32_t K = nsmall + nbig;
 
-  // 2. leaves
-  uint32_t* leaves;
-  uint32_t* nodes;
-  if (K <= (uint32_t)kHuffSmemKeys) {
-    leaves = s_dyn;
-    nodes = s_dyn + kHuffSmemKeys;  // the distinct list lives here until the phases
-  } else {
-    leaves = ws->sort_scratch[which];
-    nodes = ws->node_scratch[which];  // free once the large counts are copied
-  }
-  const uint32_t Cd = (D + kHuffThreads - 1) / kHuffThreads;
-  const uint32_t e0 = min(D, (uint32_t)tid * Cd), e1 = min(D, e0 + Cd);
-  uint32_t mloc = 0u;
-  for (uint32_t d = e0; d < e1; d++) mloc += (dv[d] & 0xffffu) + 1u;
-  uint32_t tot;
-  uint32_t start = block_excl_sum(mloc, s_w, &tot);
-  for (uint32_t o = tid; o < nsmall; o += kHuffThreads) leaves[o] = 0u;
-  __syncthreads();
-  for (uint32_t d = e0; d < e1; d++) {
-    const uint32_t q = dv[d];
-    leaves[start] = q >> 16;
-    start += (q & 0xffffu) + 1u;
-  }
-  for (uint32_t i = tid; i < nbig; i += kHuffThreads) leaves[nsmall + i] = big[i];
-  __syncthreads();
-  {
-    const uint32_t C = (nsmall + kHuffThreads - 1) / kHuffThreads;
-    const uint32_t o0 = min(nsmall, (uint32_t)tid * C), o1 = min(nsmall, o0 + C);
-    uint32_t run = 0u;
-    for (uint32_t o = o0; o < o1; o++) run = max(run, leaves[o]);
-    uint32_t carry = block_excl_max(run, s_w);
-    for (uint32_t o = o0; o < o1; o++) {
-      carry = max(carry, leaves[o]);
-      leaves[o] = carry;
-    }
-  }
-  __syncthreads();
-  bitonic_sort(leaves + nsmall, (int)nbig);
-
-  // 3. phases
   unsigned long long cost = 0ull;
-  if (K == 1) {
-    cost = (tid == 0) ? ns : 0ull;
-  } else if (K > 1) {
-    uint32_t lh = 0u, ih = 0u, it = 0u;  // leaf head, node head, node tail
-    for (;;) {
-      if ((K - lh) + (it - ih) <= 1u) break;
-      if (tid < 32) {
-        unsigned long long c4[4] = {~0ull, ~0ull, ~0ull, ~0ull};
-        if (lh < K) c4[0] = leaves[lh];
-        if (lh + 1 < K) c4[1] = leaves[lh + 1];
-        if (ih < it) c4[2] = nodes[ih];
-        if (ih + 1 < it) c4[3] = nodes[ih + 1];
-        const unsigned long long m01 = min(c4[0], c4[1]), x01 = max(c4[0], c4[1]);
-        const unsigned long long m23 = min(c4[2], c4[3]), x23 = max(c4[2], c4[3]);
-        const unsigned long long a0 = min(m01, m23);
-        const unsigned long long a1 = m01 < m23 ? min(x01, m23) : min(x23, m01);
-        uint32_t ml, mi;
-        warp_count_below2(leaves + lh, K - lh, nodes + ih, it - ih, a0 + a1, ml, mi);
-        // leaves among the 2 np paired items: all ml, unless the count is
-        // odd and the last item below T in merged order (ties: leaves
-        // first) is a leaf; that item waits for the next phase
-        uint32_t cl = ml;
-        if ((ml + mi) & 1u) {
-          if (mi == 0u || (ml > 0u && leaves[lh + ml - 1] > nodes[ih + mi - 1])) cl = ml - 1u;
-        }
-        if (tid == 0) {
-          s_w[0] = ml;
-          s_w[1] = mi;
-          s_w[2] = cl;
-        }
+  const uint32_t R = D + nbig;
+  const bool runs = K > (uint32_t)kHuffSmemKeys && 2u * R + 1u <= (uint32_t)kHuffSmemKeys &&
+                    2u * R + 1u + (3u * K + 3u) / 4u + 1u <= 2u * (uint32_t)kHuffSmemKeys;
+  if (runs) {
+    cost = huffman_runs(dv, D, big, nbig, nsmall, K, s_dyn, s_w);
+  } else {
+    // 2. leaves
+    uint32_t* leaves;
+    uint32_t* nodes;
+    if (K <= (uint32_t)kHuffSmemKeys) {
+      leaves = s_dyn;
+      nodes = s_dyn + kHuffSmemKeys;  // the distinct list lives here until the phases
+    } else {
+      leaves = ws->sort_scratch[which];
+      nodes = ws->node_scratch[which];  // free once the large counts are copied
+    }
+    const uint32_t Cd = (D + kHuffThreads - 1) / kHuffThreads;
+    const uint32_t e0 = min(D, (uint32_t)tid * Cd), e1 = min(D, e0 + Cd);
+    uint32_t mloc = 0u;
+    for (uint32_t d = e0; d < e1; d++) mloc += (dv[d] & 0xffffu) + 1u;
+    uint32_t tot;
+    uint32_t start = block_excl_sum(mloc, s_w, &tot);
+    for (uint32_t o = tid; o < nsmall; o += kHuffThreads) leaves[o] = 0u;
+    __syncthreads();
+    for (uint32_t d = e0; d < e1; d++) {
+      const uint32_t q = dv[d];
+      leaves[start] = q >> 16;
+      start += (q & 0xffffu) + 1u;
+    }
+    for (uint32_t i = tid; i < nbig; i += kHuffThreads) leaves[nsmall + i] = big[i];
+    __syncthreads();
+    {
+      const uint32_t C = (nsmall + kHuffThreads - 1) / kHuffThreads;
+      const uint32_t o0 = min(nsmall, (uint32_t)tid * C), o1 = min(nsmall, o0 + C);
+      uint32_t run = 0u;
+      for (uint32_t o = o0; o < o1; o++) run = max(run, leaves[o]);
+      uint32_t carry = block_excl_max(run, s_w);
+      for (uint32_t o = o0; o < o1; o++) {
+        carry = max(carry, leaves[o]);
+        leaves[o] = carry;
       }
-      __syncthreads();
-      const uint32_t ml = s_w[0], mi = s_w[1], cl = s_w[2];
-      const uint32_t np = (ml + mi) >> 1;
-      const uint32_t* A = leaves + lh;
-      const uint32_t* B = nodes + ih;
-      // each thread pairs a contiguous run of the merged order (at least
-      // kMinPairs, so that few warps search when the phase is small)
-      const uint32_t per_t = max(kMinPairs, (np + kHuffThreads - 1) / kHuffThreads);
-      const uint32_t j0 = (uint32_t)tid * per_t;
-      const uint32_t j1 = min(np, j0 + per_t);
-      if (j0 < j1) {
-        uint32_t i = merge_split(A, ml, B, mi, 2u * j0);
-        uint32_t k = 2u * j0 - i;
-        for (uint32_t j = j0; j < j1; j++) {
-          uint32_t e0v, e1v;
-          if (i < ml && (k >= mi || A[i] <= B[k])) e0v = A[i++]; else e0v = B[k++];
-          if (i < ml && (k >= mi || A[i] <= B[k])) e1v = A[i++]; else e1v = B[k++];
-          const uint32_t sum = e0v + e1v;
-          nodes[it + j] = sum;
-          cost += sum;
+    }
+    __syncthreads();
+    bitonic_sort(leaves + nsmall, (int)nbig);
+
+    // 3. phases
+    if (K == 1) {
+      cost = (tid == 0) ? ns : 0ull;
+    } else if (K > 1) {
+      uint32_t lh = 0u, ih = 0u, it = 0u;  // leaf head, node head, node tail
+      for (;;) {
+        if ((K - lh) + (it - ih) <= 1u) break;
+        if (tid < 32) {
+          unsigned long long c4[4] = {~0ull, ~0ull, ~0ull, ~0ull};
+          if (lh < K) c4[0] = leaves[lh];
+          if (lh + 1 < K) c4[1] = leaves[lh + 1];
+          if (ih < it) c4[2] = nodes[ih];
+          if (ih + 1 < it) c4[3] = nodes[ih + 1];
+          const unsigned long long m01 = min(c4[0], c4[1]), x01 = max(c4[0], c4[1]);
+          const unsigned long long m23 = min(c4[2], c4[3]), x23 = max(c4[2], c4[3]);
+          const unsigned long long a0 = min(m01, m23);
+          const unsigned long long a1 = m01 < m23 ? min(x01, m23) : min(x23, m01);
+          uint32_t ml, mi;
+          warp_count_below2(leaves + lh, K - lh, nodes + ih, it - ih, a0 + a1, ml, mi);
+          // leaves among the 2 np paired items: all ml, unless the count is
+          // odd and the last item below T in merged order (ties: leaves
+          // first) is a leaf; that item waits for the next phase
+          uint32_t cl = ml;
+          if ((ml + mi) & 1u) {
+            if (mi == 0u || (ml > 0u && leaves[lh + ml - 1] > nodes[ih + mi - 1])) cl = ml - 1u;
+          }
+          if (tid == 0) {
+            s_w[0] = ml;
+            s_w[1] = mi;
+            s_w[2] = cl;
+          }
         }
+        __syncthreads();
+        const uint32_t ml = s_w[0], mi = s_w[1], cl = s_w[2];
+        const uint32_t np = (ml + mi) >> 1;
+        const uint32_t* A = leaves + lh;
+        const uint32_t* B = nodes + ih;
+        // each thread pairs a contiguous run of the merged order (at least
+        // kMinPairs, so that few warps search when the phase is small)
+        const uint32_t per_t = max(kMinPairs, (np + kHuffThreads - 1) / kHuffThreads);
+        const uint32_t j0 = (uint32_t)tid * per_t;
+        const uint32_t j1 = min(np, j0 + per_t);
+        if (j0 < j1) {
+          uint32_t i = merge_split(A, ml, B, mi, 2u * j0);
+          uint32_t k = 2u * j0 - i;
+          for (uint32_t j = j0; j < j1; j++) {
+            uint32_t e0v, e1v;
+            if (i < ml && (k >= mi || A[i] <= B[k])) e0v = A[i++]; else e0v = B[k++];
+            if (i < ml && (k >= mi || A[i] <= B[k])) e1v = A[i++]; else e1v = B[k++];
+            const uint32_t sum = e0v + e1v;
+            nodes[it + j] = sum;
+            cost += sum;
+          }
+        }
+        __syncthreads();
+        lh += cl;
+        ih += 2u * np - cl;
+        it += np;
       }
-      __syncthreads();
-      lh += cl;
-      ih += 2u * np - cl;
-      it += np;
     }
   }
   cost = block_sum_u64(cost, s_w64);

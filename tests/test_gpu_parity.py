@@ -337,6 +337,47 @@ def test_large_alphabet_huffman(R, ctx):
     assert os_["sz_nsym"] > 0
 
 
+def _residual_field(counts):
+    """A 1D field whose Lorenzo residuals (x[i] - x[i-1], x[-1] = 0) at bin
+    width 1 have the histogram counts[t] for the codes +t and -t (t >= 1) and
+    counts[0] for code 0: pairs (t, 0) of values, shuffled, all exact in
+    float32."""
+    rng = np.random.default_rng(11)
+    ts = np.repeat(np.arange(1, len(counts)), np.asarray(counts[1:], np.int64))
+    rng.shuffle(ts)
+    x = np.zeros(2 * len(ts) + int(counts[0]), np.float32)
+    x[0:2 * len(ts):2] = ts
+    return x
+
+
+@pytest.mark.parametrize("form", ["runs", "runs_large_counts", "global"])
+def test_huffman_forms_for_wide_alphabets(R, ctx, form):
+    """Alphabets past the linear shared-memory form: 60001 codes whose counts
+    take a few distinct values (leaves as runs of equal weight, nodes in a
+    ring), the same with three counts of 2^16 or more, and 65535 codes with
+    4100 distinct counts (too many runs: linear queues in global memory)."""
+    if form == "global":
+        t = np.arange(32768)
+        counts = np.where(t <= 4100, t, 1)
+        counts[0] = 5
+    else:
+        t = np.arange(30001)
+        counts = 1 + t % 5
+        if form == "runs_large_counts":
+            counts[1:4] = [70000, 65536, 131071]
+    x = _residual_field(counts)
+    op = O.params(eb=1e-3, r_sp=1.0)
+    xd = torch.from_numpy(x).cuda()
+    gs = ctx.estimate_sz(xd, _gp(R, op), delta=1.0)
+    os_ = O.estimate_sz(x, op, delta=1.0, want_hist=True)
+    h = os_["hist"]
+    assert int((h > 0).sum()) == 2 * (len(counts) - 1) + 1
+    assert np.array_equal(ctx.histograms()[0], h)
+    for k in ("sz_ns", "sz_huff_bits", "sz_nesc", "sz_nsym", "br_sz_huff"):
+        assert gs[k] == os_[k], k
+    assert _rel(gs["br_sz"], os_["br_sz"]) <= REL_ENTROPY
+
+
 # ---------------------------------------------------------------------------
 # Full-size Hurricane-shaped field (100 x 500 x 500), as the benchmark runs it
 # ---------------------------------------------------------------------------
