@@ -209,9 +209,11 @@ def bench_snapshot(R, ctx, stream, steps: int, peak: float, peak_kind: str, subs
     for _ in range(3):
         call.run(stream)
     ctx.reset_profile()
-    for _ in range(5):
+    nprof = 5
+    for _ in range(nprof):
         call.run(stream)
-    kstats = {k: v[0] / v[1] for k, v in ctx.kernel_stats().items() if v[1] and k.startswith("batch")}
+    # per call (the sampled-blocks pass is one launch per dimensionality)
+    kstats = {k: v[0] / nprof for k, v in ctx.kernel_stats().items() if v[1] and k.startswith("batch")}
     ctx.set_profiling(False)
     # plain: one rd_select per field, arguments marshalled beforehand
     L = R.lib()

@@ -198,22 +198,25 @@ int32_t rd_select_static(const rd_field* field, const rd_params* params,
 /* Work split of the batched estimate.  The results do not depend on it. */
 typedef struct {
   int64_t range_values; /* values per range work item (rounded up to a multiple of 4) */
-  int32_t zfp_blocks;   /* sampled blocks per work item of the block pass */
-  int32_t sz_blocks;    /* sampled blocks per work item of the SZ histogram */
+  int32_t zfp_blocks;   /* sampled blocks of a 3D field per work item of the block
+                           passes (4^(3-d) times as many for d dimensions) */
+  int32_t sz_blocks;    /* the same for the SZ histogram */
   int32_t ctas;         /* cap on each pass's CTAs; 0 = every CTA the SMs hold at once */
   int32_t tuned;        /* output: 1 when the autotuner chose this split */
 } rd_batch_config;
 
 /* Algorithm 1 lines 2-12 for n fields at once, e.g. every field of a
  * simulation snapshot, of uneven 2D/3D sizes (the paper's algorithm loops
- * over the fields of a snapshot).  Six launches cover all fields: a reset;
- * three persistent passes over work items of every field (runs of a field's
- * values for the range; runs of its sampled blocks, read once for both
- * estimators, for the ZFP estimate and the SZ residuals; the stored
- * residuals for the SZ histogram; the CTA that ends a field's last range
- * item derives VR and eb_abs, the one that ends its last block item derives
- * delta); the count-of-counts; one CTA per field for the Huffman cost,
- * entropy, rates, PSNRs and selection.
+ * over the fields of a snapshot).  Six launches plus one per dimensionality
+ * present cover all fields: a reset; persistent passes over work items of
+ * every field (runs of a field's values for the range; runs of its sampled
+ * blocks, read once for both estimators, whose SZ residuals and ZFP
+ * coefficients are stored, one launch per dimensionality; the stored
+ * coefficients for the ZFP estimate; the stored residuals for the SZ
+ * histogram; the CTA that ends a field's last range item derives VR and
+ * eb_abs, the one that ends its last ZFP item derives delta); the
+ * count-of-counts; one CTA per field for the Huffman cost, entropy, rates,
+ * PSNRs and selection.
  *  - fields[i]: DEVICE memory only (RD_ERR_INVALID_ARG otherwise);
  *    params[i]: the parameters of field i.  n >= 1.
  *  - results[n] is required; truths[n] may be NULL, else each field's ground
@@ -223,8 +226,11 @@ typedef struct {
  *    failing field (whose records are zeroed; the others stay valid), or a
  *    call-level error (RD_ERR_INVALID_ARG, _OOM, _BUDGET, _CUDA) with every
  *    record zeroed.
- *  - The context holds one workspace per field (about 2.6 MB each) and caches
- *    a plan per distinct set of fields and parameters: the plan's first call
+ *  - The context holds one workspace per field (about 2.7 MB each) and caches
+ *    a plan per distinct set of fields and parameters, with the stored SZ
+ *    residuals, ZFP coefficients and exponents of its sampled blocks (4^d +
+ *    EC positions + 1 words per sampled block: 6-8% of the fields' bytes at
+ *    r_sp = 0.05, counted against the HBM budget): the plan's first call
  *    runs the autotuner (three work-item sizes, the passes timed, the fastest
  *    kept) unless rd_batch_set_config forced a split; its second call
  *    captures a CUDA graph that later calls replay.

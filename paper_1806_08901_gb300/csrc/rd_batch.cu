@@ -5,16 +5,20 @@
 //     eb_abs and the precision exponent (Algorithm 1 line 2);
 //   sampled blocks: runs of a field's sampled blocks, one thread per block:
 //     the block and its one-cell low halo are read once; the SZ residuals
-//     of its points (which do not depend on the bin width) are stored, and
-//     the ZFP estimator terms accumulated (lines 3-6); the CTA that ends a
-//     field's last item derives delta (line 7);
+//     of its points (which do not depend on the bin width) and the ZFP
+//     block exponent and transformed coefficients (which do not depend on
+//     the error bound) are stored;
+//   ZFP estimate: the stored coefficients, truncated at the precision the
+//     error bound sets, give the estimator terms (lines 3-6); the CTA that
+//     ends a field's last item derives delta (line 7);
 //   SZ histogram: the stored residuals, quantised at delta, coalesced
 //     (line 8).
 // The sampled blocks are scattered: each block row costs a whole DRAM
 // fetch, so one pass that serves both estimators reads about a third of the
 // field where two passes read about six tenths.
 // CTAs stride over the items of their pass; the passes are stream-ordered
-// launches, so no CTA waits on another.
+// launches, so no CTA waits on another.  The sampled-blocks pass depends on
+// nothing the range pass derives.
 #include <math.h>
 #include <stdint.h>
 
@@ -28,7 +32,8 @@ namespace rdk {
 
 constexpr int kBatchRangeThreads = 512;
 constexpr int kBatchBlockThreads = 128;
-constexpr int kBatchSzThreads = 256;
+constexpr int kBatchZfpThreads = 256;
+constexpr int kBatchSzThreads = 1024;
 
 // ---------------------------------------------------------------------------
 // Range
@@ -105,25 +110,70 @@ __device__ __forceinline__ void load_cube(const FieldDev& f, const int* o, float
   }
 }
 
+// Order-preserving 32-bit key of a residual; NaN (a point past the extent)
+// gets all ones, after every valid key.
+__device__ __forceinline__ uint32_t res_key(float r) {
+  const uint32_t b = __float_as_uint(r);
+  return isnan(r) ? 0xffffffffu : (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float key_res(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// Ascending bitonic sorting network over N keys held in registers (every
+// index is a compile-time constant once unrolled).
+template <int N>
+__device__ __forceinline__ void sort_keys(uint32_t* a) {
+#pragma unroll
+  for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+      for (int i = 0; i < N; i++) {
+        const int l = i ^ j;
+        if (l > i) {
+          const uint32_t x = a[i], y = a[l];
+          const bool up = (i & k) == 0;
+          a[i] = up ? min(x, y) : max(x, y);
+          a[l] = up ? max(x, y) : min(x, y);
+        }
+      }
+    }
+  }
+}
+
 // One thread per sampled block: the SZ residuals of the block's points (the
 // float32 nested differences of est_residual; NaN past the extent) are
-// stored for the histogram pass, and the ZFP estimator terms of the block
-// (Alg. 1 lines 4-6) are accumulated.
+// stored for the histogram pass as ascending keys (the histogram does not
+// depend on the order of a block's points, and sorted codes let a warp
+// count runs of equal codes with one atomic each), and the block's ZFP
+// exponent and
+// negabinary coefficients in sequency order (the EC positions, or all of
+// them) for the ZFP estimate pass.  The block-floating-point cast and the
+// decorrelating transform use only the block exponent, so nothing here
+// depends on the error bound.
 template <int D>
-__device__ __forceinline__ void sampled_blocks_item(const BatchField& F, long long b0, long long b1,
-                                                    int minexp, unsigned long long& my_s2,
-                                                    unsigned long long* s_lo,
-                                                    unsigned long long* s_hi) {
+__device__ __forceinline__ void sampled_blocks_item(const BatchField& F, long long b0, long long b1) {
   constexpr int NB = 1 << (2 * D);
   constexpr int NC = D == 3 ? 125 : D == 2 ? 25 : 5;
+  constexpr EcPositions<D> EC{};
   const FieldDev& f = F.f;
   const bool ec_all = F.p.ec_mode == RD_EC_ALL;
+  const long long ns = f.nsampled;
   for (long long sb = b0 + threadIdx.x; sb < b1; sb += blockDim.x) {
     int o[3] = {0, 0, 0};
     sampled_block_origin<D>(f, sb, o);
     float cube[NC];
     load_cube<D>(f, o, cube);
-    // SZ residuals
+    // ZFP: the block's values (with far-edge replication) are the cube's
+    // entries with every index >= 1
+    float v[NB];
+#pragma unroll
+    for (int t = 0; t < NB; t++) {
+      const int k = t & 3, j = D >= 2 ? (t >> 2) & 3 : 0, i = D == 3 ? t >> 4 : 0;
+      v[t] = cube[((D == 3 ? i + 1 : 0) * 5 + (D >= 2 ? j + 1 : 0)) * 5 + k + 1];
+    }
+    // SZ residuals (the cube is dead after these)
     float r[NB];
 #pragma unroll
     for (int t = 0; t < NB; t++) {
@@ -140,128 +190,278 @@ __device__ __forceinline__ void sampled_blocks_item(const BatchField& F, long lo
       if (D == 3) ok = ok && o[0] + i < f.n[0];
       r[t] = ok ? est_residual<D>(nb) : __int_as_float(0x7fc00000);
     }
-    float* dst = F.res + sb * NB;
-    if (D == 1) {
+    uint32_t key[NB];
 #pragma unroll
-      for (int t = 0; t < NB; t++) dst[t] = r[t];
-    } else {
+    for (int t = 0; t < NB; t++) key[t] = res_key(r[t]);
+    {
+      BlockWork<D> w;
+      w.forward(v, 0);  // the precision (and so minexp) is not used here
+      F.ze[sb] = w.bi.emax;
+      if (ec_all) {
 #pragma unroll
-      for (int t = 0; t < NB; t += 4)
-        *reinterpret_cast<float4*>(dst + t) = make_float4(r[t], r[t + 1], r[t + 2], r[t + 3]);
+        for (int q = 0; q < NB; q++) F.zc[q * ns + sb] = w.u[q];
+      } else {
+#pragma unroll
+        for (int j = 0; j < EcPositions<D>::M; j++) F.zc[j * ns + sb] = w.u[EC.pos[j]];
+      }
     }
-    // ZFP: the block's values (with far-edge replication) are the cube's
-    // entries with every index >= 1
-    float v[NB];
+    sort_keys<NB>(key);
+    uint4* dst = reinterpret_cast<uint4*>(F.res + sb * NB);
 #pragma unroll
-    for (int t = 0; t < NB; t++) {
-      const int k = t & 3, j = D >= 2 ? (t >> 2) & 3 : 0, i = D == 3 ? t >> 4 : 0;
-      v[t] = cube[((D == 3 ? i + 1 : 0) * 5 + (D >= 2 ? j + 1 : 0)) * 5 + k + 1];
-    }
-    BlockWork<D> w;
-    w.forward(v, minexp);
-    zfp_est_accumulate<D>(w, ec_all, my_s2, s_lo, s_hi);
+    for (int t = 0; t < NB; t += 4) dst[t / 4] = make_uint4(key[t], key[t + 1], key[t + 2], key[t + 3]);
   }
 }
 
+// ZFP estimator terms of the sampled blocks [b0, b1) of one field from the
+// stored coefficients: the precision of a block follows from its exponent
+// and the field's minexp (block_info's rule), then zfp_est_terms.
+template <int D>
+__device__ __forceinline__ void zfp_stored_item(const BatchField& F, long long b0, long long b1,
+                                                int minexp, unsigned long long& my_s2,
+                                                unsigned long long* s_lo, unsigned long long* s_hi) {
+  const bool ec_all = F.p.ec_mode == RD_EC_ALL;
+  const long long ns = F.f.nsampled;
+  for (long long base = b0; base < b1; base += blockDim.x) {  // warp-uniform trips
+    const long long sb = base + threadIdx.x;
+    bool has = false;
+    int emax = -127;
+    unsigned long long lo = 0ull, hi = 0ull;
+    if (sb < b1) {
+      // every load of the block issued before any use
+      constexpr int NB = 1 << (2 * D), M = EcPositions<D>::M;
+      const uint32_t* zc = F.zc + sb;
+      emax = __ldcs(F.ze + sb);
+      const bool all_zero = emax == -127;
+      const int prec = all_zero ? 0 : min(32, max(0, emax - minexp + 2 * (D + 1)));
+      const int kmin = 32 - prec;
+      long long s2 = 0;
+      if (ec_all) {
+        // every coefficient, independent terms: in chunks of M
+#pragma unroll 1
+        for (int q0 = 0; q0 < NB; q0 += M) {
+          uint32_t u[M];
+#pragma unroll
+          for (int j = 0; j < M; j++) u[j] = q0 + j < NB ? __ldcs(zc + (q0 + j) * ns) : 0u;
+#pragma unroll
+          for (int j = 0; j < M; j++) {
+            if (q0 + j < NB) {
+              s2 += 2 * zfp_nsb(u[j], kmin);
+              zfp_add_err(u[j], kmin, lo, hi);
+            }
+          }
+        }
+      } else {
+        uint32_t u[M];
+#pragma unroll
+        for (int j = 0; j < M; j++) u[j] = __ldcs(zc + j * ns);
+        zfp_est_terms<D>(kmin, false, [&](int j) { return u[j]; }, s2, lo, hi);
+      }
+      my_s2 += (unsigned long long)s2;
+      has = !all_zero && (lo | hi);
+    }
+    mse_add_warp(has, mse_bin<D>(emax), lo, hi, s_lo, s_hi);
+  }
+}
+
+// One launch per dimensionality (the items of d-dimensional fields): the
+// registers of the 3D form would otherwise set the occupancy of all.
+template <int D>
 __global__ void __launch_bounds__(kBatchBlockThreads) k_batch_blocks(const BatchField* __restrict__ bf,
                                                                      const BatchItem* __restrict__ items,
                                                                      int nitems) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const BatchItem item = items[it];
+    sampled_blocks_item<D>(bf[item.field], item.begin, item.end);
+  }
+}
+
+// The items [i0, i1) a CTA takes: contiguous, so that consecutive items of
+// one field share the CTA's accumulators and their flush.
+__device__ __forceinline__ void cta_items(int nitems, int& i0, int& i1) {
+  const int per = (nitems + (int)gridDim.x - 1) / (int)gridDim.x;
+  i0 = min(nitems, (int)blockIdx.x * per);
+  i1 = min(nitems, i0 + per);
+}
+
+// Adds the CTA's ZFP terms of field F (cnt items) to its workspace; the CTA
+// that brings the field's item count to items_zfp derives delta.
+__device__ __forceinline__ void zfp_commit(const BatchField& F, uint32_t cnt,
+                                           unsigned long long my_s2, unsigned long long* s_lo,
+                                           unsigned long long* s_hi, unsigned long long* s_s2,
+                                           int* s_last) {
+  Workspace* ws = F.ws;
+  my_s2 = warp_sum(my_s2);
+  if ((threadIdx.x & 31) == 0 && my_s2) atomicAdd(s_s2, my_s2);
+  __syncthreads();
+  if (threadIdx.x == 0 && *s_s2) atomicAdd(&ws->sc.s2, *s_s2);
+  for (int i = threadIdx.x; i < kMseBins; i += blockDim.x)
+    if (s_lo[i] | s_hi[i]) atomic_add_u128(&ws->sc.mse_lo[i], &ws->sc.mse_hi[i], s_lo[i], s_hi[i]);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    *s_last = atomicAdd(&ws->sc.done[1], cnt) + cnt == F.items_zfp;
+  }
+  __syncthreads();
+  if (*s_last && threadIdx.x < 32) {
+    __threadfence();
+    delta_warp(F.p, ws, DELTA_FROM_MSE, 0.0, 1, F.need_gt, F.ncoeff, F.npoints);
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBatchZfpThreads) k_batch_zfp(const BatchField* __restrict__ bf,
+                                                                const BatchItem* __restrict__ items,
+                                                                int nitems) {
   __shared__ unsigned long long s_lo[kMseBins], s_hi[kMseBins];
   __shared__ unsigned long long s_s2;
   __shared__ int s_last;
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+  int i0, i1;
+  cta_items(nitems, i0, i1);
+  int cur = -1;  // the field the accumulators hold
+  uint32_t cnt = 0u;
+  unsigned long long my_s2 = 0ull;
+  for (int it = i0; it < i1; it++) {
     const BatchItem item = items[it];
+    if (item.field != cur) {  // uniform over the CTA
+      if (cur >= 0) zfp_commit(bf[cur], cnt, my_s2, s_lo, s_hi, &s_s2, &s_last);
+      for (int i = threadIdx.x; i < kMseBins; i += blockDim.x) {
+        s_lo[i] = 0ull;
+        s_hi[i] = 0ull;
+      }
+      if (threadIdx.x == 0) s_s2 = 0ull;
+      __syncthreads();
+      cur = item.field;
+      cnt = 0u;
+      my_s2 = 0ull;
+    }
     const BatchField& F = bf[item.field];
     Workspace* ws = F.ws;
-    const bool live = ws->sc.status == RD_OK && !ws->sc.constant;
-    for (int i = threadIdx.x; i < kMseBins; i += blockDim.x) {
-      s_lo[i] = 0ull;
-      s_hi[i] = 0ull;
+    cnt++;
+    if (ws->sc.status != RD_OK || ws->sc.constant) continue;
+    const int minexp = ws->sc.minexp;
+    switch (F.f.d) {
+      case 1: zfp_stored_item<1>(F, item.begin, item.end, minexp, my_s2, s_lo, s_hi); break;
+      case 2: zfp_stored_item<2>(F, item.begin, item.end, minexp, my_s2, s_lo, s_hi); break;
+      default: zfp_stored_item<3>(F, item.begin, item.end, minexp, my_s2, s_lo, s_hi); break;
     }
-    if (threadIdx.x == 0) s_s2 = 0ull;
-    __syncthreads();
-    if (live) {
-      unsigned long long my_s2 = 0ull;
-      const int minexp = ws->sc.minexp;
-      switch (F.f.d) {
-        case 1: sampled_blocks_item<1>(F, item.begin, item.end, minexp, my_s2, s_lo, s_hi); break;
-        case 2: sampled_blocks_item<2>(F, item.begin, item.end, minexp, my_s2, s_lo, s_hi); break;
-        default: sampled_blocks_item<3>(F, item.begin, item.end, minexp, my_s2, s_lo, s_hi); break;
-      }
-      my_s2 = warp_sum(my_s2);
-      if ((threadIdx.x & 31) == 0 && my_s2) atomicAdd(&s_s2, my_s2);
-    }
-    __syncthreads();
-    if (live) {
-      if (threadIdx.x == 0 && s_s2) atomicAdd(&ws->sc.s2, s_s2);
-      for (int i = threadIdx.x; i < kMseBins; i += blockDim.x)
-        if (s_lo[i] | s_hi[i]) atomic_add_u128(&ws->sc.mse_lo[i], &ws->sc.mse_hi[i], s_lo[i], s_hi[i]);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      s_last = atomicAdd(&ws->sc.done[1], 1u) == F.items_zfp - 1u;
-    }
-    __syncthreads();
-    if (s_last && threadIdx.x < 32) {
-      __threadfence();
-      delta_warp(F.p, ws, DELTA_FROM_MSE, 0.0, 1, F.need_gt, F.ncoeff, F.npoints);
-    }
-    __syncthreads();
   }
+  if (cur >= 0) zfp_commit(bf[cur], cnt, my_s2, s_lo, s_hi, &s_s2, &s_last);
 }
 
 // ---------------------------------------------------------------------------
 // SZ histogram of the stored residuals (Alg. 1 line 8), coalesced
 // ---------------------------------------------------------------------------
-// the shared window of the residual histogram: +-8192 codes around zero
-// (the residuals of rough fields at fine bounds spread over thousands of
-// codes; outside the window a code takes a global atomic)
-constexpr int kWideWin = 16384;
-constexpr int kWideWinLo = kCenter - kWideWin / 2;
+// The whole alphabet in shared memory: 65536 16-bit counters, code s in
+// half s >> 15 of word s & 0x7fff (so neighbouring codes, which the runs of
+// a warp often hit together, fall in different words).  The residuals of
+// rough fields at fine bounds spread over tens of thousands of codes: a
+// partial window sent most of them to global atomics, which set the pace.
+// A counter cannot pass 65535 between flushes: the window is flushed before
+// it has counted kFlushPoints points.
+constexpr int kPackWords = 32768;
+constexpr long long kFlushPoints = 65535;
+constexpr long long kRoundPoints = 21844;  // points between flush checks (3 rounds fit; a multiple of 4)
+
+// Counts 64 consecutive keys of the residual list, two per lane (lane i
+// holds positions 2i and 2i+1): within a block they ascend, so their codes
+// form runs of equal values; the first position of every run adds the run's
+// length with one atomic on its 16-bit counter.  All-ones keys (points past
+// the extent, or past the list) count nothing.  Every lane of the warp
+// calls.
+__device__ __forceinline__ void hist_add_runs(uint32_t* s_win, uint32_t ka, uint32_t kb, float inv,
+                                              int R) {
+  const int lane = threadIdx.x & 31;
+  const int sa = ka != 0xffffffffu ? est_symbol(key_res(ka), inv, R) : -1;
+  const int sb = kb != 0xffffffffu ? est_symbol(key_res(kb), inv, R) : -1;
+  const int prev = __shfl_up_sync(0xffffffffu, sb, 1);  // the code before position 2i
+  const bool ha = lane == 0 || sa != prev;
+  const bool hb = sb != sa;
+  const unsigned ba = __ballot_sync(0xffffffffu, ha);
+  const unsigned bb = __ballot_sync(0xffffffffu, hb);
+  // the first run start after position 2i+1
+  const unsigned later = (ba | bb) & ~((2u << lane) - 1u);
+  int next = 64;
+  if (later) {
+    const int j = __ffs(later) - 1;
+    next = 2 * j + (((ba >> j) & 1u) ? 0 : 1);
+  }
+  auto add = [&](int sym, unsigned cnt) { atomicAdd(&s_win[sym & 0x7fff], cnt << ((sym >> 15) << 4)); };
+  if (ha && sa >= 0) add(sa, hb ? 1u : (unsigned)(next - 2 * lane));
+  if (hb && sb >= 0) add(sb, (unsigned)(next - 2 * lane - 1));
+}
+
+__device__ __forceinline__ void window_flush(uint32_t* s_win, uint32_t* g_hist) {
+  __syncthreads();
+  uint4* w4 = reinterpret_cast<uint4*>(s_win);
+  for (int i = threadIdx.x; i < kPackWords / 4; i += blockDim.x) {
+    const uint4 c = w4[i];
+    if (c.x | c.y | c.z | c.w) {
+      const uint32_t cw[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        if (cw[k] & 0xffffu) atomicAdd(&g_hist[4 * i + k], cw[k] & 0xffffu);
+        if (cw[k] >> 16) atomicAdd(&g_hist[4 * i + k + 32768], cw[k] >> 16);
+      }
+      w4[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+  }
+  __syncthreads();
+}
 
 __global__ void __launch_bounds__(kBatchSzThreads) k_batch_sz_hist(const BatchField* __restrict__ bf,
                                                                    const BatchItem* __restrict__ items,
                                                                    int nitems) {
-  extern __shared__ uint32_t s_win[];  // kWideWin counters
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+  extern __shared__ uint32_t s_win[];  // kPackWords words of two counters
+  int i0, i1;
+  cta_items(nitems, i0, i1);
+  for (int i = threadIdx.x; i < kPackWords; i += blockDim.x) s_win[i] = 0u;
+  __syncthreads();
+  int cur = -1;        // the field the window holds
+  long long held = 0;  // points counted since the last flush
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int W = kBatchSzThreads / 32;
+  constexpr int U = 4;  // independent 8-byte loads in flight per lane
+  for (int it = i0; it < i1; it++) {
     const BatchItem item = items[it];
     const BatchField& F = bf[item.field];
     Workspace* ws = F.ws;
-    if (ws->sc.status != RD_OK || ws->sc.constant) continue;  // uniform over the CTA
-    for (int i = threadIdx.x; i < kWideWin; i += blockDim.x) s_win[i] = 0u;
-    __syncthreads();
+    if (item.field != cur) {  // uniform over the CTA
+      if (cur >= 0) window_flush(s_win, bf[cur].ws->hist[0]);
+      cur = item.field;
+      held = 0;
+    }
+    if (ws->sc.status != RD_OK || ws->sc.constant) continue;
     const float inv = ws->sc.inv;
     const int R = F.p.R;
-    const long long nb = 1ll << (2 * F.f.d);  // a multiple of 4: float4 granules
-    const float4* r4 = reinterpret_cast<const float4*>(F.res + item.begin * nb);
-    const int n4 = (int)((item.end - item.begin) * nb / 4);
-    constexpr int U = 4;  // independent 16-byte loads in flight per thread
-    const float nan = __int_as_float(0x7fc00000);
-    for (int i0 = threadIdx.x; i0 - (int)threadIdx.x < n4; i0 += U * kBatchSzThreads) {
-      float4 q[U];
-#pragma unroll
-      for (int k = 0; k < U; k++) {
-        const int i = i0 + k * kBatchSzThreads;
-        q[k] = i < n4 ? __ldcs(r4 + i) : make_float4(nan, nan, nan, nan);
+    const long long nb = 1ll << (2 * F.f.d);
+    // the item's keys as pairs, in rounds of kRoundPoints keys; a warp
+    // takes 64 consecutive keys (2 per lane) at a time
+    const uint2* k2 = reinterpret_cast<const uint2*>(F.res + item.begin * nb);
+    const long long npts = (item.end - item.begin) * nb;
+    for (long long r0 = 0; r0 < npts; r0 += kRoundPoints) {
+      const long long rn = npts - r0 < kRoundPoints ? npts - r0 : kRoundPoints;
+      if (held + rn > kFlushPoints) {  // uniform over the CTA
+        window_flush(s_win, ws->hist[0]);
+        held = 0;
       }
+      held += rn;
+      const uint2* q2 = k2 + r0 / 2;
+      const int n2 = (int)(rn / 2);
+      const int nchunks = (n2 + 31) >> 5;
+      for (int c0 = warp; c0 < nchunks; c0 += U * W) {  // warp-uniform
+        uint2 q[U];
 #pragma unroll
-      for (int k = 0; k < U; k++) {
-        const float rv[4] = {q[k].x, q[k].y, q[k].z, q[k].w};
-#pragma unroll
-        for (int c = 0; c < 4; c++) {
-          const bool ok = !isnan(rv[c]);
-          hist_add_sorted(s_win, kWideWinLo, kWideWin, ws->hist[0], ok ? est_symbol(rv[c], inv, R) : 0, ok);
+        for (int k = 0; k < U; k++) {
+          const int c = c0 + k * W;
+          const int g = 32 * c + lane;
+          q[k] = (c < nchunks && g < n2) ? __ldcs(q2 + g) : make_uint2(0xffffffffu, 0xffffffffu);
         }
+#pragma unroll
+        for (int k = 0; k < U; k++) hist_add_runs(s_win, q[k].x, q[k].y, inv, R);
       }
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kWideWin; i += blockDim.x) {
-      const uint32_t c = s_win[i];
-      if (c) atomicAdd(&ws->hist[0][kWideWinLo + i], c);
-    }
-    __syncthreads();
   }
+  if (cur >= 0) window_flush(s_win, bf[cur].ws->hist[0]);
 }
 
 // ---------------------------------------------------------------------------
@@ -278,15 +478,27 @@ cudaError_t launch_batch_range(const BatchField* bf, const BatchItem* items, int
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_blocks(const BatchField* bf, const BatchItem* items, int nitems, int ctas,
-                                cudaStream_t s) {
-  k_batch_blocks<<<grid_for(nitems, ctas), kBatchBlockThreads, 0, s>>>(bf, items, nitems);
+cudaError_t launch_batch_blocks(const BatchField* bf, const BatchItem* items, int nitems, int d,
+                                int ctas, cudaStream_t s) {
+  const int g = grid_for(nitems, ctas);
+  if (d == 1)
+    k_batch_blocks<1><<<g, kBatchBlockThreads, 0, s>>>(bf, items, nitems);
+  else if (d == 2)
+    k_batch_blocks<2><<<g, kBatchBlockThreads, 0, s>>>(bf, items, nitems);
+  else
+    k_batch_blocks<3><<<g, kBatchBlockThreads, 0, s>>>(bf, items, nitems);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_zfp(const BatchField* bf, const BatchItem* items, int nitems, int ctas,
+                             cudaStream_t s) {
+  k_batch_zfp<<<grid_for(nitems, ctas), kBatchZfpThreads, 0, s>>>(bf, items, nitems);
   return cudaGetLastError();
 }
 
 cudaError_t launch_batch_sz_hist(const BatchField* bf, const BatchItem* items, int nitems, int ctas,
                                  cudaStream_t s) {
-  k_batch_sz_hist<<<grid_for(nitems, ctas), kBatchSzThreads, kWideWin * sizeof(uint32_t), s>>>(
+  k_batch_sz_hist<<<grid_for(nitems, ctas), kBatchSzThreads, kPackWords * sizeof(uint32_t), s>>>(
       bf, items, nitems);
   return cudaGetLastError();
 }
@@ -298,14 +510,17 @@ static int occupancy(const void* fn, int threads, int num_sms) {
   return per * num_sms;
 }
 
-void batch_occupancy(int num_sms, int* range_ctas, int* zfp_ctas, int* sz_ctas) {
+void batch_occupancy(int num_sms, int* range_ctas, int* blocks_ctas, int* zfp_ctas, int* sz_ctas) {
   *range_ctas = occupancy((const void*)k_batch_range, kBatchRangeThreads, num_sms);
-  *zfp_ctas = occupancy((const void*)k_batch_blocks, kBatchBlockThreads, num_sms);
+  blocks_ctas[0] = occupancy((const void*)k_batch_blocks<1>, kBatchBlockThreads, num_sms);
+  blocks_ctas[1] = occupancy((const void*)k_batch_blocks<2>, kBatchBlockThreads, num_sms);
+  blocks_ctas[2] = occupancy((const void*)k_batch_blocks<3>, kBatchBlockThreads, num_sms);
+  *zfp_ctas = occupancy((const void*)k_batch_zfp, kBatchZfpThreads, num_sms);
   cudaFuncSetAttribute(k_batch_sz_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       kWideWin * (int)sizeof(uint32_t));
+                       kPackWords * (int)sizeof(uint32_t));
   int per = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void*)k_batch_sz_hist, kBatchSzThreads,
-                                                    kWideWin * sizeof(uint32_t)) != cudaSuccess ||
+                                                    kPackWords * sizeof(uint32_t)) != cudaSuccess ||
       per < 1)
     per = 1;
   *sz_ctas = per * num_sms;

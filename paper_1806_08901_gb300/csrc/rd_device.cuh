@@ -223,37 +223,52 @@ __device__ __forceinline__ void hist_add(uint32_t* s_win, uint32_t* g_hist, int 
 }
 
 // Warp-aggregated histogram insert without warp matching (whose unit runs it
-// at a low rate on this GPU): the warp sorts its 32 symbols with a bitonic
-// network of shuffles, and the first lane of every run of equal symbols adds
-// the run's length with one atomic (shared window [win_lo, win_lo + win),
-// else the global histogram).  Every lane of the warp calls; lanes with
-// ok == false contribute nothing.
-__device__ __forceinline__ void hist_add_sorted(uint32_t* s_win, int win_lo, int win,
-                                                uint32_t* g_hist, int sym, bool ok) {
+// at a low rate on this GPU), two symbols per lane: each lane packs two
+// 16-bit symbols into one word, and the warp sorts both 32-symbol sequences
+// at once with a bitonic network of shuffles and paired 16-bit min/max (the
+// network does not depend on the data, so both halves come out sorted).
+// The first lane of every run of equal symbols in a half adds the run's
+// length with one atomic (shared window [win_lo, win_lo + win), else the
+// global histogram): sorted runs land on consecutive words, so the atomics
+// of a warp rarely meet in a bank.  Lanes whose symbol is not valid carry
+// 0xffff, which sorts last, and are taken off that symbol's run.  Every lane
+// of the warp calls.
+__device__ __forceinline__ void hist_add_sorted2(uint32_t* s_win, int win_lo, int win,
+                                                 uint32_t* g_hist, uint32_t keys, bool ok_lo,
+                                                 bool ok_hi) {
   const int lane = threadIdx.x & 31;
-  int key = ok ? sym : 0x7fffffff;
+  const unsigned bad_lo = __popc(__ballot_sync(0xffffffffu, !ok_lo));
+  const unsigned bad_hi = __popc(__ballot_sync(0xffffffffu, !ok_hi));
+  uint32_t key = keys;
 #pragma unroll
   for (int k = 2; k <= 32; k <<= 1) {
 #pragma unroll
     for (int j = k >> 1; j > 0; j >>= 1) {
-      const int other = __shfl_xor_sync(0xffffffffu, key, j);
+      const uint32_t other = __shfl_xor_sync(0xffffffffu, key, j);
       const bool up = (lane & k) == 0;
       const bool low = (lane & j) == 0;
-      key = (low == up) ? min(key, other) : max(key, other);
+      key = (low == up) ? __vminu2(key, other) : __vmaxu2(key, other);
     }
   }
-  const int prev = __shfl_up_sync(0xffffffffu, key, 1);
-  const bool head = lane == 0 || key != prev;
-  const unsigned heads = __ballot_sync(0xffffffffu, head);
-  if (head && key != 0x7fffffff) {
-    const unsigned later = heads & ~((2u << lane) - 1u);  // heads after this lane
-    const int next = later ? __ffs(later) - 1 : 32;
-    const unsigned cnt = (unsigned)(next - lane);
-    const int wi = key - win_lo;
-    if ((unsigned)wi < (unsigned)win)
-      atomicAdd(&s_win[wi], cnt);
-    else
-      atomicAdd(&g_hist[key], cnt);
+  const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    const uint32_t kh = (key >> (16 * h)) & 0xffffu, ph = (prev >> (16 * h)) & 0xffffu;
+    const bool head = lane == 0 || kh != ph;
+    const unsigned heads = __ballot_sync(0xffffffffu, head);
+    if (head) {
+      const unsigned later = heads & ~((2u << lane) - 1u);  // heads after this lane
+      const int next = later ? __ffs(later) - 1 : 32;
+      unsigned cnt = (unsigned)(next - lane);
+      if (kh == 0xffffu) cnt -= h ? bad_hi : bad_lo;
+      if (cnt) {
+        const int wi = (int)kh - win_lo;
+        if ((unsigned)wi < (unsigned)win)
+          atomicAdd(&s_win[wi], cnt);
+        else
+          atomicAdd(&g_hist[kh], cnt);
+      }
+    }
   }
 }
 

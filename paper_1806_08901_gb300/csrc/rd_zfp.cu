@@ -39,8 +39,15 @@ __global__ void __launch_bounds__(kZfpThreads) k_zfp(FieldDev f, ParamsDev p, Wo
   float my_max = 0.0f;
   const bool ec_all = p.ec_mode == RD_EC_ALL;
 
-  for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < units;
-       u += (long long)gridDim.x * blockDim.x) {
+  constexpr EcPositions<D> EC{};
+  // warp-uniform trip count: the estimator's bin sums are added per warp
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < units;
+       base += (long long)gridDim.x * blockDim.x) {
+    const long long u = base + threadIdx.x;
+    bool est_has = false;
+    int est_bin = 0;
+    unsigned long long est_lo = 0ull, est_hi = 0ull;
+    if (u < units) {
     int b[3] = {0, 0, 0};
     decode_block<D>(f, u, !GT, b);
     bool sampled = true;
@@ -53,7 +60,14 @@ __global__ void __launch_bounds__(kZfpThreads) k_zfp(FieldDev f, ParamsDev p, Wo
     BlockWork<D> w;
     w.forward(v, minexp);
 
-    if (EST && sampled) zfp_est_accumulate<D>(w, ec_all, my_s2, s_lo, s_hi);
+    if (EST && sampled) {
+      long long s2;
+      zfp_est_terms<D>(w.bi.kmin, ec_all, [&](int j) { return ec_all ? w.u[j] : w.u[EC.pos[j]]; },
+                       s2, est_lo, est_hi);
+      my_s2 += (unsigned long long)s2;
+      est_has = !w.bi.all_zero && (est_lo | est_hi);
+      est_bin = mse_bin<D>(w.bi.emax);
+    }
 
     if (GT) {
       my_bits += w.bits();
@@ -108,6 +122,8 @@ __global__ void __launch_bounds__(kZfpThreads) k_zfp(FieldDev f, ParamsDev p, Wo
         my_sse += (double)e2[0] * __longlong_as_double((long long)(1023 - 2 * k) << 52);
       }
     }
+    }
+    if (EST) mse_add_warp(est_has, est_bin, est_lo, est_hi, s_lo, s_hi);
   }
 
   // reductions: warp, then CTA, then one global update per CTA

@@ -191,31 +191,39 @@ __device__ __forceinline__ void decode_block(const FieldDev& f, long long u, boo
 }
 
 // Estimator terms of one sampled block (Alg. 1 lines 4-6): the doubled
-// interpolated n_sb sum into s2, and the exact squared truncation errors at
-// the EC-sampled coefficients into the 128-bit bin of the block exponent.
-// uj(j) is the j-th sampled coefficient (negabinary): coefficient j of the
-// sequency order when every coefficient is sampled, else the one at EC
-// position j.
+// interpolated n_sb sum (s2), and the exact sum of the squared truncation
+// errors at the EC-sampled coefficients as a 128-bit (lo, hi) pair, which
+// belongs to the bin of the block exponent (mse_bin).  uj(j) is the j-th
+// sampled coefficient (negabinary): coefficient j of the sequency order
+// when every coefficient is sampled, else the one at EC position j.
+// Significant bits of coefficient u in the planes kmin..31.
+__device__ __forceinline__ int zfp_nsb(unsigned u, int kmin) {
+  const int bb = 31 - __clz((int)u);
+  return bb >= kmin ? bb - kmin + 1 : 0;
+}
+
+// Squared truncation error of coefficient u (planes below kmin dropped)
+// added to the 128-bit (lo, hi) pair.
+__device__ __forceinline__ void zfp_add_err(unsigned u, int kmin, unsigned long long& lo,
+                                            unsigned long long& hi) {
+  const unsigned keep = kmin >= 32 ? 0u : (0xffffffffu << kmin);
+  long long d = (long long)from_negabinary(u) - (long long)from_negabinary(u & keep);
+  unsigned long long ad = (unsigned long long)(d < 0 ? -d : d);
+  unsigned long long sq = ad * ad;  // |d| < 2^32
+  lo += sq;
+  hi += (lo < sq);
+}
+
 template <int D, class UJ>
-__device__ __forceinline__ void zfp_est_core(bool all_zero, int emax, int kmin, bool ec_all, UJ uj,
-                                             unsigned long long& my_s2, unsigned long long* s_lo,
-                                             unsigned long long* s_hi) {
+__device__ __forceinline__ void zfp_est_terms(int kmin, bool ec_all, UJ uj, long long& s2,
+                                              unsigned long long& lo, unsigned long long& hi) {
   constexpr int NB = 1 << (2 * D);
   constexpr EcPositions<D> EC{};
-  auto nsb = [&](unsigned u) {
-    int bb = 31 - __clz((int)u);
-    return bb >= kmin ? bb - kmin + 1 : 0;
-  };
-  const unsigned keep = kmin >= 32 ? 0u : (0xffffffffu << kmin);
-  long long s2 = 0;
-  unsigned long long lo = 0ull, hi = 0ull;
-  auto add_err = [&](unsigned u) {
-    long long d = (long long)from_negabinary(u) - (long long)from_negabinary(u & keep);
-    unsigned long long ad = (unsigned long long)(d < 0 ? -d : d);
-    unsigned long long sq = ad * ad;  // |d| < 2^32
-    lo += sq;
-    hi += (lo < sq);
-  };
+  auto nsb = [&](unsigned u) { return zfp_nsb(u, kmin); };
+  s2 = 0;
+  lo = 0ull;
+  hi = 0ull;
+  auto add_err = [&](unsigned u) { zfp_add_err(u, kmin, lo, hi); };
   if (ec_all) {
 #pragma unroll
     for (int q = 0; q < NB; q++) {
@@ -236,41 +244,39 @@ __device__ __forceinline__ void zfp_est_core(bool all_zero, int emax, int kmin, 
       add_err(u);
     }
   }
-  my_s2 += (unsigned long long)s2;
-  if (!all_zero && (lo | hi)) {
-    const int bin = emax + D + 126;  // exponent of the 2^d-rescaled error
-    unsigned long long old = atomicAdd(&s_lo[bin], lo);
-    unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
-    if (hi + carry) atomicAdd(&s_hi[bin], hi + carry);
-  }
 }
 
+// Bin of the exponent of the 2^d-rescaled error of a block with exponent emax.
 template <int D>
-__device__ __forceinline__ void zfp_est_accumulate(const BlockWork<D>& w, bool ec_all,
-                                                   unsigned long long& my_s2,
-                                                   unsigned long long* s_lo,
-                                                   unsigned long long* s_hi) {
-  constexpr EcPositions<D> EC{};
-  zfp_est_core<D>(w.bi.all_zero, w.bi.emax, w.bi.kmin, ec_all,
-                  [&](int j) { return ec_all ? w.u[j] : w.u[EC.pos[j]]; }, my_s2, s_lo, s_hi);
-}
+__device__ __forceinline__ int mse_bin(int emax) { return emax + D + 126; }
 
-// Sampled blocks [u0, u1) of one field, strided over the CTA's threads.
-template <int D>
-__device__ __forceinline__ void zfp_est_item(const FieldDev& f, const ParamsDev& p, int minexp,
-                                             long long u0, long long u1,
-                                             unsigned long long& my_s2, unsigned long long* s_lo,
+// Adds each lane's 128-bit error sum (when has) to its bin of the shared
+// (s_lo, s_hi) arrays.  Every lane of the warp calls.  The blocks of a warp
+// mostly share one exponent: then the warp sums the pairs with shuffles and
+// one lane adds the total (32 lanes adding to one 64-bit word would be
+// serialised); otherwise each lane adds its own.
+__device__ __forceinline__ void mse_add_warp(bool has, int bin, unsigned long long lo,
+                                             unsigned long long hi, unsigned long long* s_lo,
                                              unsigned long long* s_hi) {
-  constexpr int NB = 1 << (2 * D);
-  const bool ec_all = p.ec_mode == RD_EC_ALL;
-  for (long long u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
-    int b[3] = {0, 0, 0};
-    decode_block<D>(f, u, true, b);
-    float v[NB];
-    load_block<D>(f, b, v);
-    BlockWork<D> w;
-    w.forward(v, minexp);
-    zfp_est_accumulate<D>(w, ec_all, my_s2, s_lo, s_hi);
+  const int bmin = __reduce_min_sync(0xffffffffu, has ? bin : 0x7fffffff);
+  const int bmax = __reduce_max_sync(0xffffffffu, has ? bin : -1);
+  if (bmax < 0) return;  // no lane has a term
+  if (bmin == bmax) {
+    if (!has) {
+      lo = 0ull;
+      hi = 0ull;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long lo2 = __shfl_xor_sync(0xffffffffu, lo, o);
+      const unsigned long long hi2 = __shfl_xor_sync(0xffffffffu, hi, o);
+      const unsigned long long sum = lo + lo2;
+      hi += hi2 + (sum < lo ? 1ull : 0ull);
+      lo = sum;
+    }
+    if ((threadIdx.x & 31) == 0) atomic_add_u128(&s_lo[bmin], &s_hi[bmin], lo, hi);
+  } else if (has) {
+    atomic_add_u128(&s_lo[bin], &s_hi[bin], lo, hi);
   }
 }
 

@@ -137,13 +137,16 @@ def test_work_split_and_graph_replay_change_nothing(R, ctx, dev_fields, singles,
         ctx.batch_set_config(None)
 
 
-def test_replay_is_six_launches(R, ctx, dev_fields):
+def test_replay_launch_count(R, ctx, dev_fields):
+    """reset, range, one sampled-blocks launch per dimensionality present,
+    ZFP estimate, SZ histogram, code prep, final."""
     ps = _params(R)
     for _ in range(2):
         ctx.select_batch(dev_fields, ps)
     n0 = ctx.launch_count()
     ctx.select_batch(dev_fields, ps)
-    assert ctx.launch_count() - n0 == 6
+    dims = {x.dim() for x in dev_fields}
+    assert ctx.launch_count() - n0 == 6 + len(dims)
 
 
 def test_batch_truth_equals_evaluate(R, ctx, dev_fields):
