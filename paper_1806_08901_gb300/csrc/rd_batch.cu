@@ -120,34 +120,10 @@ __device__ __forceinline__ float key_res(uint32_t k) {
   return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
-// Ascending bitonic sorting network over N keys held in registers (every
-// index is a compile-time constant once unrolled).
-template <int N>
-__device__ __forceinline__ void sort_keys(uint32_t* a) {
-#pragma unroll
-  for (int k = 2; k <= N; k <<= 1) {
-#pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-#pragma unroll
-      for (int i = 0; i < N; i++) {
-        const int l = i ^ j;
-        if (l > i) {
-          const uint32_t x = a[i], y = a[l];
-          const bool up = (i & k) == 0;
-          a[i] = up ? min(x, y) : max(x, y);
-          a[l] = up ? max(x, y) : min(x, y);
-        }
-      }
-    }
-  }
-}
-
 // One thread per sampled block: the SZ residuals of the block's points (the
 // float32 nested differences of est_residual; NaN past the extent) are
-// stored for the histogram pass as ascending keys (the histogram does not
-// depend on the order of a block's points, and sorted codes let a warp
-// count runs of equal codes with one atomic each), and the block's ZFP
-// exponent and
+// stored for the histogram pass as order-preserving keys, and the block's
+// ZFP exponent and
 // negabinary coefficients in sequency order (the EC positions, or all of
 // them) for the ZFP estimate pass.  The block-floating-point cast and the
 // decorrelating transform use only the block exponent, so nothing here
@@ -165,15 +141,7 @@ __device__ __forceinline__ void sampled_blocks_item(const BatchField& F, long lo
     sampled_block_origin<D>(f, sb, o);
     float cube[NC];
     load_cube<D>(f, o, cube);
-    // ZFP: the block's values (with far-edge replication) are the cube's
-    // entries with every index >= 1
-    float v[NB];
-#pragma unroll
-    for (int t = 0; t < NB; t++) {
-      const int k = t & 3, j = D >= 2 ? (t >> 2) & 3 : 0, i = D == 3 ? t >> 4 : 0;
-      v[t] = cube[((D == 3 ? i + 1 : 0) * 5 + (D >= 2 ? j + 1 : 0)) * 5 + k + 1];
-    }
-    // SZ residuals (the cube is dead after these)
+    // SZ residuals
     float r[NB];
 #pragma unroll
     for (int t = 0; t < NB; t++) {
@@ -190,52 +158,59 @@ __device__ __forceinline__ void sampled_blocks_item(const BatchField& F, long lo
       if (D == 3) ok = ok && o[0] + i < f.n[0];
       r[t] = ok ? est_residual<D>(nb) : __int_as_float(0x7fc00000);
     }
-    uint32_t key[NB];
-#pragma unroll
-    for (int t = 0; t < NB; t++) key[t] = res_key(r[t]);
-    {
-      BlockWork<D> w;
-      w.forward(v, 0);  // the precision (and so minexp) is not used here
-      F.ze[sb] = w.bi.emax;
-      if (ec_all) {
-#pragma unroll
-        for (int q = 0; q < NB; q++) F.zc[q * ns + sb] = w.u[q];
-      } else {
-#pragma unroll
-        for (int j = 0; j < EcPositions<D>::M; j++) F.zc[j * ns + sb] = w.u[EC.pos[j]];
-      }
-    }
-    sort_keys<NB>(key);
     uint4* dst = reinterpret_cast<uint4*>(F.res + sb * NB);
 #pragma unroll
-    for (int t = 0; t < NB; t += 4) dst[t / 4] = make_uint4(key[t], key[t + 1], key[t + 2], key[t + 3]);
+    for (int t = 0; t < NB; t += 4)
+      dst[t / 4] = make_uint4(res_key(r[t]), res_key(r[t + 1]), res_key(r[t + 2]), res_key(r[t + 3]));
+    // ZFP: the block's values (with far-edge replication) are the cube's
+    // entries with every index >= 1
+    float v[NB];
+#pragma unroll
+    for (int t = 0; t < NB; t++) {
+      const int k = t & 3, j = D >= 2 ? (t >> 2) & 3 : 0, i = D == 3 ? t >> 4 : 0;
+      v[t] = cube[((D == 3 ? i + 1 : 0) * 5 + (D >= 2 ? j + 1 : 0)) * 5 + k + 1];
+    }
+    BlockWork<D> w;
+    w.forward(v, 0);  // the precision (and so minexp) is not used here
+    F.ze[sb] = w.bi.emax;
+    if (ec_all) {
+#pragma unroll
+      for (int q = 0; q < NB; q++) F.zc[q * ns + sb] = w.u[q];
+    } else {
+#pragma unroll
+      for (int j = 0; j < EcPositions<D>::M; j++) F.zc[j * ns + sb] = w.u[EC.pos[j]];
+    }
   }
 }
 
 // ZFP estimator terms of the sampled blocks [b0, b1) of one field from the
 // stored coefficients: the precision of a block follows from its exponent
-// and the field's minexp (block_info's rule), then zfp_est_terms.
+// and the field's minexp (block_info's rule), then zfp_est_terms.  A lane
+// takes kZfpPerLane blocks at a time, every load issued before any use.
+constexpr int kZfpPerLane = 1;
+
 template <int D>
 __device__ __forceinline__ void zfp_stored_item(const BatchField& F, long long b0, long long b1,
                                                 int minexp, unsigned long long& my_s2,
                                                 unsigned long long* s_lo, unsigned long long* s_hi) {
+  constexpr int NB = 1 << (2 * D), M = EcPositions<D>::M;
   const bool ec_all = F.p.ec_mode == RD_EC_ALL;
   const long long ns = F.f.nsampled;
-  for (long long base = b0; base < b1; base += blockDim.x) {  // warp-uniform trips
-    const long long sb = base + threadIdx.x;
-    bool has = false;
-    int emax = -127;
-    unsigned long long lo = 0ull, hi = 0ull;
-    if (sb < b1) {
-      // every load of the block issued before any use
-      constexpr int NB = 1 << (2 * D), M = EcPositions<D>::M;
-      const uint32_t* zc = F.zc + sb;
-      emax = __ldcs(F.ze + sb);
-      const bool all_zero = emax == -127;
-      const int prec = all_zero ? 0 : min(32, max(0, emax - minexp + 2 * (D + 1)));
-      const int kmin = 32 - prec;
-      long long s2 = 0;
-      if (ec_all) {
+  auto kmin_of = [&](int emax) {
+    const int prec = emax == -127 ? 0 : min(32, max(0, emax - minexp + 2 * (D + 1)));
+    return 32 - prec;
+  };
+  if (ec_all) {
+    for (long long base = b0; base < b1; base += blockDim.x) {  // warp-uniform trips
+      const long long sb = base + threadIdx.x;
+      bool has = false;
+      int emax = -127;
+      unsigned long long lo = 0ull, hi = 0ull;
+      if (sb < b1) {
+        const uint32_t* zc = F.zc + sb;
+        emax = __ldcs(F.ze + sb);
+        const int kmin = kmin_of(emax);
+        long long s2 = 0;
         // every coefficient, independent terms: in chunks of M
 #pragma unroll 1
         for (int q0 = 0; q0 < NB; q0 += M) {
@@ -250,16 +225,33 @@ __device__ __forceinline__ void zfp_stored_item(const BatchField& F, long long b
             }
           }
         }
-      } else {
-        uint32_t u[M];
-#pragma unroll
-        for (int j = 0; j < M; j++) u[j] = __ldcs(zc + j * ns);
-        zfp_est_terms<D>(kmin, false, [&](int j) { return u[j]; }, s2, lo, hi);
+        my_s2 += (unsigned long long)s2;
+        has = emax != -127 && (lo | hi);
       }
-      my_s2 += (unsigned long long)s2;
-      has = !all_zero && (lo | hi);
+      mse_add_warp(has, mse_bin<D>(emax), lo, hi, s_lo, s_hi);
     }
-    mse_add_warp(has, mse_bin<D>(emax), lo, hi, s_lo, s_hi);
+    return;
+  }
+  constexpr int P = kZfpPerLane;
+  for (long long base = b0; base < b1; base += (long long)P * blockDim.x) {  // warp-uniform trips
+    uint32_t u[P][M];
+    int emax[P];
+#pragma unroll
+    for (int p = 0; p < P; p++) {
+      const long long sb = base + (long long)p * blockDim.x + threadIdx.x;
+      const bool in = sb < b1;
+      emax[p] = in ? __ldcs(F.ze + sb) : -127;
+#pragma unroll
+      for (int j = 0; j < M; j++) u[p][j] = in ? __ldcs(F.zc + j * ns + sb) : 0u;
+    }
+#pragma unroll
+    for (int p = 0; p < P; p++) {
+      long long s2;
+      unsigned long long lo, hi;
+      zfp_est_terms<D>(kmin_of(emax[p]), false, [&](int j) { return u[p][j]; }, s2, lo, hi);
+      my_s2 += (unsigned long long)s2;
+      mse_add_warp(emax[p] != -127 && (lo | hi), mse_bin<D>(emax[p]), lo, hi, s_lo, s_hi);
+    }
   }
 }
 
@@ -363,9 +355,9 @@ constexpr long long kFlushPoints = 65535;
 constexpr long long kRoundPoints = 21844;  // points between flush checks (3 rounds fit; a multiple of 4)
 
 // Counts 64 consecutive keys of the residual list, two per lane (lane i
-// holds positions 2i and 2i+1): within a block they ascend, so their codes
-// form runs of equal values; the first position of every run adds the run's
-// length with one atomic on its 16-bit counter.  All-ones keys (points past
+// holds positions 2i and 2i+1): neighbouring points of a smooth field often
+// share a code, so the first position of every run of equal codes adds the
+// run's length with one atomic on its 16-bit counter.  All-ones keys (points past
 // the extent, or past the list) count nothing.  Every lane of the warp
 // calls.
 __device__ __forceinline__ void hist_add_runs(uint32_t* s_win, uint32_t ka, uint32_t kb, float inv,

@@ -252,31 +252,28 @@ __device__ __forceinline__ int mse_bin(int emax) { return emax + D + 126; }
 
 // Adds each lane's 128-bit error sum (when has) to its bin of the shared
 // (s_lo, s_hi) arrays.  Every lane of the warp calls.  The blocks of a warp
-// mostly share one exponent: then the warp sums the pairs with shuffles and
-// one lane adds the total (32 lanes adding to one 64-bit word would be
-// serialised); otherwise each lane adds its own.
+// share few exponents: for each bin present, the warp sums its lanes' pairs
+// with shuffles and one lane adds the total (lanes adding 64-bit words of
+// one bin one by one would be serialised).
 __device__ __forceinline__ void mse_add_warp(bool has, int bin, unsigned long long lo,
                                              unsigned long long hi, unsigned long long* s_lo,
                                              unsigned long long* s_hi) {
-  const int bmin = __reduce_min_sync(0xffffffffu, has ? bin : 0x7fffffff);
-  const int bmax = __reduce_max_sync(0xffffffffu, has ? bin : -1);
-  if (bmax < 0) return;  // no lane has a term
-  if (bmin == bmax) {
-    if (!has) {
-      lo = 0ull;
-      hi = 0ull;
-    }
+  unsigned pending = __ballot_sync(0xffffffffu, has);
+  while (pending) {  // warp-uniform
+    const int leader = __ffs(pending) - 1;
+    const int b = __shfl_sync(0xffffffffu, bin, leader);
+    const bool mine = has && bin == b;
+    pending &= ~__ballot_sync(0xffffffffu, mine);
+    unsigned long long l = mine ? lo : 0ull, h = mine ? hi : 0ull;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long lo2 = __shfl_xor_sync(0xffffffffu, lo, o);
-      const unsigned long long hi2 = __shfl_xor_sync(0xffffffffu, hi, o);
-      const unsigned long long sum = lo + lo2;
-      hi += hi2 + (sum < lo ? 1ull : 0ull);
-      lo = sum;
+      const unsigned long long l2 = __shfl_xor_sync(0xffffffffu, l, o);
+      const unsigned long long h2 = __shfl_xor_sync(0xffffffffu, h, o);
+      const unsigned long long sum = l + l2;
+      h += h2 + (sum < l ? 1ull : 0ull);
+      l = sum;
     }
-    if ((threadIdx.x & 31) == 0) atomic_add_u128(&s_lo[bmin], &s_hi[bmin], lo, hi);
-  } else if (has) {
-    atomic_add_u128(&s_lo[bin], &s_hi[bin], lo, hi);
+    if ((int)(threadIdx.x & 31) == leader) atomic_add_u128(&s_lo[b], &s_hi[b], l, h);
   }
 }
 
