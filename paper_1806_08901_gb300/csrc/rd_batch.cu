@@ -348,20 +348,23 @@ __global__ void __launch_bounds__(kBatchZfpThreads) k_batch_zfp(const BatchField
 // a warp often hit together, fall in different words).  The residuals of
 // rough fields at fine bounds spread over tens of thousands of codes: a
 // partial window sent most of them to global atomics, which set the pace.
-// A counter cannot pass 65535 between flushes: the window is flushed before
-// it has counted kFlushPoints points.
+// A counter cannot pass 65535 between flushes: an add that takes a counter
+// to kHotCount or more raises a flag, and the CTA flushes at the end of the
+// round of kRoundPoints points in progress, which adds at most kRoundPoints
+// to any counter.  Wide code distributions, whose counters stay low, flush
+// only when the field changes.
 constexpr int kPackWords = 32768;
-constexpr long long kFlushPoints = 65535;
-constexpr long long kRoundPoints = 21844;  // points between flush checks (3 rounds fit; a multiple of 4)
+constexpr long long kRoundPoints = 16384;  // points between flush checks (a multiple of 4)
+constexpr uint32_t kHotCount = 65535u - (uint32_t)kRoundPoints;
 
 // Counts 64 consecutive keys of the residual list, two per lane (lane i
 // holds positions 2i and 2i+1): neighbouring points of a smooth field often
 // share a code, so the first position of every run of equal codes adds the
-// run's length with one atomic on its 16-bit counter.  All-ones keys (points past
-// the extent, or past the list) count nothing.  Every lane of the warp
-// calls.
+// run's length with one atomic on its 16-bit counter (and raises *s_hot
+// when the counter reaches kHotCount).  All-ones keys (points past the
+// extent, or past the list) count nothing.  Every lane of the warp calls.
 __device__ __forceinline__ void hist_add_runs(uint32_t* s_win, uint32_t ka, uint32_t kb, float inv,
-                                              int R) {
+                                              int R, int* s_hot) {
   const int lane = threadIdx.x & 31;
   const int sa = ka != 0xffffffffu ? est_symbol(key_res(ka), inv, R) : -1;
   const int sb = kb != 0xffffffffu ? est_symbol(key_res(kb), inv, R) : -1;
@@ -377,7 +380,11 @@ __device__ __forceinline__ void hist_add_runs(uint32_t* s_win, uint32_t ka, uint
     const int j = __ffs(later) - 1;
     next = 2 * j + (((ba >> j) & 1u) ? 0 : 1);
   }
-  auto add = [&](int sym, unsigned cnt) { atomicAdd(&s_win[sym & 0x7fff], cnt << ((sym >> 15) << 4)); };
+  auto add = [&](int sym, unsigned cnt) {
+    const int sh = (sym >> 15) << 4;
+    const uint32_t old = atomicAdd(&s_win[sym & 0x7fff], cnt << sh);
+    if (((old >> sh) & 0xffffu) + cnt >= kHotCount) *s_hot = 1;
+  };
   if (ha && sa >= 0) add(sa, hb ? 1u : (unsigned)(next - 2 * lane));
   if (hb && sb >= 0) add(sb, (unsigned)(next - 2 * lane - 1));
 }
@@ -400,16 +407,17 @@ __device__ __forceinline__ void window_flush(uint32_t* s_win, uint32_t* g_hist) 
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kBatchSzThreads) k_batch_sz_hist(const BatchField* __restrict__ bf,
+__global__ void __launch_bounds__(kBatchSzThreads, 1) k_batch_sz_hist(const BatchField* __restrict__ bf,
                                                                    const BatchItem* __restrict__ items,
                                                                    int nitems) {
   extern __shared__ uint32_t s_win[];  // kPackWords words of two counters
+  __shared__ int s_hot;                // a counter reached kHotCount
   int i0, i1;
   cta_items(nitems, i0, i1);
   for (int i = threadIdx.x; i < kPackWords; i += blockDim.x) s_win[i] = 0u;
+  if (threadIdx.x == 0) s_hot = 0;
   __syncthreads();
-  int cur = -1;        // the field the window holds
-  long long held = 0;  // points counted since the last flush
+  int cur = -1;  // the field the window holds
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int W = kBatchSzThreads / 32;
   constexpr int U = 4;  // independent 8-byte loads in flight per lane
@@ -420,7 +428,6 @@ __global__ void __launch_bounds__(kBatchSzThreads) k_batch_sz_hist(const BatchFi
     if (item.field != cur) {  // uniform over the CTA
       if (cur >= 0) window_flush(s_win, bf[cur].ws->hist[0]);
       cur = item.field;
-      held = 0;
     }
     if (ws->sc.status != RD_OK || ws->sc.constant) continue;
     const float inv = ws->sc.inv;
@@ -432,11 +439,6 @@ __global__ void __launch_bounds__(kBatchSzThreads) k_batch_sz_hist(const BatchFi
     const long long npts = (item.end - item.begin) * nb;
     for (long long r0 = 0; r0 < npts; r0 += kRoundPoints) {
       const long long rn = npts - r0 < kRoundPoints ? npts - r0 : kRoundPoints;
-      if (held + rn > kFlushPoints) {  // uniform over the CTA
-        window_flush(s_win, ws->hist[0]);
-        held = 0;
-      }
-      held += rn;
       const uint2* q2 = k2 + r0 / 2;
       const int n2 = (int)(rn / 2);
       const int nchunks = (n2 + 31) >> 5;
@@ -449,7 +451,13 @@ __global__ void __launch_bounds__(kBatchSzThreads) k_batch_sz_hist(const BatchFi
           q[k] = (c < nchunks && g < n2) ? __ldcs(q2 + g) : make_uint2(0xffffffffu, 0xffffffffu);
         }
 #pragma unroll
-        for (int k = 0; k < U; k++) hist_add_runs(s_win, q[k].x, q[k].y, inv, R);
+        for (int k = 0; k < U; k++) hist_add_runs(s_win, q[k].x, q[k].y, inv, R, &s_hot);
+      }
+      __syncthreads();
+      if (s_hot) {  // uniform after the barrier
+        window_flush(s_win, ws->hist[0]);
+        if (threadIdx.x == 0) s_hot = 0;
+        __syncthreads();
       }
     }
   }
