@@ -207,14 +207,13 @@ typedef struct {
 
 /* Algorithm 1 lines 2-12 for n fields at once, e.g. every field of a
  * simulation snapshot, of uneven 2D/3D sizes (the paper's algorithm loops
- * over the fields of a snapshot).  Six launches plus one per dimensionality
+ * over the fields of a snapshot).  Five launches plus one per dimensionality
  * present cover all fields: a reset; persistent passes over work items of
  * every field (runs of a field's values for the range; runs of its sampled
- * blocks, read once for both estimators, whose SZ residuals and ZFP
- * coefficients are stored, one launch per dimensionality; the stored
- * coefficients for the ZFP estimate; the stored residuals for the SZ
- * histogram; the CTA that ends a field's last range item derives VR and
- * eb_abs, the one that ends its last ZFP item derives delta); the
+ * blocks, read once for both estimators, one launch per dimensionality,
+ * for the ZFP estimate and the SZ residuals; the stored residuals for the
+ * SZ histogram; the CTA that ends a field's last range item derives VR and
+ * eb_abs, the one that ends its last block item derives delta); the
  * count-of-counts; one CTA per field for the Huffman cost, entropy, rates,
  * PSNRs and selection.
  *  - fields[i]: DEVICE memory only (RD_ERR_INVALID_ARG otherwise);
@@ -228,12 +227,11 @@ typedef struct {
  *    record zeroed.
  *  - The context holds one workspace per field (about 2.7 MB each) and caches
  *    a plan per distinct set of fields and parameters, with the stored SZ
- *    residuals, ZFP coefficients and exponents of its sampled blocks (4^d +
- *    EC positions + 1 words per sampled block: 6-8% of the fields' bytes at
- *    r_sp = 0.05, counted against the HBM budget): the plan's first call
- *    runs the autotuner (three work-item sizes, the passes timed, the fastest
- *    kept) unless rd_batch_set_config forced a split; its second call
- *    captures a CUDA graph that later calls replay.
+ *    residuals of its sampled blocks (4^d words per sampled block: about 5%
+ *    of the fields' bytes at r_sp = 0.05, counted against the HBM budget):
+ *    the plan's first call runs the autotuner (three work-item sizes, the
+ *    passes timed, the fastest kept) unless rd_batch_set_config forced a
+ *    split; its second call captures a CUDA graph that later calls replay.
  *  - Each field's records equal those of rd_select (and of rd_evaluate for
  *    the truth) on that field alone. */
 int32_t rd_select_batch(rd_context* ctx, const rd_field* fields,

@@ -21,7 +21,7 @@ namespace {
 const char* kKernelNames[K_COUNT] = {
     "reset", "range", "prepare", "zfp_pass", "delta", "sz_est", "sz_pass",
     "code_prep", "huffman", "finish", "zfp_inspect", "sz_inspect",
-    "batch_reset", "batch_range", "batch_blocks", "batch_zfp", "batch_sz_hist", "batch_code_prep",
+    "batch_reset", "batch_range", "batch_blocks", "batch_sz_hist", "batch_code_prep",
     "batch_final", "batch_truth"};
 
 struct KStat {
@@ -79,12 +79,11 @@ struct BatchPlan {
   std::vector<BatchField> hbf;
   std::vector<Geometry> geo;
   BatchField* dbf = nullptr;
-  // range items, sampled-block items (grouped by dimensionality), ZFP
-  // estimate items, SZ items; each list in field order
+  // range items, sampled-block items (grouped by dimensionality), SZ items
   BatchItem* ditems = nullptr;
-  float* dres = nullptr;        // per sampled block: SZ residuals, ZFP coefficients, exponent
+  float* dres = nullptr;        // SZ residual keys of every field's sampled blocks
   size_t res_bytes = 0;
-  int n_range = 0, n_blk = 0, n_zfp = 0, n_sz = 0;
+  int n_range = 0, n_blk = 0, n_sz = 0;
   int blk_first[4] = {0, 0, 0, 0};  // sampled-block items of d-dimensional fields: [blk_first[d-1], blk_first[d])
 
   cudaGraphExec_t exec = nullptr;
@@ -116,7 +115,7 @@ struct rd_context {
   int range_ctas = 0;
   int zfp_ctas[4] = {0, 0, 0, 0};
   int sz_ctas[4] = {0, 0, 0, 0};
-  int b_range_ctas = 0, b_zfp_ctas = 0, b_sz_ctas = 0;  // resident CTAs of the batched passes
+  int b_range_ctas = 0, b_sz_ctas = 0;                   // resident CTAs of the batched passes
   int b_blocks_ctas[3] = {0, 0, 0};                       // sampled-blocks pass, per dimensionality
   bool profiling = false;
   KStat stats[K_COUNT];
@@ -610,11 +609,11 @@ int ensure_batch_capacity(rd_context* c, int n) {
 }
 
 // Work items of the passes for one split: range items (runs of
-// range_values values); sampled-block items grouped by dimensionality, ZFP
-// estimate items and SZ items (runs of zfp_blocks / sz_blocks sampled blocks
-// of a 3D field; 4^(3-d) times as many of a d-dimensional one, so that every
-// item holds about as many points); each list in field order.  Per-field
-// item counts go into the field table.
+// range_values values); sampled-block items grouped by dimensionality and SZ
+// items (runs of zfp_blocks / sz_blocks sampled blocks of a 3D field;
+// 4^(3-d) times as many of a d-dimensional one, so that every item holds
+// about as many points); each list otherwise in field order.  Per-field item
+// counts go into the field table.
 void build_items(BatchPlan* b, const rd_batch_config& cfg, std::vector<BatchItem>& items) {
   auto per_item = [](long long blocks3d, int d) { return blocks3d << (2 * (3 - d)); };
   items.clear();
@@ -637,14 +636,11 @@ void build_items(BatchPlan* b, const rd_batch_config& cfg, std::vector<BatchItem
   b->blk_first[0] = 0;
   for (int d = 1; d <= 3; d++) {
     for (int i = 0; i < n; i++)
-      if (b->hbf[i].f.d == d) split(i, b->hbf[i].f.nsampled, per_item(cfg.zfp_blocks, d));
+      if (b->hbf[i].f.d == d)
+        b->hbf[i].items_zfp = split(i, b->hbf[i].f.nsampled, per_item(cfg.zfp_blocks, d));
     b->blk_first[d] = (int)(items.size() - base);
   }
   b->n_blk = (int)(items.size() - base);
-  base = items.size();
-  for (int i = 0; i < n; i++)
-    b->hbf[i].items_zfp = split(i, b->hbf[i].f.nsampled, per_item(cfg.zfp_blocks, b->hbf[i].f.d));
-  b->n_zfp = (int)(items.size() - base);
   base = items.size();
   for (int i = 0; i < n; i++) split(i, b->hbf[i].f.nsampled, per_item(cfg.sz_blocks, b->hbf[i].f.d));
   b->n_sz = (int)(items.size() - base);
@@ -694,16 +690,15 @@ rd_batch_config split_level(const rd_context* c, int level, int ctas) {
 
 // The estimate launches of a batch (reset .. final), optionally with an
 // event pair around the item-based passes (the autotuner's timing).  The
-// passes are stream-ordered: running the compute-bound ZFP and SZ passes of
-// some fields beside the bandwidth-bound range pass of others, on a second
-// stream, slowed both more than it overlapped.
+// passes are stream-ordered: running the compute-bound passes of some fields
+// beside the bandwidth-bound range pass of others, on a second stream,
+// slowed both more than it overlapped.
 int issue_batch_estimate(rd_context* c, BatchPlan* b, cudaStream_t s, cudaEvent_t* ev) {
   const int n = b->n;
   const int cap = b->cfg.ctas;
   const BatchItem* rit = b->ditems;
   const BatchItem* bit = rit + b->n_range;
-  const BatchItem* zit = bit + b->n_blk;
-  const BatchItem* sit = zit + b->n_zfp;
+  const BatchItem* sit = bit + b->n_blk;
   int rc;
   if ((rc = launch(c, K_B_RESET, s, [&] { return launch_batch_reset(b->dbf, n, b->need_gt, s); })))
     return rc;
@@ -721,10 +716,6 @@ int issue_batch_estimate(rd_context* c, BatchPlan* b, cudaStream_t s, cudaEvent_
          })))
       return rc;
   }
-  if ((rc = launch(c, K_B_ZEST, s, [&] {
-         return launch_batch_zfp(b->dbf, zit, b->n_zfp, pass_ctas(c->b_zfp_ctas, cap), s);
-       })))
-    return rc;
   if ((rc = launch(c, K_B_SZ, s, [&] {
          return launch_batch_sz_hist(b->dbf, sit, b->n_sz, pass_ctas(c->b_sz_ctas, cap), s);
        })))
@@ -868,16 +859,10 @@ int batch_call(rd_context* c, const rd_field* fields, const rd_params* params, i
     b->need_gt = need_gt;
     b->geo = geo;
     b->hbf.resize((size_t)n);
-    // per sampled block: the SZ residuals of its points (4^d floats), its
-    // kept ZFP coefficients and its exponent (one word each)
-    size_t res_floats = 0, coef_words = 0, exp_words = 0;
-    for (int i = 0; i < n; i++) {
-      const size_t nsb = (size_t)geo[i].f.nsampled;
-      res_floats += nsb << (2 * geo[i].f.d);
-      coef_words += nsb * (size_t)ec_count(geo[i].f.d, params[i].ec_mode);
-      exp_words += nsb;
-    }
-    b->res_bytes = (res_floats + coef_words + exp_words) * sizeof(float);
+    // the SZ residuals of every field's sampled blocks (4^d keys each)
+    size_t res_floats = 0;
+    for (int i = 0; i < n; i++) res_floats += (size_t)geo[i].f.nsampled << (2 * geo[i].f.d);
+    b->res_bytes = res_floats * sizeof(float);
     if (c->budget && c->held + b->res_bytes > c->budget) {
       delete b;
       return RD_ERR_BUDGET;
@@ -888,9 +873,7 @@ int batch_call(rd_context* c, const rd_field* fields, const rd_params* params, i
       return RD_ERR_OOM;
     }
     c->held += b->res_bytes;
-    size_t roff = 0, coff = 0, eoff = 0;
-    uint32_t* coef = reinterpret_cast<uint32_t*>(b->dres + res_floats);
-    int32_t* exps = reinterpret_cast<int32_t*>(b->dres + res_floats + coef_words);
+    size_t roff = 0;
     for (int i = 0; i < n; i++) {
       BatchField& F = b->hbf[i];
       memset(&F, 0, sizeof(F));
@@ -902,11 +885,6 @@ int batch_call(rd_context* c, const rd_field* fields, const rd_params* params, i
       F.need_gt = need_gt;
       F.res = b->dres + roff;
       roff += (size_t)F.f.nsampled << (2 * F.f.d);
-      F.mc = ec_count(F.f.d, params[i].ec_mode);
-      F.zc = coef + coff;
-      coff += (size_t)F.f.nsampled * (size_t)F.mc;
-      F.ze = exps + eoff;
-      eoff += (size_t)F.f.nsampled;
     }
     if (forced) {
       rd_batch_config cfg = c->batch_force;
@@ -1048,7 +1026,7 @@ int32_t rd_context_create(int32_t device, size_t hbm_budget, rd_context** out) {
     c->zfp_ctas[d] = zfp_occupancy(d, c->num_sms);
     c->sz_ctas[d] = sz_occupancy(d, c->num_sms);
   }
-  batch_occupancy(c->num_sms, &c->b_range_ctas, c->b_blocks_ctas, &c->b_zfp_ctas, &c->b_sz_ctas);
+  batch_occupancy(c->num_sms, &c->b_range_ctas, c->b_blocks_ctas, &c->b_sz_ctas);
   *out = c;
   return RD_OK;
 }

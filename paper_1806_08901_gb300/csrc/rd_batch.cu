@@ -3,22 +3,20 @@
 //   range: runs of a field's values; the CTA that ends a field's last item
 //     (a counter in the field's workspace, fenced on both sides) derives VR,
 //     eb_abs and the precision exponent (Algorithm 1 line 2);
-//   sampled blocks: runs of a field's sampled blocks, one thread per block:
-//     the block and its one-cell low halo are read once; the SZ residuals
-//     of its points (which do not depend on the bin width) and the ZFP
-//     block exponent and transformed coefficients (which do not depend on
-//     the error bound) are stored;
-//   ZFP estimate: the stored coefficients, truncated at the precision the
-//     error bound sets, give the estimator terms (lines 3-6); the CTA that
-//     ends a field's last item derives delta (line 7);
+//   sampled blocks (one launch per dimensionality): runs of a field's
+//     sampled blocks, one thread per block: the block and its one-cell low
+//     halo are read once; the SZ residuals of its points (which do not
+//     depend on the bin width) are stored, and the ZFP estimator terms
+//     accumulated (lines 3-6); the CTA that ends a field's last item
+//     derives delta (line 7);
 //   SZ histogram: the stored residuals, quantised at delta, coalesced
 //     (line 8).
 // The sampled blocks are scattered: each block row costs a whole DRAM
 // fetch, so one pass that serves both estimators reads about a third of the
 // field where two passes read about six tenths.
-// CTAs stride over the items of their pass; the passes are stream-ordered
-// launches, so no CTA waits on another.  The sampled-blocks pass depends on
-// nothing the range pass derives.
+// CTAs take contiguous ranges of the items of their pass (so that the items
+// of one field share a CTA's accumulators); the passes are stream-ordered
+// launches, so no CTA waits on another.
 #include <math.h>
 #include <stdint.h>
 
@@ -32,7 +30,6 @@ namespace rdk {
 
 constexpr int kBatchRangeThreads = 512;
 constexpr int kBatchBlockThreads = 128;
-constexpr int kBatchZfpThreads = 256;
 constexpr int kBatchSzThreads = 1024;
 
 // ---------------------------------------------------------------------------
@@ -123,147 +120,67 @@ __device__ __forceinline__ float key_res(uint32_t k) {
 // One thread per sampled block: the SZ residuals of the block's points (the
 // float32 nested differences of est_residual; NaN past the extent) are
 // stored for the histogram pass as order-preserving keys, and the block's
-// ZFP exponent and
-// negabinary coefficients in sequency order (the EC positions, or all of
-// them) for the ZFP estimate pass.  The block-floating-point cast and the
-// decorrelating transform use only the block exponent, so nothing here
-// depends on the error bound.
+// ZFP estimator terms (Alg. 1 lines 4-6) accumulated, the exact error sums
+// per block exponent added per warp.
 template <int D>
-__device__ __forceinline__ void sampled_blocks_item(const BatchField& F, long long b0, long long b1) {
+__device__ __forceinline__ void sampled_blocks_item(const BatchField& F, long long b0, long long b1,
+                                                    int minexp, unsigned long long& my_s2,
+                                                    unsigned long long* s_lo,
+                                                    unsigned long long* s_hi) {
   constexpr int NB = 1 << (2 * D);
   constexpr int NC = D == 3 ? 125 : D == 2 ? 25 : 5;
   constexpr EcPositions<D> EC{};
   const FieldDev& f = F.f;
   const bool ec_all = F.p.ec_mode == RD_EC_ALL;
-  const long long ns = f.nsampled;
-  for (long long sb = b0 + threadIdx.x; sb < b1; sb += blockDim.x) {
-    int o[3] = {0, 0, 0};
-    sampled_block_origin<D>(f, sb, o);
-    float cube[NC];
-    load_cube<D>(f, o, cube);
-    // SZ residuals
-    float r[NB];
+  for (long long base = b0; base < b1; base += blockDim.x) {  // warp-uniform trips
+    const long long sb = base + threadIdx.x;
+    bool has = false;
+    int bin = 0;
+    unsigned long long lo = 0ull, hi = 0ull;
+    if (sb < b1) {
+      int o[3] = {0, 0, 0};
+      sampled_block_origin<D>(f, sb, o);
+      float cube[NC];
+      load_cube<D>(f, o, cube);
+      // SZ residuals
+      float r[NB];
 #pragma unroll
-    for (int t = 0; t < NB; t++) {
-      const int k = t & 3, j = D >= 2 ? (t >> 2) & 3 : 0, i = D == 3 ? t >> 4 : 0;
-      Nbr nb;
+      for (int t = 0; t < NB; t++) {
+        const int k = t & 3, j = D >= 2 ? (t >> 2) & 3 : 0, i = D == 3 ? t >> 4 : 0;
+        Nbr nb;
 #pragma unroll
-      for (int m = 0; m < (1 << D); m++) {
-        const int bx = m & 1, by = (m >> 1) & 1, bz = (m >> 2) & 1;
-        const int cz = D == 3 ? i + 1 - bz : 0, cy = D >= 2 ? j + 1 - by : 0, cx = k + 1 - bx;
-        nb.v[m] = cube[(cz * 5 + cy) * 5 + cx];
-      }
-      bool ok = o[D - 1] + k < f.n[D - 1];
-      if (D >= 2) ok = ok && o[D - 2] + j < f.n[D - 2];
-      if (D == 3) ok = ok && o[0] + i < f.n[0];
-      r[t] = ok ? est_residual<D>(nb) : __int_as_float(0x7fc00000);
-    }
-    uint4* dst = reinterpret_cast<uint4*>(F.res + sb * NB);
-#pragma unroll
-    for (int t = 0; t < NB; t += 4)
-      dst[t / 4] = make_uint4(res_key(r[t]), res_key(r[t + 1]), res_key(r[t + 2]), res_key(r[t + 3]));
-    // ZFP: the block's values (with far-edge replication) are the cube's
-    // entries with every index >= 1
-    float v[NB];
-#pragma unroll
-    for (int t = 0; t < NB; t++) {
-      const int k = t & 3, j = D >= 2 ? (t >> 2) & 3 : 0, i = D == 3 ? t >> 4 : 0;
-      v[t] = cube[((D == 3 ? i + 1 : 0) * 5 + (D >= 2 ? j + 1 : 0)) * 5 + k + 1];
-    }
-    BlockWork<D> w;
-    w.forward(v, 0);  // the precision (and so minexp) is not used here
-    F.ze[sb] = w.bi.emax;
-    if (ec_all) {
-#pragma unroll
-      for (int q = 0; q < NB; q++) F.zc[q * ns + sb] = w.u[q];
-    } else {
-#pragma unroll
-      for (int j = 0; j < EcPositions<D>::M; j++) F.zc[j * ns + sb] = w.u[EC.pos[j]];
-    }
-  }
-}
-
-// ZFP estimator terms of the sampled blocks [b0, b1) of one field from the
-// stored coefficients: the precision of a block follows from its exponent
-// and the field's minexp (block_info's rule), then zfp_est_terms.  A lane
-// takes kZfpPerLane blocks at a time, every load issued before any use.
-constexpr int kZfpPerLane = 1;
-
-template <int D>
-__device__ __forceinline__ void zfp_stored_item(const BatchField& F, long long b0, long long b1,
-                                                int minexp, unsigned long long& my_s2,
-                                                unsigned long long* s_lo, unsigned long long* s_hi) {
-  constexpr int NB = 1 << (2 * D), M = EcPositions<D>::M;
-  const bool ec_all = F.p.ec_mode == RD_EC_ALL;
-  const long long ns = F.f.nsampled;
-  auto kmin_of = [&](int emax) {
-    const int prec = emax == -127 ? 0 : min(32, max(0, emax - minexp + 2 * (D + 1)));
-    return 32 - prec;
-  };
-  if (ec_all) {
-    for (long long base = b0; base < b1; base += blockDim.x) {  // warp-uniform trips
-      const long long sb = base + threadIdx.x;
-      bool has = false;
-      int emax = -127;
-      unsigned long long lo = 0ull, hi = 0ull;
-      if (sb < b1) {
-        const uint32_t* zc = F.zc + sb;
-        emax = __ldcs(F.ze + sb);
-        const int kmin = kmin_of(emax);
-        long long s2 = 0;
-        // every coefficient, independent terms: in chunks of M
-#pragma unroll 1
-        for (int q0 = 0; q0 < NB; q0 += M) {
-          uint32_t u[M];
-#pragma unroll
-          for (int j = 0; j < M; j++) u[j] = q0 + j < NB ? __ldcs(zc + (q0 + j) * ns) : 0u;
-#pragma unroll
-          for (int j = 0; j < M; j++) {
-            if (q0 + j < NB) {
-              s2 += 2 * zfp_nsb(u[j], kmin);
-              zfp_add_err(u[j], kmin, lo, hi);
-            }
-          }
+        for (int m = 0; m < (1 << D); m++) {
+          const int bx = m & 1, by = (m >> 1) & 1, bz = (m >> 2) & 1;
+          const int cz = D == 3 ? i + 1 - bz : 0, cy = D >= 2 ? j + 1 - by : 0, cx = k + 1 - bx;
+          nb.v[m] = cube[(cz * 5 + cy) * 5 + cx];
         }
-        my_s2 += (unsigned long long)s2;
-        has = emax != -127 && (lo | hi);
+        bool ok = o[D - 1] + k < f.n[D - 1];
+        if (D >= 2) ok = ok && o[D - 2] + j < f.n[D - 2];
+        if (D == 3) ok = ok && o[0] + i < f.n[0];
+        r[t] = ok ? est_residual<D>(nb) : __int_as_float(0x7fc00000);
       }
-      mse_add_warp(has, mse_bin<D>(emax), lo, hi, s_lo, s_hi);
-    }
-    return;
-  }
-  constexpr int P = kZfpPerLane;
-  for (long long base = b0; base < b1; base += (long long)P * blockDim.x) {  // warp-uniform trips
-    uint32_t u[P][M];
-    int emax[P];
+      uint4* dst = reinterpret_cast<uint4*>(F.res + sb * NB);
 #pragma unroll
-    for (int p = 0; p < P; p++) {
-      const long long sb = base + (long long)p * blockDim.x + threadIdx.x;
-      const bool in = sb < b1;
-      emax[p] = in ? __ldcs(F.ze + sb) : -127;
+      for (int t = 0; t < NB; t += 4)
+        dst[t / 4] = make_uint4(res_key(r[t]), res_key(r[t + 1]), res_key(r[t + 2]), res_key(r[t + 3]));
+      // ZFP: the block's values (with far-edge replication) are the cube's
+      // entries with every index >= 1
+      float v[NB];
 #pragma unroll
-      for (int j = 0; j < M; j++) u[p][j] = in ? __ldcs(F.zc + j * ns + sb) : 0u;
-    }
-#pragma unroll
-    for (int p = 0; p < P; p++) {
+      for (int t = 0; t < NB; t++) {
+        const int k = t & 3, j = D >= 2 ? (t >> 2) & 3 : 0, i = D == 3 ? t >> 4 : 0;
+        v[t] = cube[((D == 3 ? i + 1 : 0) * 5 + (D >= 2 ? j + 1 : 0)) * 5 + k + 1];
+      }
+      BlockWork<D> w;
+      w.forward(v, minexp);
       long long s2;
-      unsigned long long lo, hi;
-      zfp_est_terms<D>(kmin_of(emax[p]), false, [&](int j) { return u[p][j]; }, s2, lo, hi);
+      zfp_est_terms<D>(w.bi.kmin, ec_all, [&](int j) { return ec_all ? w.u[j] : w.u[EC.pos[j]]; }, s2,
+                       lo, hi);
       my_s2 += (unsigned long long)s2;
-      mse_add_warp(emax[p] != -127 && (lo | hi), mse_bin<D>(emax[p]), lo, hi, s_lo, s_hi);
+      has = !w.bi.all_zero && (lo | hi);
+      bin = mse_bin<D>(w.bi.emax);
     }
-  }
-}
-
-// One launch per dimensionality (the items of d-dimensional fields): the
-// registers of the 3D form would otherwise set the occupancy of all.
-template <int D>
-__global__ void __launch_bounds__(kBatchBlockThreads) k_batch_blocks(const BatchField* __restrict__ bf,
-                                                                     const BatchItem* __restrict__ items,
-                                                                     int nitems) {
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const BatchItem item = items[it];
-    sampled_blocks_item<D>(bf[item.field], item.begin, item.end);
+    mse_add_warp(has, bin, lo, hi, s_lo, s_hi);
   }
 }
 
@@ -301,9 +218,12 @@ __device__ __forceinline__ void zfp_commit(const BatchField& F, uint32_t cnt,
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kBatchZfpThreads) k_batch_zfp(const BatchField* __restrict__ bf,
-                                                                const BatchItem* __restrict__ items,
-                                                                int nitems) {
+// One launch per dimensionality (the items of d-dimensional fields): the
+// registers of the 3D form would otherwise set the occupancy of all.
+template <int D>
+__global__ void __launch_bounds__(kBatchBlockThreads) k_batch_blocks(const BatchField* __restrict__ bf,
+                                                                     const BatchItem* __restrict__ items,
+                                                                     int nitems) {
   __shared__ unsigned long long s_lo[kMseBins], s_hi[kMseBins];
   __shared__ unsigned long long s_s2;
   __shared__ int s_last;
@@ -329,13 +249,8 @@ __global__ void __launch_bounds__(kBatchZfpThreads) k_batch_zfp(const BatchField
     const BatchField& F = bf[item.field];
     Workspace* ws = F.ws;
     cnt++;
-    if (ws->sc.status != RD_OK || ws->sc.constant) continue;
-    const int minexp = ws->sc.minexp;
-    switch (F.f.d) {
-      case 1: zfp_stored_item<1>(F, item.begin, item.end, minexp, my_s2, s_lo, s_hi); break;
-      case 2: zfp_stored_item<2>(F, item.begin, item.end, minexp, my_s2, s_lo, s_hi); break;
-      default: zfp_stored_item<3>(F, item.begin, item.end, minexp, my_s2, s_lo, s_hi); break;
-    }
+    if (ws->sc.status != RD_OK || ws->sc.constant) continue;  // uniform over the CTA
+    sampled_blocks_item<D>(F, item.begin, item.end, ws->sc.minexp, my_s2, s_lo, s_hi);
   }
   if (cur >= 0) zfp_commit(bf[cur], cnt, my_s2, s_lo, s_hi, &s_s2, &s_last);
 }
@@ -490,12 +405,6 @@ cudaError_t launch_batch_blocks(const BatchField* bf, const BatchItem* items, in
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_zfp(const BatchField* bf, const BatchItem* items, int nitems, int ctas,
-                             cudaStream_t s) {
-  k_batch_zfp<<<grid_for(nitems, ctas), kBatchZfpThreads, 0, s>>>(bf, items, nitems);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_batch_sz_hist(const BatchField* bf, const BatchItem* items, int nitems, int ctas,
                                  cudaStream_t s) {
   k_batch_sz_hist<<<grid_for(nitems, ctas), kBatchSzThreads, kPackWords * sizeof(uint32_t), s>>>(
@@ -510,12 +419,11 @@ static int occupancy(const void* fn, int threads, int num_sms) {
   return per * num_sms;
 }
 
-void batch_occupancy(int num_sms, int* range_ctas, int* blocks_ctas, int* zfp_ctas, int* sz_ctas) {
+void batch_occupancy(int num_sms, int* range_ctas, int* blocks_ctas, int* sz_ctas) {
   *range_ctas = occupancy((const void*)k_batch_range, kBatchRangeThreads, num_sms);
   blocks_ctas[0] = occupancy((const void*)k_batch_blocks<1>, kBatchBlockThreads, num_sms);
   blocks_ctas[1] = occupancy((const void*)k_batch_blocks<2>, kBatchBlockThreads, num_sms);
   blocks_ctas[2] = occupancy((const void*)k_batch_blocks<3>, kBatchBlockThreads, num_sms);
-  *zfp_ctas = occupancy((const void*)k_batch_zfp, kBatchZfpThreads, num_sms);
   cudaFuncSetAttribute(k_batch_sz_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        kPackWords * (int)sizeof(uint32_t));
   int per = 0;

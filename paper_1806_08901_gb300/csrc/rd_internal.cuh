@@ -100,14 +100,12 @@ struct BatchField {
   ParamsDev p;
   Workspace* ws;                 // the field's own workspace
   float* res;                    // SZ residuals of the sampled blocks' points (4^d per block)
-  uint32_t* zc;                  // ZFP coefficients of the sampled blocks: mc planes of nsampled
-  int32_t* ze;                   // block exponent of each sampled block (-127: all zero)
   unsigned long long ncoeff;     // EC-sampled coefficients (denominator of MSE_sp)
   unsigned long long npoints;    // valid points of the sampled blocks
   uint32_t items_range;          // range work items of the field
   uint32_t items_zfp;            // sampled-block work items of the field
   int32_t need_gt;               // the quantiser is also prepared for the ground truth
-  int32_t mc;                    // coefficients kept per block: the EC positions, or all 4^d
+  int32_t pad;
 };
 
 // A work item of a batched pass: units [begin, end) of one field (values
@@ -142,7 +140,6 @@ enum KernelId {
   K_B_RESET,
   K_B_RANGE,
   K_B_ZFP,
-  K_B_ZEST,
   K_B_SZ,
   K_B_PREP,
   K_B_FINAL,
@@ -205,20 +202,16 @@ cudaError_t launch_batch_reset(const BatchField* bf, int n, int need_gt, cudaStr
 // range; the CTA ending a field's last item derives VR, eb_abs, minexp
 cudaError_t launch_batch_range(const BatchField* bf, const BatchItem* items, int nitems, int ctas,
                                cudaStream_t s);
-// sampled blocks of d-dimensional fields: SZ residuals and ZFP
-// coefficients stored (no dependence on the error bound)
+// sampled blocks of d-dimensional fields (ZFP estimate, stored SZ
+// residuals); the CTA ending a field's last item derives delta
 cudaError_t launch_batch_blocks(const BatchField* bf, const BatchItem* items, int nitems, int d,
                                 int ctas, cudaStream_t s);
-// ZFP estimate from the stored coefficients; the CTA ending a field's last
-// item derives delta
-cudaError_t launch_batch_zfp(const BatchField* bf, const BatchItem* items, int nitems, int ctas,
-                             cudaStream_t s);
 // SZ histogram of the stored residuals
 cudaError_t launch_batch_sz_hist(const BatchField* bf, const BatchItem* items, int nitems, int ctas,
                                  cudaStream_t s);
 // resident CTAs of the item-based passes
 // (blocks_ctas: one count per dimensionality 1..3)
-void batch_occupancy(int num_sms, int* range_ctas, int* blocks_ctas, int* zfp_ctas, int* sz_ctas);
+void batch_occupancy(int num_sms, int* range_ctas, int* blocks_ctas, int* sz_ctas);
 cudaError_t launch_batch_code_prep(const BatchField* bf, int n, cudaStream_t s);
 // Huffman cost, entropy and finish of every field; result records and
 // statuses gathered into res[n] and status[n]

@@ -139,14 +139,14 @@ def test_work_split_and_graph_replay_change_nothing(R, ctx, dev_fields, singles,
 
 def test_replay_launch_count(R, ctx, dev_fields):
     """reset, range, one sampled-blocks launch per dimensionality present,
-    ZFP estimate, SZ histogram, code prep, final."""
+    SZ histogram, code prep, final."""
     ps = _params(R)
     for _ in range(2):
         ctx.select_batch(dev_fields, ps)
     n0 = ctx.launch_count()
     ctx.select_batch(dev_fields, ps)
     dims = {x.dim() for x in dev_fields}
-    assert ctx.launch_count() - n0 == 6 + len(dims)
+    assert ctx.launch_count() - n0 == 5 + len(dims)
 
 
 def test_batch_truth_equals_evaluate(R, ctx, dev_fields):
