@@ -19,7 +19,7 @@ using namespace rdk;
 namespace {
 
 const char* kKernelNames[K_COUNT] = {
-    "reset", "range", "prepare", "zfp_pass", "delta", "sz_est", "sz_pass",
+    "reset", "range", "zfp_pass", "delta", "sz_est", "sz_pass",
     "code_prep", "huffman", "finish", "zfp_inspect", "sz_inspect",
     "batch_reset", "batch_range", "batch_blocks", "batch_sz_hist", "batch_code_prep",
     "batch_final", "batch_truth"};
@@ -368,14 +368,18 @@ int issue(rd_context* c, const CallKey& k, const Geometry& g, cudaStream_t s) {
   int rc;
 
   if ((rc = launch(c, K_RESET, s, [&] { return launch_reset(ws, s); }))) return rc;
-  if ((rc = launch(c, K_RANGE, s, [&] { return launch_range(f, ws, c->range_ctas, s); }))) return rc;
-  if ((rc = launch(c, K_PREPARE, s, [&] { return launch_prepare(p, ws, s); }))) return rc;
-  if (passes & (P_ZFP_EST | P_ZFP_GT)) {
+  if ((rc = launch(c, K_RANGE, s, [&] { return launch_range(f, p, ws, c->range_ctas, s); }))) return rc;
+  // delta: by the last CTA of the ZFP pass when there is one, else its own launch
+  const bool need_delta = need_quant || (passes & P_ZFP_EST);
+  const DeltaArgs da{need_delta ? 1 : 0, delta_mode, delta_arg, need_quant ? 1 : 0, need_gt ? 1 : 0,
+                     ncoeff, g.npoints_sampled};
+  const bool zfp = passes & (P_ZFP_EST | P_ZFP_GT);
+  if (zfp) {
     int zp = passes & (P_ZFP_EST | P_ZFP_GT);
-    if ((rc = launch(c, K_ZFP, s, [&] { return launch_zfp(f, p, zp, ws, c->zfp_ctas[d], s, &zfp_parts); })))
+    if ((rc = launch(c, K_ZFP, s, [&] { return launch_zfp(f, p, zp, da, ws, c->zfp_ctas[d], s, &zfp_parts); })))
       return rc;
   }
-  if (need_quant || (passes & P_ZFP_EST)) {
+  if (need_delta && !zfp) {
     if ((rc = launch(c, K_DELTA, s, [&] {
            return launch_delta(p, ws, delta_mode, delta_arg, need_quant ? 1 : 0, need_gt ? 1 : 0,
                                ncoeff, g.npoints_sampled, s);
@@ -742,7 +746,7 @@ int issue_batch(rd_context* c, BatchPlan* b, cudaStream_t s) {
       const int d = f.d;
       int zparts = 0, sparts = 0;
       if ((rc = launch(c, K_ZFP, s, [&] {
-             return launch_zfp(f, p, P_ZFP_GT, ws, c->zfp_ctas[d], s, &zparts);
+             return launch_zfp(f, p, P_ZFP_GT, DeltaArgs{}, ws, c->zfp_ctas[d], s, &zparts);
            })))
         return rc;
       if ((rc = launch(c, K_SZ_GT, s, [&] {

@@ -127,7 +127,6 @@ struct LaunchCfg {
 enum KernelId {
   K_RESET = 0,
   K_RANGE,
-  K_PREPARE,
   K_ZFP,
   K_DELTA,
   K_SZ_EST,
@@ -157,13 +156,24 @@ enum PassFlags : int {
 
 enum DeltaMode { DELTA_FROM_MSE = 0, DELTA_EXPLICIT = 1, DELTA_FROM_EB_SZ = 2 };
 
+// The bin-width step (delta_warp) that the last CTA of the ZFP pass runs
+// when on is set, with the arguments of a separate k_delta launch.
+struct DeltaArgs {
+  int on, mode;
+  double arg;
+  int need_quant, need_gt;
+  unsigned long long ncoeff, npoints;
+};
+
 // ---- launchers (each returns the cudaError_t of the launch) ----
 // the table v log2 v (v < 2^16) of the entropy sums, kNsym doubles (once)
 cudaError_t launch_init_tables(double* xlogx, cudaStream_t s);
 cudaError_t launch_reset(Workspace* ws, cudaStream_t s);
-cudaError_t launch_range(const FieldDev& f, Workspace* ws, int ctas, cudaStream_t s);
-cudaError_t launch_prepare(const ParamsDev& p, Workspace* ws, cudaStream_t s);
-cudaError_t launch_zfp(const FieldDev& f, const ParamsDev& p, int passes,
+// value range; the CTA that ends last derives VR, eb_abs and minexp
+cudaError_t launch_range(const FieldDev& f, const ParamsDev& p, Workspace* ws, int ctas,
+                         cudaStream_t s);
+// ZFP pass; with da.on, its last CTA derives delta
+cudaError_t launch_zfp(const FieldDev& f, const ParamsDev& p, int passes, const DeltaArgs& da,
                        Workspace* ws, int ctas, cudaStream_t s, int* grid_used);
 cudaError_t launch_delta(const ParamsDev& p, Workspace* ws, int mode, double arg,
                          int need_quant, int need_gt, unsigned long long ncoeff,

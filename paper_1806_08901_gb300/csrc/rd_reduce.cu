@@ -78,25 +78,31 @@ cudaError_t launch_reset(Workspace* ws, cudaStream_t s) {
 // Value range: min / max over every value, with a non-finite test.  Rows are
 // read as float4 where the pointer allows it.
 // ---------------------------------------------------------------------------
+// The CTA that ends last (a counter, fenced on both sides) derives VR,
+// eb_abs and minexp (Algorithm 1 line 2).
 __global__ void __launch_bounds__(512) k_range(const float* __restrict__ x, long long n,
-                                               Workspace* ws) {
+                                               ParamsDev p, Workspace* ws) {
+  __shared__ int s_last;
   RangeAcc acc;
   range_span(x, 0, n, (long long)blockIdx.x * blockDim.x + threadIdx.x,
              (long long)gridDim.x * blockDim.x, acc);
   range_commit(acc, ws);
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&ws->sc.done[0], 1u) == gridDim.x - 1u;
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    __threadfence();
+    prepare_field(p, ws);
+  }
 }
 
-cudaError_t launch_range(const FieldDev& f, Workspace* ws, int ctas, cudaStream_t s) {
+cudaError_t launch_range(const FieldDev& f, const ParamsDev& p, Workspace* ws, int ctas,
+                         cudaStream_t s) {
   long long want = (f.N / 4 + 511) / 512;
   int g = (int)(want < ctas ? (want < 1 ? 1 : want) : ctas);
-  k_range<<<g, 512, 0, s>>>(f.x, f.N, ws);
-  return cudaGetLastError();
-}
-
-__global__ void k_prepare(ParamsDev p, Workspace* ws) { prepare_field(p, ws); }
-
-cudaError_t launch_prepare(const ParamsDev& p, Workspace* ws, cudaStream_t s) {
-  k_prepare<<<1, 1, 0, s>>>(p, ws);
+  k_range<<<g, 512, 0, s>>>(f.x, f.N, p, ws);
   return cudaGetLastError();
 }
 

@@ -175,10 +175,9 @@ extern "C" int32_t rd_select_static(const rd_field* fld, const rd_params* prm, r
   // the same launch sequence as rd_select, on the static scratch; the reset
   // kernel clears accumulators, histograms and result records first
   cudaError_t e = launch_reset(ws, s);
-  if (e == cudaSuccess) e = launch_range(f, ws, slot->range_ctas, s);
-  if (e == cudaSuccess) e = launch_prepare(p, ws, s);
-  if (e == cudaSuccess) e = launch_zfp(f, p, P_ZFP_EST, ws, slot->zfp_ctas[d], s, &zparts);
-  if (e == cudaSuccess) e = launch_delta(p, ws, DELTA_FROM_MSE, 0.0, 1, 0, ncoeff, npts, s);
+  const DeltaArgs da{1, DELTA_FROM_MSE, 0.0, 1, 0, ncoeff, npts};
+  if (e == cudaSuccess) e = launch_range(f, p, ws, slot->range_ctas, s);
+  if (e == cudaSuccess) e = launch_zfp(f, p, P_ZFP_EST, da, ws, slot->zfp_ctas[d], s, &zparts);
   if (e == cudaSuccess) e = launch_sz_est(f, p, ws, slot->sz_ctas[d], s);
   if (e == cudaSuccess) e = launch_code_stats(ws, 1, slot->xlogx, s);
   if (e == cudaSuccess) e = launch_finish(p, ws, passes, zparts, 0, f.N, npts, s);

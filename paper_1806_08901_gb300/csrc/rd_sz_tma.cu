@@ -304,12 +304,13 @@ __global__ void __launch_bounds__(MarchCfg<TX, TY, R, PZ, NST>::kThreads)
   for (; j < J; j++) {
     const int st = (int)(j % NST);
     const uint32_t parity = (uint32_t)((j / NST) & 1);
+    // every thread waits for the stage itself; a wait that runs out marks
+    // the call failed, and the CTA leaves at the barrier below (the planes
+    // it counts meanwhile do not matter: the call's results are discarded)
     if (!mbar_wait(&bars[st], parity)) {
       atomicCAS((int*)&ws->sc.status, RD_OK, RD_ERR_TIMEOUT);
       s_abort = 1;
     }
-    __syncthreads();
-    if (s_abort) break;
     if (gi == 0) {
       tile_coords(lt, x0, y0, zc0, zc1);
       const int x = x0 + tx;
@@ -340,6 +341,7 @@ __global__ void __launch_bounds__(MarchCfg<TX, TY, R, PZ, NST>::kThreads)
                                                     inv, tau, scl, Rq, s_gt, s_est, ws);
     }
     __syncthreads();  // every thread is done with this stage
+    if (s_abort) break;  // copies j .. j + NST - 1 may still be in flight
     if (tid == 0 && j + NST < J) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue(j + NST);
@@ -413,10 +415,12 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 3D fields: 64 x 16 tiles, 4 rows per thread, one plane per step.
+// 3D fields: 64 x 16 tiles, 4 rows per thread, two planes per step, three
+// steps in flight (one barrier per step).
 // 2D fields (walked as rows x 1 x cols): 128-column tiles, 16 rows per step
 // (a tensor box spans at most 256 elements per axis).
-using Cfg3 = MarchCfg<64, 16, 4, 1, 4>;
+constexpr int k3TX = 64, k3TY = 16, k3R = 4, k3PZ = 2, k3NST = 3;
+using Cfg3 = MarchCfg<k3TX, k3TY, k3R, k3PZ, k3NST>;
 using Cfg2 = MarchCfg<128, 1, 1, 16, 4>;
 
 template <int TX, int TY, int R, int PZ, int NST, bool EST>
@@ -427,8 +431,8 @@ static cudaError_t set_smem() {
 }
 
 cudaError_t prepare_sz_march() {
-  cudaError_t e = set_smem<64, 16, 4, 1, 4, true>();
-  if (e == cudaSuccess) e = set_smem<64, 16, 4, 1, 4, false>();
+  cudaError_t e = set_smem<k3TX, k3TY, k3R, k3PZ, k3NST, true>();
+  if (e == cudaSuccess) e = set_smem<k3TX, k3TY, k3R, k3PZ, k3NST, false>();
   if (e == cudaSuccess) e = set_smem<128, 1, 1, 16, 4, true>();
   if (e == cudaSuccess) e = set_smem<128, 1, 1, 16, 4, false>();
   return e;
@@ -463,7 +467,7 @@ cudaError_t launch_sz_march(const FieldDev& f, const ParamsDev& p, int with_est,
   if (f.d == 3) {
     g.Z = f.n[0]; g.Y = f.n[1]; g.X = f.n[2];
     g.sZ = f.s[0]; g.sY = f.s[1]; g.sX = f.s[2];
-    TX = 64; TY = 16; PZ = 1;
+    TX = k3TX; TY = k3TY; PZ = k3PZ;
   } else {
     g.Z = f.n[0]; g.Y = 1; g.X = f.n[1];
     g.sZ = f.s[0]; g.sY = 1; g.sX = f.s[1];
@@ -498,7 +502,8 @@ cudaError_t launch_sz_march(const FieldDev& f, const ParamsDev& p, int with_est,
   const long long xy = (long long)g.tilesX * g.tilesY;
   int ctas = 0;
   if (f.d == 3)
-    ctas = with_est ? march_ctas<64, 16, 4, 1, 4, true>(num_sms) : march_ctas<64, 16, 4, 1, 4, false>(num_sms);
+    ctas = with_est ? march_ctas<k3TX, k3TY, k3R, k3PZ, k3NST, true>(num_sms)
+                    : march_ctas<k3TX, k3TY, k3R, k3PZ, k3NST, false>(num_sms);
   else
     ctas = with_est ? march_ctas<128, 1, 1, 16, 4, true>(num_sms) : march_ctas<128, 1, 1, 16, 4, false>(num_sms);
   // z chunks: enough tiles to fill the resident CTAs about twice, each chunk
@@ -514,9 +519,9 @@ cudaError_t launch_sz_march(const FieldDev& f, const ParamsDev& p, int with_est,
   if (grid_used) *grid_used = grid;
   if (f.d == 3) {
     if (with_est)
-      k_sz_march<64, 16, 4, 1, 4, true><<<grid, Cfg3::kThreads, Cfg3::kSmem, s>>>(map, g, p, ws);
+      k_sz_march<k3TX, k3TY, k3R, k3PZ, k3NST, true><<<grid, Cfg3::kThreads, Cfg3::kSmem, s>>>(map, g, p, ws);
     else
-      k_sz_march<64, 16, 4, 1, 4, false><<<grid, Cfg3::kThreads, Cfg3::kSmem, s>>>(map, g, p, ws);
+      k_sz_march<k3TX, k3TY, k3R, k3PZ, k3NST, false><<<grid, Cfg3::kThreads, Cfg3::kSmem, s>>>(map, g, p, ws);
   } else {
     if (with_est)
       k_sz_march<128, 1, 1, 16, 4, true><<<grid, Cfg2::kThreads, Cfg2::kSmem, s>>>(map, g, p, ws);

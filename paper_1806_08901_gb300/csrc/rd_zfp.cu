@@ -10,12 +10,14 @@
 //     truncation, inverse transform, reconstruction, SSE and max error.
 #include <stdint.h>
 
+#include "rd_delta.cuh"
 #include "rd_zfp_dev.cuh"
 
 namespace rdk {
 
 template <int D, bool GT, bool EST>
-__global__ void __launch_bounds__(kZfpThreads) k_zfp(FieldDev f, ParamsDev p, Workspace* ws) {
+__global__ void __launch_bounds__(kZfpThreads) k_zfp(FieldDev f, ParamsDev p, DeltaArgs da,
+                                                      Workspace* ws) {
   constexpr int NB = 1 << (2 * D);
   __shared__ unsigned long long s_lo[kMseBins], s_hi[kMseBins];
   __shared__ unsigned long long s_acc[2];
@@ -161,31 +163,46 @@ __global__ void __launch_bounds__(kZfpThreads) k_zfp(FieldDev f, ParamsDev p, Wo
     for (int i = threadIdx.x; i < kMseBins; i += blockDim.x)
       if (s_lo[i] | s_hi[i]) atomic_add_u128(&ws->sc.mse_lo[i], &ws->sc.mse_hi[i], s_lo[i], s_hi[i]);
   }
+  if (da.on) {
+    // the CTA that ends last derives delta (Algorithm 1 line 7)
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      s_last = atomicAdd(&ws->sc.done[1], 1u) == gridDim.x - 1u;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x < 32) {
+      __threadfence();
+      delta_warp(p, ws, da.mode, da.arg, da.need_quant, da.need_gt, da.ncoeff, da.npoints);
+    }
+  }
 }
 
 template <int D>
-static cudaError_t launch_zfp_d(const FieldDev& f, const ParamsDev& p, int passes, Workspace* ws,
-                                int ctas, cudaStream_t s, int* grid_used) {
+static cudaError_t launch_zfp_d(const FieldDev& f, const ParamsDev& p, int passes,
+                                const DeltaArgs& da, Workspace* ws, int ctas, cudaStream_t s,
+                                int* grid_used) {
   const bool gt = passes & P_ZFP_GT, est = passes & P_ZFP_EST;
   long long units = gt ? f.nblocks : f.nsampled;
   long long want = (units + kZfpThreads - 1) / kZfpThreads;
   int g = (int)(want < ctas ? (want < 1 ? 1 : want) : ctas);
   if (grid_used) *grid_used = g;
   if (gt && est)
-    k_zfp<D, true, true><<<g, kZfpThreads, 0, s>>>(f, p, ws);
+    k_zfp<D, true, true><<<g, kZfpThreads, 0, s>>>(f, p, da, ws);
   else if (gt)
-    k_zfp<D, true, false><<<g, kZfpThreads, 0, s>>>(f, p, ws);
+    k_zfp<D, true, false><<<g, kZfpThreads, 0, s>>>(f, p, da, ws);
   else
-    k_zfp<D, false, true><<<g, kZfpThreads, 0, s>>>(f, p, ws);
+    k_zfp<D, false, true><<<g, kZfpThreads, 0, s>>>(f, p, da, ws);
   return cudaGetLastError();
 }
 
-cudaError_t launch_zfp(const FieldDev& f, const ParamsDev& p, int passes, Workspace* ws, int ctas,
-                       cudaStream_t s, int* grid_used) {
+cudaError_t launch_zfp(const FieldDev& f, const ParamsDev& p, int passes, const DeltaArgs& da,
+                       Workspace* ws, int ctas, cudaStream_t s, int* grid_used) {
   switch (f.d) {
-    case 1: return launch_zfp_d<1>(f, p, passes, ws, ctas, s, grid_used);
-    case 2: return launch_zfp_d<2>(f, p, passes, ws, ctas, s, grid_used);
-    default: return launch_zfp_d<3>(f, p, passes, ws, ctas, s, grid_used);
+    case 1: return launch_zfp_d<1>(f, p, passes, da, ws, ctas, s, grid_used);
+    case 2: return launch_zfp_d<2>(f, p, passes, da, ws, ctas, s, grid_used);
+    default: return launch_zfp_d<3>(f, p, passes, da, ws, ctas, s, grid_used);
   }
 }
 
