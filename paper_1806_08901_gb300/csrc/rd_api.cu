@@ -115,6 +115,7 @@ struct rd_context {
   int range_ctas = 0;
   int zfp_ctas[4] = {0, 0, 0, 0};
   int sz_ctas[4] = {0, 0, 0, 0};
+  int sz_est_ctas[4] = {0, 0, 0, 0};
   int b_range_ctas = 0, b_sz_ctas = 0;                   // resident CTAs of the batched passes
   int b_blocks_ctas[3] = {0, 0, 0};                       // sampled-blocks pass, per dimensionality
   bool profiling = false;
@@ -124,6 +125,7 @@ struct rd_context {
   long long launches = 0;
   // CUDA graphs of repeated calls
   cudaStream_t cap = nullptr;  // capture stream (the legacy stream cannot capture)
+  bool capture_repeats = true;  // capture repeated calls into CUDA graphs
   std::vector<GraphEntry> graphs;
   std::vector<CallKey> seen;
   unsigned long long tick = 0;
@@ -395,7 +397,7 @@ int issue(rd_context* c, const CallKey& k, const Geometry& g, cudaStream_t s) {
          })))
       return rc;
   } else if (passes & P_SZ_EST) {
-    if ((rc = launch(c, K_SZ_EST, s, [&] { return launch_sz_est(f, p, ws, c->sz_ctas[d], s); })))
+    if ((rc = launch(c, K_SZ_EST, s, [&] { return launch_sz_est(f, p, ws, c->sz_est_ctas[d], s); })))
       return rc;
   }
   int hist_mask = ((passes & P_SZ_EST) ? 1 : 0) | ((passes & P_SZ_GT) ? 2 : 0);
@@ -492,7 +494,7 @@ int run(rd_context* c, const rd_field* fld, const rd_params* prm, int passes, in
     bool repeat = false;
     for (const CallKey& q : c->seen)
       if (memcmp(&q, &k, sizeof(CallKey)) == 0) repeat = true;
-    if (repeat) {
+    if (repeat && c->capture_repeats) {
       ent = capture_graph(c, k, g);
     } else {
       if (c->seen.size() >= kMaxSeen) c->seen.erase(c->seen.begin());
@@ -986,6 +988,11 @@ int batch_call(rd_context* c, const rd_field* fields, const rd_params* params, i
 
 }  // namespace
 
+// Off: every per-field call launches its kernels directly (the serving
+// slots, whose requests rarely repeat a key often enough to repay a graph
+// capture, which would land in one request's latency).
+void rdk_set_graph_capture(rd_context* c, bool on) { c->capture_repeats = on; }
+
 extern "C" {
 
 int32_t rd_context_create(int32_t device, size_t hbm_budget, rd_context** out) {
@@ -1018,6 +1025,7 @@ int32_t rd_context_create(int32_t device, size_t hbm_budget, rd_context** out) {
   }
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
   if (prepare_code_stats() != cudaSuccess || prepare_sz_march() != cudaSuccess ||
+      prepare_sz_est() != cudaSuccess ||
       launch_init_tables(c->xlogx, 0) != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess) {
     cudaFreeHost(c->out);
     cudaFree(c->xlogx);
@@ -1029,6 +1037,7 @@ int32_t rd_context_create(int32_t device, size_t hbm_budget, rd_context** out) {
   for (int d = 1; d <= 3; d++) {
     c->zfp_ctas[d] = zfp_occupancy(d, c->num_sms);
     c->sz_ctas[d] = sz_occupancy(d, c->num_sms);
+    c->sz_est_ctas[d] = sz_est_occupancy(d, c->num_sms);
   }
   batch_occupancy(c->num_sms, &c->b_range_ctas, c->b_blocks_ctas, &c->b_sz_ctas);
   *out = c;

@@ -258,19 +258,6 @@ __global__ void __launch_bounds__(kBatchBlockThreads) k_batch_blocks(const Batch
 // ---------------------------------------------------------------------------
 // SZ histogram of the stored residuals (Alg. 1 line 8), coalesced
 // ---------------------------------------------------------------------------
-// The whole alphabet in shared memory: 65536 16-bit counters, code s in
-// half s >> 15 of word s & 0x7fff (so neighbouring codes, which the runs of
-// a warp often hit together, fall in different words).  The residuals of
-// rough fields at fine bounds spread over tens of thousands of codes: a
-// partial window sent most of them to global atomics, which set the pace.
-// A counter cannot pass 65535 between flushes: an add that takes a counter
-// to kHotCount or more raises a flag, and the CTA flushes at the end of the
-// round of kRoundPoints points in progress, which adds at most kRoundPoints
-// to any counter.  Wide code distributions, whose counters stay low, flush
-// only when the field changes.
-constexpr int kPackWords = 32768;
-constexpr long long kRoundPoints = 16384;  // points between flush checks (a multiple of 4)
-constexpr uint32_t kHotCount = 65535u - (uint32_t)kRoundPoints;
 
 // Counts 64 consecutive keys of the residual list, two per lane (lane i
 // holds positions 2i and 2i+1): neighbouring points of a smooth field often
@@ -295,32 +282,11 @@ __device__ __forceinline__ void hist_add_runs(uint32_t* s_win, uint32_t ka, uint
     const int j = __ffs(later) - 1;
     next = 2 * j + (((ba >> j) & 1u) ? 0 : 1);
   }
-  auto add = [&](int sym, unsigned cnt) {
-    const int sh = (sym >> 15) << 4;
-    const uint32_t old = atomicAdd(&s_win[sym & 0x7fff], cnt << sh);
-    if (((old >> sh) & 0xffffu) + cnt >= kHotCount) *s_hot = 1;
-  };
+  auto add = [&](int sym, unsigned cnt) { packed_add(s_win, sym, cnt, s_hot); };
   if (ha && sa >= 0) add(sa, hb ? 1u : (unsigned)(next - 2 * lane));
   if (hb && sb >= 0) add(sb, (unsigned)(next - 2 * lane - 1));
 }
 
-__device__ __forceinline__ void window_flush(uint32_t* s_win, uint32_t* g_hist) {
-  __syncthreads();
-  uint4* w4 = reinterpret_cast<uint4*>(s_win);
-  for (int i = threadIdx.x; i < kPackWords / 4; i += blockDim.x) {
-    const uint4 c = w4[i];
-    if (c.x | c.y | c.z | c.w) {
-      const uint32_t cw[4] = {c.x, c.y, c.z, c.w};
-#pragma unroll
-      for (int k = 0; k < 4; k++) {
-        if (cw[k] & 0xffffu) atomicAdd(&g_hist[4 * i + k], cw[k] & 0xffffu);
-        if (cw[k] >> 16) atomicAdd(&g_hist[4 * i + k + 32768], cw[k] >> 16);
-      }
-      w4[i] = make_uint4(0u, 0u, 0u, 0u);
-    }
-  }
-  __syncthreads();
-}
 
 __global__ void __launch_bounds__(kBatchSzThreads, 1) k_batch_sz_hist(const BatchField* __restrict__ bf,
                                                                    const BatchItem* __restrict__ items,

@@ -272,6 +272,48 @@ __device__ __forceinline__ void hist_add_sorted2(uint32_t* s_win, int win_lo, in
   }
 }
 
+// A code histogram over the whole alphabet in shared memory (128 KB):
+// 65536 16-bit counters, code s in half s >> 15 of word s & 0x7fff (so
+// neighbouring codes, which a warp often hits together, fall in different
+// words).  The residuals of rough fields at fine bounds spread over tens of
+// thousands of codes: a partial window sent most of them to global atomics,
+// which set the pace.  A counter cannot pass 65535 between flushes: an add
+// that takes a counter to kHotCount or more raises a flag, and the CTA
+// flushes at the end of the round of at most kRoundPoints points in
+// progress.  Wide code distributions, whose counters stay low, flush only
+// when the CTA is done with the field.
+constexpr int kPackWords = 32768;
+constexpr long long kRoundPoints = 16384;  // points between flush checks (a multiple of 4)
+constexpr uint32_t kHotCount = 65535u - (uint32_t)kRoundPoints;
+
+// Adds cnt to the counter of code sym; raises *s_hot when it reaches
+// kHotCount.
+__device__ __forceinline__ void packed_add(uint32_t* s_win, int sym, unsigned cnt, int* s_hot) {
+  const int sh = (sym >> 15) << 4;
+  const uint32_t old = atomicAdd(&s_win[sym & 0x7fff], cnt << sh);
+  if (((old >> sh) & 0xffffu) + cnt >= kHotCount) *s_hot = 1;
+}
+
+// Adds the window's counters to the global histogram and clears them; every
+// thread of the CTA calls.
+__device__ __forceinline__ void window_flush(uint32_t* s_win, uint32_t* g_hist) {
+  __syncthreads();
+  uint4* w4 = reinterpret_cast<uint4*>(s_win);
+  for (int i = threadIdx.x; i < kPackWords / 4; i += blockDim.x) {
+    const uint4 c = w4[i];
+    if (c.x | c.y | c.z | c.w) {
+      const uint32_t cw[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        if (cw[k] & 0xffffu) atomicAdd(&g_hist[4 * i + k], cw[k] & 0xffffu);
+        if (cw[k] >> 16) atomicAdd(&g_hist[4 * i + k + 32768], cw[k] >> 16);
+      }
+      w4[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+  }
+  __syncthreads();
+}
+
 // Per-thread register counters of the 2H+1 symbols around the centre, where
 // nearly every code of a smooth field falls: counting them costs a few
 // predicated adds and no atomics (contended shared-memory atomics on a few
@@ -300,6 +342,18 @@ struct HotBins {
       atomicAdd(&s_win[wi], 1u);
     else
       atomicAdd(&g_hist[sym], 1u);
+  }
+  // add the warp's counters to the global histogram; every lane of the warp
+  // calls
+  __device__ __forceinline__ void flush_global(uint32_t* g_hist) {
+#pragma unroll
+    for (int k = 0; k < 2 * H + 1; k++) {
+      uint32_t v = c[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if ((threadIdx.x & 31) == 0 && v) atomicAdd(&g_hist[kCenter - H + k], v);
+    }
+    clear();
   }
   // add the warp's counters to the window; every lane of the warp calls
   __device__ __forceinline__ void flush_warp(uint32_t* s_win, int win_lo) {

@@ -178,8 +178,12 @@ cudaError_t launch_zfp(const FieldDev& f, const ParamsDev& p, int passes, const 
 cudaError_t launch_delta(const ParamsDev& p, Workspace* ws, int mode, double arg,
                          int need_quant, int need_gt, unsigned long long ncoeff,
                          unsigned long long npoints, cudaStream_t s);
+// SZ estimate; ctas from sz_est_occupancy, prepare_sz_est() once per
+// device first (128 KB of dynamic shared memory per CTA)
 cudaError_t launch_sz_est(const FieldDev& f, const ParamsDev& p, Workspace* ws,
                           int ctas, cudaStream_t s);
+cudaError_t prepare_sz_est();
+int sz_est_occupancy(int d, int num_sms);
 cudaError_t launch_sz_gt(const FieldDev& f, const ParamsDev& p, int with_est,
                          Workspace* ws, int ctas, cudaStream_t s, int* grid_used);
 // Entropy partials and count-of-counts (launch_code_prep), then the Huffman

@@ -32,6 +32,8 @@
 #include "rd_server_policy.h"
 #include "rdsel.h"
 
+void rdk_set_graph_capture(rd_context* c, bool on);  // rd_api.cu
+
 namespace {
 
 using Clock = std::chrono::steady_clock;
@@ -76,6 +78,9 @@ void serve(rd_server* s) {
   cudaStream_t st = nullptr;
   const bool ready = rd_context_create(s->device, 0, &ctx) == RD_OK &&
                      cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
+  // a graph capture on a key's second request would land in that request's
+  // latency; slots launch directly
+  if (ctx) rdk_set_graph_capture(ctx, false);
   std::unique_lock<std::mutex> lk(s->mu);
   if (!ready) s->worker_errors++;
   for (;;) {

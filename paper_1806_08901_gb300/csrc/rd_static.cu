@@ -45,6 +45,7 @@ struct DeviceSlot {
   int range_ctas;
   int zfp_ctas[4];
   int sz_ctas[4];
+  int sz_est_ctas[4];
 };
 
 std::mutex g_mu;
@@ -64,7 +65,7 @@ int setup_device(int dev, DeviceSlot** out) {
     if (cudaGetSymbolAddress(&tx, g_xlogx) != cudaSuccess || !tx) return RD_ERR_CUDA;
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return RD_ERR_CUDA;
-    if (prepare_code_stats() != cudaSuccess) return RD_ERR_CUDA;
+    if (prepare_code_stats() != cudaSuccess || prepare_sz_est() != cudaSuccess) return RD_ERR_CUDA;
     s.ws = static_cast<Workspace*>(p);
     s.xlogx = static_cast<double*>(tx);
     if (launch_init_tables(s.xlogx, 0) != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess)
@@ -73,6 +74,7 @@ int setup_device(int dev, DeviceSlot** out) {
     for (int d = 1; d <= 3; d++) {
       s.zfp_ctas[d] = zfp_occupancy(d, sms);
       s.sz_ctas[d] = sz_occupancy(d, sms);
+      s.sz_est_ctas[d] = sz_est_occupancy(d, sms);
     }
     s.ready = true;
   }
@@ -178,7 +180,7 @@ extern "C" int32_t rd_select_static(const rd_field* fld, const rd_params* prm, r
   const DeltaArgs da{1, DELTA_FROM_MSE, 0.0, 1, 0, ncoeff, npts};
   if (e == cudaSuccess) e = launch_range(f, p, ws, slot->range_ctas, s);
   if (e == cudaSuccess) e = launch_zfp(f, p, P_ZFP_EST, da, ws, slot->zfp_ctas[d], s, &zparts);
-  if (e == cudaSuccess) e = launch_sz_est(f, p, ws, slot->sz_ctas[d], s);
+  if (e == cudaSuccess) e = launch_sz_est(f, p, ws, slot->sz_est_ctas[d], s);
   if (e == cudaSuccess) e = launch_code_stats(ws, 1, slot->xlogx, s);
   if (e == cudaSuccess) e = launch_finish(p, ws, passes, zparts, 0, f.N, npts, s);
   rd_result r;

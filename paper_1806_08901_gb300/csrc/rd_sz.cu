@@ -15,25 +15,46 @@
 
 namespace rdk {
 
-// Estimator: one thread per sampled block (sz_est_block), grid-strided.
+// Estimator: one thread per sampled block (sz_est_block), grid-strided, one
+// 1024-thread CTA per SM with the whole-alphabet 16-bit window (codes of
+// fine bounds spread over tens of thousands of bins); the 2H+1 codes around
+// the centre are counted in registers.  A round is one plane of the CTA's
+// 3D blocks, or one of its 2D / 1D blocks: at most kRoundPoints points.
+constexpr int kSzEstThreads = 1024;
+static_assert(kSzEstThreads * 16 <= kRoundPoints, "a round adds at most kRoundPoints");
+
 template <int D>
-__global__ void __launch_bounds__(kSzThreads) k_sz_est(FieldDev f, ParamsDev p, Workspace* ws) {
-  __shared__ uint32_t s_win[kHistWin];
+__global__ void __launch_bounds__(kSzEstThreads, 1) k_sz_est(FieldDev f, ParamsDev p, Workspace* ws) {
+  extern __shared__ uint32_t s_win[];  // kPackWords words of two counters
+  __shared__ int s_hot;
   const Scalars& sc = ws->sc;
-  if (sc.status != RD_OK || sc.constant) return;
-  for (int i = threadIdx.x; i < kHistWin; i += blockDim.x) s_win[i] = 0u;
+  if (sc.status != RD_OK || sc.constant) return;  // uniform over the grid
+  for (int i = threadIdx.x; i < kPackWords; i += blockDim.x) s_win[i] = 0u;
+  if (threadIdx.x == 0) s_hot = 0;
   __syncthreads();
   const float inv = sc.inv;
+  uint32_t* g_hist = ws->hist[0];
   HotBins<2> hot;
   hot.clear();
+  auto add = [&](int sym) {
+    if (!hot.take(sym - kCenter)) packed_add(s_win, sym, 1u, &s_hot);
+  };
+  auto round_end = [&]() {
+    __syncthreads();
+    if (s_hot) {  // uniform after the barrier
+      window_flush(s_win, g_hist);
+      if (threadIdx.x == 0) s_hot = 0;
+      __syncthreads();
+    }
+  };
   for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < f.nsampled;
-       b0 += (long long)gridDim.x * blockDim.x) {
+       b0 += (long long)gridDim.x * blockDim.x) {  // uniform trip count over the CTA
     const long long sb = b0 + threadIdx.x;
-    sz_est_block<D>(f, sb, sb < f.nsampled, inv, p.R, s_win, ws->hist[0], hot);
+    sz_est_block<D>(f, sb, sb < f.nsampled, inv, p.R, add, round_end);
+    if (D < 3) round_end();
   }
-  hot.flush_warp(s_win, kHistWinLo);
-  __syncthreads();
-  hist_flush(s_win, ws->hist[0]);
+  hot.flush_global(g_hist);
+  window_flush(s_win, g_hist);
 }
 
 // ---------------------------------------------------------------------------
@@ -110,9 +131,9 @@ __global__ void __launch_bounds__(kSzThreads) k_sz_gt(FieldDev f, ParamsDev p, W
 template <int D>
 static cudaError_t launch_est_d(const FieldDev& f, const ParamsDev& p, Workspace* ws, int ctas,
                                 cudaStream_t s) {
-  long long want = (f.nsampled + kSzThreads - 1) / kSzThreads;
+  long long want = (f.nsampled + kSzEstThreads - 1) / kSzEstThreads;
   int g = (int)(want < ctas ? (want < 1 ? 1 : want) : ctas);
-  k_sz_est<D><<<g, kSzThreads, 0, s>>>(f, p, ws);
+  k_sz_est<D><<<g, kSzEstThreads, kPackWords * sizeof(uint32_t), s>>>(f, p, ws);
   return cudaGetLastError();
 }
 
@@ -145,6 +166,29 @@ cudaError_t launch_sz_gt(const FieldDev& f, const ParamsDev& p, int with_est, Wo
     case 2: return launch_gt_d<2>(f, p, with_est, ws, ctas, s, grid_used);
     default: return launch_gt_d<3>(f, p, with_est, ws, ctas, s, grid_used);
   }
+}
+
+cudaError_t prepare_sz_est() {
+  const int smem = kPackWords * (int)sizeof(uint32_t);
+  cudaError_t e = cudaFuncSetAttribute(k_sz_est<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sz_est<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sz_est<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return e;
+}
+
+int sz_est_occupancy(int d, int num_sms) {
+  int per = 0;
+  const void* fn = d == 1 ? (const void*)k_sz_est<1> : d == 2 ? (const void*)k_sz_est<2> : (const void*)k_sz_est<3>;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kSzEstThreads,
+                                                    kPackWords * sizeof(uint32_t)) != cudaSuccess ||
+      per < 1) {
+    cudaGetLastError();
+    per = 1;
+  }
+  long long g = (long long)per * num_sms;
+  return (int)(g > kMaxGrid ? kMaxGrid : g);
 }
 
 int sz_occupancy(int d, int num_sms) {

@@ -134,10 +134,11 @@ __device__ __forceinline__ void sampled_block_origin(const FieldDev& f, long lon
   }
 }
 
-template <int D>
+// add(sym) counts one code; for 3D blocks round_end() runs after each of
+// the four planes, in every thread of the CTA (active or not).
+template <int D, class Add, class RoundEnd>
 __device__ __forceinline__ void sz_est_block(const FieldDev& f, long long sb, bool active, float inv,
-                                             int R, uint32_t* s_win, uint32_t* g_hist,
-                                             HotBins<2>& hot) {
+                                             int R, Add&& add, RoundEnd&& round_end) {
   int o[3] = {0, 0, 0};
   if (active) sampled_block_origin<D>(f, sb, o);
   if constexpr (D == 1) {
@@ -146,7 +147,7 @@ __device__ __forceinline__ void sz_est_block(const FieldDev& f, long long sb, bo
 #pragma unroll
     for (int k = 0; k < 4; k++) {
       const bool ok = active && o[0] + k < f.n[0];
-      if (ok) hot.add(est_symbol(__fsub_rn(v[k + 1], v[k]), inv, R), s_win, kHistWinLo, kHistWin, g_hist);
+      if (ok) add(est_symbol(__fsub_rn(v[k + 1], v[k]), inv, R));
     }
   } else {
     const int ny = f.n[D - 2], nx = f.n[D - 1];
@@ -183,11 +184,12 @@ __device__ __forceinline__ void sz_est_block(const FieldDev& f, long long sb, bo
         const int j = t >> 2, k = t & 3;
         const bool ok = z_ok && y0 + j < ny && x0 + k < nx;
         const float r = D == 3 ? __fsub_rn(cur[t], prev[t]) : cur[t];
-        if (ok) hot.add(est_symbol(r, inv, R), s_win, kHistWinLo, kHistWin, g_hist);
+        if (ok) add(est_symbol(r, inv, R));
       }
       if (D == 3) {
 #pragma unroll
         for (int t = 0; t < 16; t++) prev[t] = cur[t];
+        round_end();
       }
     }
   }
