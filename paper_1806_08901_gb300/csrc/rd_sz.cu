@@ -16,10 +16,11 @@
 namespace rdk {
 
 // Estimator: one thread per sampled block (sz_est_block), grid-strided, one
-// 1024-thread CTA per SM with the whole-alphabet 16-bit window (codes of
-// fine bounds spread over tens of thousands of bins); the 2H+1 codes around
-// the centre are counted in registers.  A round is one plane of the CTA's
-// 3D blocks, or one of its 2D / 1D blocks: at most kRoundPoints points.
+// CTA of up to 1024 threads per SM with the whole-alphabet 16-bit window
+// (codes of fine bounds spread over tens of thousands of bins); the 2H+1
+// codes around the centre are counted in registers.  A round is one plane
+// of the CTA's 3D blocks, or one of its 2D / 1D blocks: at most
+// kRoundPoints points.
 constexpr int kSzEstThreads = 1024;
 static_assert(kSzEstThreads * 16 <= kRoundPoints, "a round adds at most kRoundPoints");
 
@@ -131,9 +132,14 @@ __global__ void __launch_bounds__(kSzThreads) k_sz_gt(FieldDev f, ParamsDev p, W
 template <int D>
 static cudaError_t launch_est_d(const FieldDev& f, const ParamsDev& p, Workspace* ws, int ctas,
                                 cudaStream_t s) {
-  long long want = (f.nsampled + kSzEstThreads - 1) / kSzEstThreads;
+  // one CTA per SM (ctas); fewer threads per CTA when the field has fewer
+  // sampled blocks than the CTAs' threads, so that every SM takes a share
+  long long per = (f.nsampled + ctas - 1) / ctas;
+  per = (per + 31) / 32 * 32;
+  const int threads = (int)(per < 128 ? 128 : per > kSzEstThreads ? kSzEstThreads : per);
+  long long want = (f.nsampled + threads - 1) / threads;
   int g = (int)(want < ctas ? (want < 1 ? 1 : want) : ctas);
-  k_sz_est<D><<<g, kSzEstThreads, kPackWords * sizeof(uint32_t), s>>>(f, p, ws);
+  k_sz_est<D><<<g, threads, kPackWords * sizeof(uint32_t), s>>>(f, p, ws);
   return cudaGetLastError();
 }
 
