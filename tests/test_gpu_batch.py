@@ -193,3 +193,19 @@ def test_host_fields_are_rejected(R, ctx):
 def test_single_field_batch(R, ctx, dev_fields, singles):
     res, _, st = ctx.select_batch([dev_fields[4]], _params(R)[4])
     assert st == [0] and res[0] == singles[4]
+
+
+def test_hot_code_batch_equals_per_field(R, ctx):
+    """The batched residual histogram of a field whose codes are nearly all
+    one value (a 16M-point sawtooth): the 16-bit window flushes before a
+    counter wraps, and the record equals rd_select's and the oracle's."""
+    n = 1 << 24
+    x = (3 * (np.arange(n, dtype=np.int64) % 1000)).astype(np.float32)
+    xd = torch.from_numpy(x).cuda()
+    p = R.params(eb=1e-3, r_sp=1.0)
+    single = ctx.select(xd, p)
+    res, _, st = ctx.select_batch([xd, xd], [p, p])
+    assert st == [0, 0] and res[0] == single and res[1] == single
+    o = O.select(x, O.params(eb=1e-3, r_sp=1.0))
+    for k in EXACT_RESULT:
+        assert single[k] == o[k], k

@@ -378,6 +378,24 @@ def test_huffman_forms_for_wide_alphabets(R, ctx, form):
     assert _rel(gs["br_sz"], os_["br_sz"]) <= REL_ENTROPY
 
 
+def test_hot_code_flushes_histogram_window(R, ctx):
+    """A 16M-point sawtooth whose Lorenzo residuals are nearly all one code
+    (3 at bin width 1): each CTA counts far more than 2^16 of that code, so
+    the 16-bit shared counters of the estimate histogram must be flushed
+    before they wrap.  Histogram and Huffman cost equal the oracle's."""
+    n = 1 << 24
+    x = (3 * (np.arange(n, dtype=np.int64) % 1000)).astype(np.float32)
+    op = O.params(eb=1e-3, r_sp=1.0)
+    xd = torch.from_numpy(x).cuda()
+    gs = ctx.estimate_sz(xd, _gp(R, op), delta=1.0)
+    os_ = O.estimate_sz(x, op, delta=1.0, want_hist=True)
+    h = os_["hist"]
+    assert h.max() > 1 << 23
+    assert np.array_equal(ctx.histograms()[0], h)
+    for k in ("sz_ns", "sz_huff_bits", "sz_nesc", "sz_nsym", "br_sz_huff"):
+        assert gs[k] == os_[k], k
+
+
 # ---------------------------------------------------------------------------
 # Full-size Hurricane-shaped field (100 x 500 x 500), as the benchmark runs it
 # ---------------------------------------------------------------------------
