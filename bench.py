@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--batch-subset", default="all", choices=["all", "small"],
                     help="small: 20 ATM + 2 Hurricane + 1 512^3 fields (1.3 GB), for profiling")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--no-curve", action="store_true",
+                    help="skip the rate-distortion sweep (error bounds 1e-2 .. 1e-6)")
     ap.add_argument("--serve-population", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-rates", default="100,500,2000")
@@ -259,6 +261,43 @@ def bench_snapshot(R, ctx, stream, steps: int, peak: float, peak_kind: str, subs
 
 
 SERVE_WORKLOAD = "serving_poisson_2d512-1800x3600_3d64-512cubed_f32"
+
+
+CURVE_EBS = (1e-2, 1e-3, 1e-4, 1e-5, 1e-6)
+
+
+def bench_rd_curve(R, ctx, x, stream, reps: int = 5):
+    """The rate-distortion sweep of the benchmark field over the error
+    bounds 1e-2 .. 1e-6 (rd_rd_curve: Algorithm 1 and its truth at each
+    bound, and the selection based on error bound), timed with CUDA events
+    over whole sweeps; the choices per bound."""
+    import torch
+
+    p = R.params(eb=EB_REL, r_sp=R_SP)
+    pts = ctx.rd_curve(x, p, CURVE_EBS, stream)  # warm-up
+    ms = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pts = ctx.rd_curve(x, p, CURVE_EBS, stream)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    points = []
+    for pt in pts:
+        e, t, t2 = pt["est"], pt["truth"], pt["truth_eb"]
+        points.append({"eb_rel": pt["eb"], "selection": e["selection"], "optimum_gt": t["best_gt"],
+                       "selection_eb": pt["selection_eb"], "best_eb_gt": pt["best_eb_gt"],
+                       "br_sz": e["br_sz"], "br_zfp": e["br_zfp"], "psnr_zfp": e["psnr_zfp"],
+                       "br_sz_gt": t["br_sz_gt"], "br_zfp_gt": t["br_zfp_gt"],
+                       "psnr_sz_gt": t["psnr_sz_gt"], "psnr_zfp_gt": t["psnr_zfp_gt"],
+                       "br_sz_eb": pt["est_eb"]["br_sz"], "br_sz_eb_gt": t2["br_sz_gt"],
+                       "psnr_sz_eb_gt": t2["psnr_sz_gt"], "psnr_zfp_eb_gt": t2["psnr_zfp_gt"]})
+    return {"workload": WORKLOAD, "eb_rel": list(CURVE_EBS), "r_sp": R_SP,
+            "ms_per_sweep": statistics.median(ms),
+            "calls_per_bound": "rd_evaluate + rd_estimate_sz(2 eb_abs) + rd_ground_truth(eb_abs)",
+            "points": points}
 
 
 def bench_serving(R, population: int, n_req: int, rates, budget: int = 120 << 30):
@@ -523,6 +562,8 @@ def main():
                    "br_sz_gt": truth_ref["br_sz_gt"], "br_zfp_gt": truth_ref["br_zfp_gt"],
                    "psnr_zfp": est_ref["psnr_zfp"], "psnr_zfp_gt": truth_ref["psnr_zfp_gt"]},
     }
+    if not args.no_curve and world == 1:
+        line["rd_curve"] = bench_rd_curve(R, ctx, x, stream)
     if not args.no_batch and world == 1:
         line["batched"] = bench_snapshot(R, ctx, stream, args.batch_steps, peak, peak_kind,
                                          args.batch_subset)

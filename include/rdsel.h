@@ -193,6 +193,39 @@ int32_t rd_evaluate(rd_context* ctx, const rd_field* field,
 int32_t rd_select_static(const rd_field* field, const rd_params* params,
                          rd_result* out, void* stream);
 
+/* ---- rate-distortion sweep ------------------------------------------- */
+
+/* One error bound of a sweep (rd_rd_curve). */
+typedef struct {
+  double eb;            /* the bound, in params->eb_mode */
+  rd_result est;        /* Algorithm 1 at eb: selection based on rate-distortion */
+  rd_truth truth;       /* ground truth at the matched PSNR (SZ at delta/2, ZFP at
+                           eb_abs); truth.best_gt is the "optimum" choice */
+  rd_result est_eb;     /* SZ estimate at bin 2 eb_abs: both compressors at the
+                           same maximum error */
+  rd_truth truth_eb;    /* ground truth at the same maximum error (SZ and ZFP at
+                           eb_abs) */
+  int32_t selection_eb; /* selection based on error bound, from the estimates:
+                           0 = SZ iff its bit-rate (sel_rule) is below br_zfp */
+  int32_t best_eb_gt;   /* the same from the ground truth */
+} rd_rd_point;
+
+/* Rate-distortion points of one field over the bounds eb[0..n) (evaluation
+ * section, "Analysis of Adaptability between Selection Methods Based on
+ * Fixed-PSNR vs. Fixed-Maximum-Error", Fig. f9, and the "optimum bar" of
+ * Fig. f5): at each bound, rd_evaluate (Algorithm 1 and its ground truth at
+ * the matched PSNR), and the selection based on error bound that the paper
+ * compares against: SZ with bin 2 eb_abs against ZFP at eb_abs, by
+ * estimates and by ground truth (rd_estimate_sz with delta <= 0,
+ * rd_ground_truth at eb_sz = eb_abs).  params->eb is ignored; every other
+ * parameter applies to every bound.
+ *  - field as for rd_select (host fields are copied in for each call);
+ *    eb: n host doubles > 0; out: n records, written in order.
+ *  - Return: RD_OK, or the first error (out[i..] zeroed from the failing
+ *    bound on). */
+int32_t rd_rd_curve(rd_context* ctx, const rd_field* field, const rd_params* params,
+                    const double* eb, int32_t n, rd_rd_point* out, void* stream);
+
 /* ---- batched estimate ------------------------------------------------ */
 
 /* Work split of the batched estimate.  The results do not depend on it. */

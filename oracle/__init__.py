@@ -228,6 +228,31 @@ def ground_truth(x: np.ndarray, p: Params, eb_sz: float = 0.0, want_hist: bool =
     return d
 
 
+def rd_curve(x: np.ndarray, p: Params, ebs) -> list:
+    """Rate-distortion points over the bounds ebs (evaluation section,
+    "Analysis of Adaptability between Selection Methods Based on Fixed-PSNR
+    vs. Fixed-Maximum-Error", Fig. f9, and the "optimum bar" of Fig. f5).  At
+    each bound: Algorithm 1 (select) and its ground truth at the matched PSNR
+    (SZ at delta/2; best_gt is the optimum choice); and the selection based on
+    error bound that the paper compares against, both compressors at the same
+    maximum error eb_abs: SZ with bin 2 eb_abs (estimate_sz with delta 0)
+    against ZFP at eb_abs, SZ iff its bit-rate is lower, from the estimates
+    and from the ground truth at eb_sz = eb_abs."""
+    out = []
+    for eb in ebs:
+        q = Params(float(eb), p.eb_mode, p.ec_mode, p.r_sp, p.quant_radius, p.sel_rule,
+                   p.sz_offset)
+        est = select(x, q)
+        truth = ground_truth(x, q)
+        est_eb = estimate_sz(x, q, delta=0.0)
+        truth_eb = ground_truth(x, q, eb_sz=est["eb_abs"]) if est["eb_abs"] > 0.0 else None
+        br = est_eb["br_sz_huff"] if p.sel_rule == SEL_HUFFMAN else est_eb["br_sz"]
+        out.append(dict(eb=float(eb), est=est, truth=truth, est_eb=est_eb, truth_eb=truth_eb,
+                        selection_eb=0 if br < est["br_zfp"] else 1,
+                        best_eb_gt=truth_eb["best_gt"] if truth_eb is not None else 0))
+    return out
+
+
 def zfp_blocks(x: np.ndarray, eb_abs: float, want_coeffs: bool = False):
     x, shape = _field(x)
     nblk = int(np.prod([(n + 3) // 4 for n in x.shape]))

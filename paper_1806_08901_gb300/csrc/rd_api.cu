@@ -1096,6 +1096,32 @@ int32_t rd_evaluate(rd_context* c, const rd_field* f, const rd_params* p, rd_res
              stream);
 }
 
+int32_t rd_rd_curve(rd_context* c, const rd_field* f, const rd_params* p, const double* eb, int32_t n,
+                    rd_rd_point* out, void* stream) {
+  if (!c || !f || !p || !eb || !out || n < 1) return RD_ERR_INVALID_ARG;
+  memset(out, 0, sizeof(rd_rd_point) * (size_t)n);
+  for (int32_t i = 0; i < n; i++) {
+    rd_rd_point& pt = out[i];
+    pt.eb = eb[i];
+    rd_params q = *p;
+    q.eb = eb[i];
+    int32_t rc = rd_evaluate(c, f, &q, &pt.est, &pt.truth, stream);
+    if (rc == RD_OK) rc = rd_estimate_sz(c, f, &q, 0.0, &pt.est_eb, stream);
+    if (rc == RD_OK && pt.est.eb_abs > 0.0)
+      rc = rd_ground_truth(c, f, &q, pt.est.eb_abs, &pt.truth_eb, stream);
+    if (rc != RD_OK) {
+      memset(&out[i], 0, sizeof(rd_rd_point) * (size_t)(n - i));
+      return rc;
+    }
+    // same maximum error: SZ (bin 2 eb_abs) against ZFP (fixed accuracy at
+    // eb_abs); SZ iff its bit-rate is lower (ties go to ZFP, as in rd_select)
+    const double br_sz = q.sel_rule == RD_SEL_HUFFMAN ? pt.est_eb.br_sz_huff : pt.est_eb.br_sz;
+    pt.selection_eb = br_sz < pt.est.br_zfp ? 0 : 1;
+    pt.best_eb_gt = pt.truth_eb.best_gt;
+  }
+  return RD_OK;
+}
+
 int32_t rd_select_batch(rd_context* c, const rd_field* fields, const rd_params* params, int32_t n,
                         rd_result* results, rd_truth* truths, int32_t* status, void* stream) {
   if (!c || !fields || !params || !results || n < 1) return RD_ERR_INVALID_ARG;

@@ -76,6 +76,11 @@ class rd_truth(C.Structure):
     ]
 
 
+class rd_rd_point(C.Structure):
+    _fields_ = [("eb", C.c_double), ("est", rd_result), ("truth", rd_truth), ("est_eb", rd_result),
+                ("truth_eb", rd_truth), ("selection_eb", C.c_int32), ("best_eb_gt", C.c_int32)]
+
+
 class rd_batch_config(C.Structure):
     _fields_ = [("range_values", C.c_int64), ("zfp_blocks", C.c_int32), ("sz_blocks", C.c_int32),
                 ("ctas", C.c_int32), ("tuned", C.c_int32)]
@@ -111,6 +116,8 @@ _SIGNATURES = {
     "rd_select": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), _P(rd_result), C.c_void_p]),
     "rd_ground_truth": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), C.c_double,
                                     _P(rd_truth), C.c_void_p]),
+    "rd_rd_curve": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), _P(C.c_double), C.c_int32,
+                                _P(rd_rd_point), C.c_void_p]),
     "rd_evaluate": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), _P(rd_result),
                                 _P(rd_truth), C.c_void_p]),
     "rd_select_static": (C.c_int32, [_P(rd_field), _P(rd_params), _P(rd_result), C.c_void_p]),
@@ -286,6 +293,22 @@ def rd_ground_truth(ctx, field, prm: rd_params, eb_sz: float = 0.0, stream=None)
     _check(lib().rd_ground_truth(ctx, C.byref(f), C.byref(prm), float(eb_sz), C.byref(t),
                                  _stream(stream)), "rd_ground_truth")
     return _todict(t)
+
+
+def rd_rd_curve(ctx, field, prm: rd_params, ebs, stream=None) -> list:
+    """Rate-distortion points over the bounds ebs: one dict per bound with
+    eb, est, truth, est_eb, truth_eb (dicts) and selection_eb, best_eb_gt."""
+    f, keep = make_field(field)
+    n = len(ebs)
+    eb = (C.c_double * n)(*[float(e) for e in ebs])
+    out = (rd_rd_point * n)()
+    _check(lib().rd_rd_curve(ctx, C.byref(f), C.byref(prm), eb, n, out, _stream(stream)), "rd_rd_curve")
+    res = []
+    for pt in out:
+        res.append({"eb": pt.eb, "est": _todict(pt.est), "truth": _todict(pt.truth),
+                    "est_eb": _todict(pt.est_eb), "truth_eb": _todict(pt.truth_eb),
+                    "selection_eb": pt.selection_eb, "best_eb_gt": pt.best_eb_gt})
+    return res
 
 
 def rd_evaluate(ctx, field, prm: rd_params, stream=None) -> tuple:
@@ -541,6 +564,9 @@ class Context:
 
     def evaluate(self, x, p, stream=None):
         return rd_evaluate(self.h, x, p, stream)
+
+    def rd_curve(self, x, p, ebs, stream=None):
+        return rd_rd_curve(self.h, x, p, ebs, stream)
 
     def select_batch(self, fields, prms, truth=False, stream=None, check=True):
         return rd_select_batch(self.h, fields, prms, truth, stream, check)

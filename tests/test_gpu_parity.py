@@ -378,6 +378,32 @@ def test_huffman_forms_for_wide_alphabets(R, ctx, form):
     assert _rel(gs["br_sz"], os_["br_sz"]) <= REL_ENTROPY
 
 
+@pytest.mark.parametrize("name,sel_rule", [("3d_ragged", 0), ("2d_ragged", 1), ("3d_noise", 0)])
+def test_rd_curve_matches_oracle(R, ctx, name, sel_rule):
+    """The rate-distortion sweep: Algorithm 1 and its truth at each bound,
+    and the selection based on error bound (both compressors at the same
+    maximum error), by estimates and by ground truth."""
+    x = FIELDS[name]
+    ebs = [1e-2, 1e-3, 1e-4, 1e-5, 1e-6]
+    op = O.params(eb=1.0, r_sp=0.25, sel_rule=sel_rule)
+    xd = torch.from_numpy(x).cuda()
+    got = ctx.rd_curve(xd, _gp(R, op), ebs)
+    ref = O.rd_curve(x, op, ebs)
+    assert len(got) == len(ebs)
+    for g, o in zip(got, ref):
+        assert g["eb"] == o["eb"]
+        check_result(g["est"], o["est"], x.ndim)
+        check_truth(g["truth"], o["truth"])
+        for k in ("sz_ns", "sz_huff_bits", "sz_nesc", "sz_nsym", "br_sz_huff", "delta", "eb_abs"):
+            assert g["est_eb"][k] == o["est_eb"][k], k
+        assert g["est_eb"]["delta"] == 2 * g["est"]["eb_abs"]
+        for k in ("entropy", "br_sz"):
+            assert _rel(g["est_eb"][k], o["est_eb"][k]) <= REL_ENTROPY, k
+        check_truth(g["truth_eb"], o["truth_eb"])
+        assert g["selection_eb"] == o["selection_eb"]
+        assert g["best_eb_gt"] == o["best_eb_gt"]
+
+
 def test_hot_code_flushes_histogram_window(R, ctx):
     """A 16M-point sawtooth whose Lorenzo residuals are nearly all one code
     (3 at bin width 1): each CTA counts far more than 2^16 of that code, so

@@ -560,3 +560,22 @@ def test_estimate_sz_agrees_with_select_and_closed_form():
     e2 = O.estimate_sz(x, p, delta=0.0)
     assert e2["delta"] == 2 * e2["eb_abs"]
     assert e2["psnr_sz"] == pytest.approx(-20 * math.log10(1e-3) + 10 * math.log10(3), rel=1e-12)
+
+
+def test_rd_curve_fixed_error_selection_follows_the_paper():
+    """Evaluation section, fixed-PSNR vs fixed-maximum-error selection
+    (Fig. f9): at the same maximum error (eb_abs = 1e-3 of the value range)
+    the selection based on error bound picks SZ on smooth fields, by
+    estimate and by ground truth, while ZFP over-preserves the error (a
+    higher PSNR than SZ at the same bound); both stay within eb_abs.  The
+    rate-distortion selection is the one of Algorithm 1 at each bound."""
+    for x in (synth.config1_field(), synth.config2_field(seed=14, shape=(24, 40, 44))):
+        p = O.params(eb=1.0, r_sp=1.0)
+        (pt,) = O.rd_curve(x, p, [1e-3])
+        assert pt["selection_eb"] == 0 and pt["best_eb_gt"] == 0
+        t = pt["truth_eb"]
+        assert t["psnr_zfp_gt"] > t["psnr_sz_gt"]
+        assert t["maxerr_zfp"] <= pt["est"]["eb_abs"] and t["maxerr_sz"] <= pt["est"]["eb_abs"]
+        assert t["eb_sz"] == pt["est"]["eb_abs"]
+        assert pt["est_eb"]["delta"] == 2 * pt["est"]["eb_abs"]
+        assert pt["est"] == O.select(x, O.params(eb=1e-3, r_sp=1.0))
