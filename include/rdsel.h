@@ -262,8 +262,8 @@ typedef struct {
  *    a plan per distinct set of fields and parameters, with the stored SZ
  *    residuals of its sampled blocks (4^d words per sampled block: about 5%
  *    of the fields' bytes at r_sp = 0.05, counted against the HBM budget):
- *    the plan's first call runs the autotuner (three work-item sizes, the
- *    passes timed, the fastest kept) unless rd_batch_set_config forced a
+ *    the plan's first call runs the autotuner (three work-item sizes, each
+ *    run twice, the passes timed, the fastest kept) unless rd_batch_set_config forced a
  *    split; its second call captures a CUDA graph that later calls replay.
  *  - Each field's records equal those of rd_select (and of rd_evaluate for
  *    the truth) on that field alone. */
