@@ -133,6 +133,8 @@ def lib():
             "rdo_ec_positions": [C.c_int, C.c_int32, i32p, i32p],
             "rdo_sampling": [C.c_int, i64p, C.c_double, i32p, u64p, u64p],
             "rdo_mse_numerator": [i32p, i64p, C.c_int64, P(C.c_double)],
+            "rdo_classic_sz": [f32p, C.c_int, i64p, P(Params), C.c_double, P(Truth), u32p, i32p,
+                               f32p],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -225,6 +227,34 @@ def ground_truth(x: np.ndarray, p: Params, eb_sz: float = 0.0, want_hist: bool =
     d = _todict(t)
     if want_hist:
         d["hist"] = h
+    return d
+
+
+def classic_sz(x: np.ndarray, p: Params, eb_sz: float, want_hist: bool = False,
+               want_recon: bool = False, want_sym: bool = False):
+    """Classic SZ at the absolute bound eb_sz (Section "Prediction-Based
+    Transformation": prediction from the reconstructed neighbours, point by
+    point in storage order).  Returns the SZ fields of the truth record, and
+    the histogram and reconstruction when asked."""
+    x, shape = _field(x)
+    t = Truth()
+    h = np.zeros(NSYM, dtype=np.uint32) if want_hist else None
+    r = np.zeros(x.shape, dtype=np.float32) if want_recon else None
+    sy = np.zeros(x.shape, dtype=np.int32) if want_sym else None
+    rc = lib().rdo_classic_sz(_ptr(x, C.c_float), x.ndim, _ptr(shape, C.c_int64), C.byref(p),
+                              float(eb_sz), C.byref(t),
+                              _ptr(h, C.c_uint32) if h is not None else None,
+                              _ptr(sy, C.c_int32) if sy is not None else None,
+                              _ptr(r, C.c_float) if r is not None else None)
+    if rc:
+        raise OracleError(rc, "rdo_classic_sz")
+    d = _todict(t)
+    if want_hist:
+        d["hist"] = h
+    if want_recon:
+        d["recon"] = r
+    if want_sym:
+        d["sym"] = sy
     return d
 
 

@@ -1148,3 +1148,112 @@ int rdo_ground_truth(const float* x, int ndim, const int64_t* shape,
   free(h);
   return RDO_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Classic SZ ground truth (Section "Prediction-Based Transformation"):      */
+/* every point, in storage order, is predicted by the Lorenzo predictor from */
+/* the *reconstructed* values of its preceding neighbours (zero outside the  */
+/* field), as compression and decompression must predict alike.  The         */
+/* residual is quantised with bin w = 2 eb_sz; the reconstruction            */
+/* pred + q w is kept when |q| < R and it lies within tau of the value,      */
+/* otherwise the value escapes (stored exactly, symbol 0).  Stream cost and  */
+/* PSNR as in rdo_ground_truth.                                              */
+/* ------------------------------------------------------------------------ */
+
+/* Lorenzo prediction at idx from the reconstruction xh: the neighbours
+ * idx - s for the nonzero subsets s of the axes, added when s has an odd
+ * number of axes and subtracted when even, in increasing order of s (bit k
+ * of s steps back along axis d-1-k), as float operations. */
+static float classic_pred(const field_t* f, const float* xh, const int64_t* idx) {
+  float pred = 0.0f;
+  for (int s = 1; s < (1 << f->d); s++) {
+    int64_t j[3];
+    int odd = 0, inside = 1;
+    for (int k = 0; k < f->d; k++) j[k] = idx[k];
+    for (int b = 0; b < f->d; b++) {
+      if ((s >> b) & 1) {
+        j[f->d - 1 - b] -= 1;
+        odd ^= 1;
+      }
+    }
+    for (int k = 0; k < f->d; k++)
+      if (j[k] < 0) inside = 0;
+    float v = inside ? xh[lin_index(f, j)] : 0.0f;
+    pred = odd ? pred + v : pred - v;
+  }
+  return pred;
+}
+
+int rdo_classic_sz(const float* x, int ndim, const int64_t* shape, const rdo_params* p,
+                   double eb_sz, rdo_truth* t, uint32_t* hist, int32_t* sym_out, float* recon) {
+  field_t f;
+  int rc = field_init(&f, x, ndim, shape);
+  if (rc) return rc;
+  if ((rc = check_params(p))) return rc;
+  if (!t || !(eb_sz > 0.0) || !isfinite(eb_sz)) return RDO_ERR_INVALID_ARG;
+  memset(t, 0, sizeof(*t));
+  float vmin, vmax;
+  if ((rc = value_range(&f, &vmin, &vmax))) return rc;
+  double vr = (double)vmax - (double)vmin;
+  double delta = 2.0 * eb_sz;
+  t->delta = delta;
+  t->eb_sz = eb_sz;
+  if (vr == 0.0) {
+    t->flags |= RDO_F_CONSTANT;
+    t->psnr_sz_gt = INFINITY;
+    return RDO_OK;
+  }
+  sz_quant_t qz;
+  if ((rc = sz_quant_init(delta, &qz))) return rc;
+  float* xh = (float*)malloc((size_t)f.N * sizeof(float));
+  uint32_t* h = (uint32_t*)calloc(RDO_NSYM, sizeof(uint32_t));
+  if (!xh || !h) {
+    free(xh);
+    free(h);
+    return RDO_ERR_INVALID_ARG;
+  }
+  const float R = (float)p->quant_radius;
+  for (int64_t i = 0; i < f.N; i++) {
+    int64_t idx[3], rem = i;
+    for (int k = f.d - 1; k >= 0; k--) {
+      idx[k] = rem % f.n[k];
+      rem /= f.n[k];
+    }
+    const float pred = classic_pred(&f, xh, idx);
+    const float q = rintf((f.x[i] - pred) * qz.inv);
+    int sym = 0;
+    float rec = f.x[i];
+    if (fabsf(q) < R) {
+      const float cand = pred + q * qz.w;
+      if (fabsf(f.x[i] - cand) <= qz.tau) {
+        sym = (int)q + 32768;
+        rec = cand;
+      }
+    }
+    xh[i] = rec;
+    h[sym]++;
+    if (sym_out) sym_out[i] = sym;
+  }
+  double sse = 0.0, smax = 0.0;
+  for (int64_t i = 0; i < f.N; i++) {
+    double e = (double)f.x[i] - (double)xh[i];
+    sse += e * e;
+    if (fabs(e) > smax) smax = fabs(e);
+  }
+  uint64_t huff;
+  uint32_t K;
+  huffman_of_hist(h, &huff, &K);
+  t->sz_huff_gt = huff;
+  t->sz_nsym_gt = K;
+  t->sz_nesc_gt = h[0];
+  t->sz_bits_gt = huff + 32ull * h[0] + 22ull * K + 64ull;
+  t->br_sz_gt = (double)t->sz_bits_gt / (double)f.N;
+  t->sse_sz = sse;
+  t->maxerr_sz = smax;
+  t->psnr_sz_gt = psnr_of(vr, sse / (double)f.N);
+  if (hist) memcpy(hist, h, RDO_NSYM * sizeof(uint32_t));
+  if (recon) memcpy(recon, xh, (size_t)f.N * sizeof(float));
+  free(xh);
+  free(h);
+  return RDO_OK;
+}

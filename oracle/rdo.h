@@ -115,6 +115,14 @@ int rdo_ground_truth(const float* x, int ndim, const int64_t* shape,
                      const rdo_params* p, double eb_sz, rdo_truth* t,
                      uint32_t* hist_gt);
 
+/* Classic SZ at the absolute bound eb_sz > 0: prediction from the
+ * reconstructed neighbours, point by point in storage order.  Fills the SZ
+ * fields of t (eb_sz, delta, sz_*, br_sz_gt, sse_sz, maxerr_sz, psnr_sz_gt);
+ * hist: 65536 counts, sym: N symbols (0 = escaped), recon: N floats; each
+ * may be NULL. */
+int rdo_classic_sz(const float* x, int ndim, const int64_t* shape, const rdo_params* p,
+                   double eb_sz, rdo_truth* t, uint32_t* hist, int32_t* sym, float* recon);
+
 /* Per-block ZFP records over all blocks (block order, last axis fastest). */
 int rdo_zfp_blocks(const float* x, int ndim, const int64_t* shape,
                    double eb_abs, int32_t* emax, int32_t* prec,

@@ -579,3 +579,55 @@ def test_rd_curve_fixed_error_selection_follows_the_paper():
         assert t["eb_sz"] == pt["est"]["eb_abs"]
         assert pt["est_eb"]["delta"] == 2 * pt["est"]["eb_abs"]
         assert pt["est"] == O.select(x, O.params(eb=1e-3, r_sp=1.0))
+
+
+def _lorenzo_decode(sym, x, w):
+    """Decompression of a classic SZ stream written independently of the
+    oracle: each value is the Lorenzo prediction from the already decoded
+    neighbours (textbook stencil: 1D x[i-1]; 2D x[i,j-1] + x[i-1,j] -
+    x[i-1,j-1]; 3D the seven-term inclusion-exclusion) plus its code times
+    the bin, or the stored value where the code escaped."""
+    d = x.ndim
+    xs = np.zeros(x.shape, dtype=np.float64)
+    for idx in np.ndindex(*x.shape):
+        pred = 0.0
+        for sub in range(1, 1 << d):
+            off = [(sub >> (d - 1 - k)) & 1 for k in range(d)]
+            j = tuple(i - o for i, o in zip(idx, off))
+            if min(j) < 0:
+                continue
+            pred += (1.0 if sum(off) % 2 else -1.0) * xs[j]
+        s = int(sym[idx])
+        xs[idx] = x[idx] if s == 0 else pred + (s - 32768) * w
+    return xs
+
+
+@pytest.mark.parametrize("shape", [(57,), (9, 13), (5, 6, 7)])
+def test_classic_sz_stream_decodes_and_bounds(shape):
+    """Classic SZ (prediction from reconstructed neighbours): an independent
+    decoder reproduces the oracle's reconstruction from its codes and the
+    escaped values (to rounding), every point is within eb_sz, and the
+    histogram counts the codes."""
+    rng = np.random.default_rng(31)
+    x = np.cumsum(rng.standard_normal(shape), axis=-1).astype(np.float32)
+    eb_sz = 0.05
+    t = O.classic_sz(x, O.params(eb=1e-3, quant_radius=8), eb_sz, want_hist=True,
+                     want_recon=True, want_sym=True)
+    w = np.float32(2 * eb_sz)
+    dec = _lorenzo_decode(t["sym"], x, float(w))
+    assert np.max(np.abs(dec - t["recon"].astype(np.float64))) < 1e-4
+    assert np.all(np.abs(x.astype(np.float64) - t["recon"]) <= eb_sz)
+    assert t["maxerr_sz"] <= eb_sz
+    assert np.array_equal(np.bincount(t["sym"].ravel(), minlength=65536), t["hist"])
+    assert t["sz_nesc_gt"] == int((t["sym"] == 0).sum()) > 0  # the small radius forces escapes
+
+
+def test_classic_sz_integer_ramp_closed_form():
+    """A 1D integer ramp at bin 1 (eb_sz 0.5): the first point is predicted
+    from the zero boundary (code +0), every later one from its exact
+    predecessor (code +1), and the reconstruction is exact."""
+    x = np.arange(1000, dtype=np.float32)
+    t = O.classic_sz(x, O.params(eb=1e-3), 0.5, want_hist=True, want_recon=True)
+    h = t["hist"]
+    assert h[32768] == 1 and h[32769] == 999 and h.sum() == 1000
+    assert np.array_equal(t["recon"], x) and t["maxerr_sz"] == 0.0
