@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
     ap.add_argument("--no-curve", action="store_true",
                     help="skip the rate-distortion sweep (error bounds 1e-2 .. 1e-6)")
+    ap.add_argument("--no-classic", action="store_true",
+                    help="skip the classic SZ truth beside the prequantised one")
     ap.add_argument("--serve-population", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-rates", default="100,500,2000")
@@ -298,6 +300,45 @@ def bench_rd_curve(R, ctx, x, stream, reps: int = 5):
             "ms_per_sweep": statistics.median(ms),
             "calls_per_bound": "rd_evaluate + rd_estimate_sz(2 eb_abs) + rd_ground_truth(eb_abs)",
             "points": points}
+
+
+def bench_classic(R, ctx, x, stream, reps: int = 3):
+    """The classic SZ truth (prediction from reconstructed neighbours, one
+    launch per wavefront) beside the prequantised truth at the same bound
+    eb_sz = EB_REL * VR, on the benchmark field and on one 1800x3600
+    ATM-shaped field: device time per call and what each truth reports."""
+    import torch
+
+    import synth
+
+    def timed(fn):
+        fn()  # first call, then a captured repeat
+        fn()
+        ms = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            out = fn()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms), out
+
+    atm = synth.make_field_torch(synth.snapshot_specs()[0])
+    res = {}
+    for name, f in (("hurricane_100x500x500", x), ("atm_1800x3600", atm)):
+        vr = float(f.max()) - float(f.min())
+        eb_sz = EB_REL * vr
+        p = R.params(eb=EB_REL, r_sp=R_SP)
+        ms_c, tc = timed(lambda: ctx.ground_truth_classic(f, p, eb_sz, stream=stream))
+        ms_d, td = timed(lambda: ctx.ground_truth(f, p, eb_sz, stream))
+        res[name] = {"eb_sz": eb_sz, "ms_classic": ms_c, "ms_prequantised": ms_d,
+                     "br_sz_classic": tc["br_sz_gt"], "br_sz_prequantised": td["br_sz_gt"],
+                     "psnr_classic": tc["psnr_sz_gt"], "psnr_prequantised": td["psnr_sz_gt"],
+                     "nesc_classic": tc["sz_nesc_gt"], "nesc_prequantised": td["sz_nesc_gt"]}
+    del atm
+    return res
 
 
 def bench_serving(R, population: int, n_req: int, rates, budget: int = 120 << 30):
@@ -564,6 +605,8 @@ def main():
     }
     if not args.no_curve and world == 1:
         line["rd_curve"] = bench_rd_curve(R, ctx, x, stream)
+    if not args.no_classic and world == 1:
+        line["classic_truth"] = bench_classic(R, ctx, x, stream)
     if not args.no_batch and world == 1:
         line["batched"] = bench_snapshot(R, ctx, stream, args.batch_steps, peak, peak_kind,
                                          args.batch_subset)

@@ -162,6 +162,34 @@ int32_t rd_ground_truth(rd_context* ctx, const rd_field* field,
                         const rd_params* params, double eb_sz,
                         rd_truth* out, void* stream);
 
+/* Classic SZ ground truth (Section "Prediction-Based Transformation"):
+ * every point predicted by the Lorenzo predictor from the RECONSTRUCTED
+ * values of its preceding neighbours (zero outside the field), the residual
+ * quantised with bin w = float(2 eb_sz), the reconstruction pred + q w kept
+ * when |q| < quant_radius and |x - (pred + q w)| <= tau (the largest float
+ * not above eb_sz (1 - 2^-23)), else the value escapes (symbol 0, stored
+ * exactly).  The stream is costed as in rd_ground_truth (Huffman bits +
+ * 32 bits per escape + 22 bits per distinct symbol + 64).  This is the
+ * serial predictor that rd_ground_truth's prequantised codes stand in for:
+ * it measures how far that stand-in is from what a sequential SZ writes.
+ *  - eb_sz: the absolute bound, > 0 and finite (else RD_ERR_INVALID_ARG).
+ *  - Fills the SZ fields of *out (delta = 2 eb_sz, eb_sz, sz_huff_gt,
+ *    sz_nsym_gt, sz_nesc_gt, sz_bits_gt, br_sz_gt, sse_sz, maxerr_sz,
+ *    psnr_sz_gt) and flags; the ZFP fields stay 0.
+ *  - recon: NULL, or DEVICE memory for N floats (caller-owned, the field's
+ *    row-major order) that receives the reconstruction a decompressor
+ *    would produce (for a constant field: the field itself).
+ *  - Device work: the points are taken in dependency wavefronts (1D: one
+ *    chain; 2D: 32x128 tiles, one launch per anti-diagonal of tiles; 3D: one
+ *    launch per point wavefront i+j+k = s), so the call is far slower than
+ *    rd_ground_truth.  The context keeps an N-float reconstruction buffer,
+ *    counted against its memory budget (RD_ERR_BUDGET when it would not fit).
+ *  - Results are bit-identical for codes, histogram, escapes and bits; the
+ *    SSE differs from a sequential sum by rounding order only. */
+int32_t rd_ground_truth_classic(rd_context* ctx, const rd_field* field,
+                                const rd_params* params, double eb_sz,
+                                rd_truth* out, float* recon, void* stream);
+
 /* rd_select followed by rd_ground_truth at delta/2, fused into three passes
  * over the field (range; ZFP estimate + ZFP truth; SZ estimate + SZ truth).
  * Either output may be NULL. */

@@ -22,7 +22,7 @@ const char* kKernelNames[K_COUNT] = {
     "reset", "range", "zfp_pass", "delta", "sz_est", "sz_pass",
     "code_prep", "huffman", "finish", "zfp_inspect", "sz_inspect",
     "batch_reset", "batch_range", "batch_blocks", "batch_sz_hist", "batch_code_prep",
-    "batch_final", "batch_truth"};
+    "batch_final", "batch_truth", "sz_classic", "sz_classic_err"};
 
 struct KStat {
   double ms;
@@ -50,6 +50,7 @@ struct CallKey {
   double delta_arg;
   int profiling;
   int pad;
+  const void* aux;  // the reconstruction buffer of a classic SZ truth, else NULL
 };
 
 struct GraphEntry {
@@ -111,6 +112,8 @@ struct rd_context {
   HostOut* out = nullptr;  // pinned
   float* staging = nullptr;
   size_t staging_bytes = 0;
+  float* xhat = nullptr;  // reconstruction of the classic SZ truth
+  size_t xhat_bytes = 0;
   int num_sms = 0;
   int range_ctas = 0;
   int zfp_ctas[4] = {0, 0, 0, 0};
@@ -194,6 +197,14 @@ int launch(rd_context* c, int kid, cudaStream_t s, F&& fn) {
   else
     c->launches++;
   return cuda_status(e);
+}
+
+// Kernels launched by one launch() call beyond the first.
+void count_extra(rd_context* c, long long n) {
+  if (c->capturing)
+    c->cap_kernels += n;
+  else
+    c->launches += n;
 }
 
 void add_times(rd_context* c, const std::vector<Pending>& evs) {
@@ -364,7 +375,8 @@ int issue(rd_context* c, const CallKey& k, const Geometry& g, cudaStream_t s) {
   Workspace* ws = c->ws;
   const int d = f.d;
   const bool need_gt = passes & P_SZ_GT;
-  const bool need_quant = passes & (P_SZ_EST | P_SZ_GT);
+  const bool classic = passes & P_SZ_CLASSIC;
+  const bool need_quant = passes & (P_SZ_EST | P_SZ_GT | P_SZ_CLASSIC);
   const unsigned long long ncoeff = (unsigned long long)f.nsampled * ec_count(d, p.ec_mode);
   int zfp_parts = 0, sz_parts = 0;
   int rc;
@@ -400,13 +412,25 @@ int issue(rd_context* c, const CallKey& k, const Geometry& g, cudaStream_t s) {
     if ((rc = launch(c, K_SZ_EST, s, [&] { return launch_sz_est(f, p, ws, c->sz_est_ctas[d], s); })))
       return rc;
   }
-  int hist_mask = ((passes & P_SZ_EST) ? 1 : 0) | ((passes & P_SZ_GT) ? 2 : 0);
+  if (classic) {
+    // the classic truth shares the truth histogram and the SSE partials
+    float* xh = static_cast<float*>(const_cast<void*>(k.aux));
+    if ((rc = launch(c, K_SZ_CLASSIC, s, [&] { return launch_classic_waves(f, p, xh, ws, s); })))
+      return rc;
+    count_extra(c, classic_launches(f) - 1);
+    if ((rc = launch(c, K_SZ_CLASSIC_ERR, s, [&] {
+           return launch_classic_err(f, xh, ws, c->num_sms * 8, s, &sz_parts);
+         })))
+      return rc;
+  }
+  int hist_mask = ((passes & P_SZ_EST) ? 1 : 0) | ((passes & (P_SZ_GT | P_SZ_CLASSIC)) ? 2 : 0);
+  const int fin_passes = classic ? (passes | P_SZ_GT) : passes;
   if (hist_mask) {
     if ((rc = launch(c, K_CODE_PREP, s, [&] { return launch_code_prep(ws, hist_mask, s); }))) return rc;
     if ((rc = launch(c, K_HUFFMAN, s, [&] { return launch_huffman(ws, hist_mask, c->xlogx, s); }))) return rc;
   }
   if ((rc = launch(c, K_FINISH, s, [&] {
-         return launch_finish(p, ws, passes, zfp_parts, sz_parts, f.N, g.npoints_sampled, s);
+         return launch_finish(p, ws, fin_passes, zfp_parts, sz_parts, f.N, g.npoints_sampled, s);
        })))
     return rc;
   // one copy of the result records and the device status
@@ -485,6 +509,21 @@ int run(rd_context* c, const rd_field* fld, const rd_params* prm, int passes, in
   k.delta_mode = delta_mode;
   k.delta_arg = delta_arg;
   k.profiling = c->profiling ? 1 : 0;
+  if (passes & P_SZ_CLASSIC) {
+    // the reconstruction buffer, grown to the field
+    const size_t bytes = (size_t)g.f.N * sizeof(float);
+    if (bytes > c->xhat_bytes) {
+      if (c->budget && c->held + (bytes - c->xhat_bytes) > c->budget) return RD_ERR_BUDGET;
+      if (c->xhat) cudaFree(c->xhat);
+      c->held -= c->xhat_bytes;
+      c->xhat = nullptr;
+      c->xhat_bytes = 0;
+      if (cudaMalloc(&c->xhat, bytes) != cudaSuccess) return RD_ERR_OOM;
+      c->xhat_bytes = bytes;
+      c->held += bytes;
+    }
+    k.aux = c->xhat;
+  }
   const FieldDev& f = g.f;
   const int d = f.d;
   const unsigned long long ncoeff = (unsigned long long)f.nsampled * ec_count(d, prm->ec_mode);
@@ -1060,6 +1099,7 @@ int32_t rd_context_destroy(rd_context* c) {
   free_batch_buffers(c);
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->staging) cudaFree(c->staging);
+  if (c->xhat) cudaFree(c->xhat);
   if (c->ws) cudaFree(c->ws);
   if (c->xlogx) cudaFree(c->xlogx);
   if (c->out) cudaFreeHost(c->out);
@@ -1091,6 +1131,24 @@ int32_t rd_ground_truth(rd_context* c, const rd_field* f, const rd_params* p, do
   if (eb_sz > 0.0)
     return run(c, f, p, P_ZFP_GT | P_SZ_GT, DELTA_FROM_EB_SZ, eb_sz, nullptr, out, stream);
   return run(c, f, p, P_ZFP_GT | P_ZFP_EST | P_SZ_GT, DELTA_FROM_MSE, 0.0, nullptr, out, stream);
+}
+
+int32_t rd_ground_truth_classic(rd_context* c, const rd_field* f, const rd_params* p, double eb_sz,
+                                rd_truth* out, float* recon, void* stream) {
+  if (!out || !(eb_sz > 0.0) || !isfinite(eb_sz)) return RD_ERR_INVALID_ARG;
+  int rc = run(c, f, p, P_SZ_CLASSIC, DELTA_FROM_EB_SZ, eb_sz, nullptr, out, stream);
+  if (rc || !recon) return rc;
+  CallGuard guard(c->device);
+  size_t n = 1;
+  for (int k = 0; k < f->ndim; k++) n *= (size_t)f->shape[k];
+  const bool constant = out->flags & RD_F_CONSTANT;
+  const void* src = constant ? (const void*)f->data : (const void*)c->xhat;
+  const cudaMemcpyKind kind =
+      constant && f->location == RD_LOC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(recon, src, n * sizeof(float), kind, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return cuda_status(e);
 }
 
 int32_t rd_evaluate(rd_context* c, const rd_field* f, const rd_params* p, rd_result* est,

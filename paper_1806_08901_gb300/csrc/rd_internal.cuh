@@ -143,6 +143,8 @@ enum KernelId {
   K_B_PREP,
   K_B_FINAL,
   K_B_TRUTH,
+  K_SZ_CLASSIC,
+  K_SZ_CLASSIC_ERR,
   K_COUNT
 };
 
@@ -152,6 +154,7 @@ enum PassFlags : int {
   P_ZFP_GT = 2,    // ZFP truth over every block
   P_SZ_EST = 4,    // SZ estimate over points of sampled blocks
   P_SZ_GT = 8,     // SZ truth over every point
+  P_SZ_CLASSIC = 16,  // classic SZ truth (prediction from reconstructed values)
 };
 
 enum DeltaMode { DELTA_FROM_MSE = 0, DELTA_EXPLICIT = 1, DELTA_FROM_EB_SZ = 2 };
@@ -184,6 +187,14 @@ cudaError_t launch_sz_est(const FieldDev& f, const ParamsDev& p, Workspace* ws,
                           int ctas, cudaStream_t s);
 cudaError_t prepare_sz_est();
 int sz_est_occupancy(int d, int num_sms);
+// classic SZ truth: the wavefront launches over the field (their number is
+// classic_launches(f)), which write the reconstruction to xh (N floats) and
+// the codes to the truth histogram, then the error pass (per-CTA partials)
+long long classic_launches(const FieldDev& f);
+cudaError_t launch_classic_waves(const FieldDev& f, const ParamsDev& p, float* xh, Workspace* ws,
+                                 cudaStream_t s);
+cudaError_t launch_classic_err(const FieldDev& f, const float* xh, Workspace* ws, int ctas,
+                               cudaStream_t s, int* grid_used);
 cudaError_t launch_sz_gt(const FieldDev& f, const ParamsDev& p, int with_est,
                          Workspace* ws, int ctas, cudaStream_t s, int* grid_used);
 // Entropy partials and count-of-counts (launch_code_prep), then the Huffman

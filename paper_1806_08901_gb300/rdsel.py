@@ -116,6 +116,8 @@ _SIGNATURES = {
     "rd_select": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), _P(rd_result), C.c_void_p]),
     "rd_ground_truth": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), C.c_double,
                                     _P(rd_truth), C.c_void_p]),
+    "rd_ground_truth_classic": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), C.c_double,
+                                            _P(rd_truth), C.c_void_p, C.c_void_p]),
     "rd_rd_curve": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), _P(C.c_double), C.c_int32,
                                 _P(rd_rd_point), C.c_void_p]),
     "rd_evaluate": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), _P(rd_result),
@@ -292,6 +294,26 @@ def rd_ground_truth(ctx, field, prm: rd_params, eb_sz: float = 0.0, stream=None)
     t = rd_truth()
     _check(lib().rd_ground_truth(ctx, C.byref(f), C.byref(prm), float(eb_sz), C.byref(t),
                                  _stream(stream)), "rd_ground_truth")
+    return _todict(t)
+
+
+def rd_ground_truth_classic(ctx, field, prm: rd_params, eb_sz: float, recon=None,
+                            stream=None) -> dict:
+    """Classic SZ truth at the absolute bound eb_sz; recon, when given, is a
+    contiguous float32 device tensor of the field's size that receives the
+    reconstruction."""
+    f, keep = make_field(field)
+    t = rd_truth()
+    rp = None
+    if recon is not None:
+        import torch
+        n = int(np.prod([f.shape[k] for k in range(f.ndim)]))
+        if not (isinstance(recon, torch.Tensor) and recon.is_cuda and recon.dtype == torch.float32
+                and recon.is_contiguous() and recon.numel() == n):
+            raise ValueError("recon must be a contiguous float32 CUDA tensor of the field's size")
+        rp = C.c_void_p(recon.data_ptr())
+    _check(lib().rd_ground_truth_classic(ctx, C.byref(f), C.byref(prm), float(eb_sz), C.byref(t),
+                                         rp, _stream(stream)), "rd_ground_truth_classic")
     return _todict(t)
 
 
@@ -561,6 +583,9 @@ class Context:
 
     def ground_truth(self, x, p, eb_sz=0.0, stream=None):
         return rd_ground_truth(self.h, x, p, eb_sz, stream)
+
+    def ground_truth_classic(self, x, p, eb_sz, recon=None, stream=None):
+        return rd_ground_truth_classic(self.h, x, p, eb_sz, recon, stream)
 
     def evaluate(self, x, p, stream=None):
         return rd_evaluate(self.h, x, p, stream)
