@@ -1196,13 +1196,15 @@ int rdo_classic_sz(const float* x, int ndim, const int64_t* shape, const rdo_par
   if ((rc = value_range(&f, &vmin, &vmax))) return rc;
   double vr = (double)vmax - (double)vmin;
   double delta = 2.0 * eb_sz;
-  t->delta = delta;
-  t->eb_sz = eb_sz;
   if (vr == 0.0) {
+    /* nothing to quantise: the record holds the flag and PSNR only, as
+     * rdo_ground_truth's does */
     t->flags |= RDO_F_CONSTANT;
     t->psnr_sz_gt = INFINITY;
     return RDO_OK;
   }
+  t->delta = delta;
+  t->eb_sz = eb_sz;
   sz_quant_t qz;
   if ((rc = sz_quant_init(delta, &qz))) return rc;
   float* xh = (float*)malloc((size_t)f.N * sizeof(float));
