@@ -180,8 +180,8 @@ int32_t rd_ground_truth(rd_context* ctx, const rd_field* field,
  *    row-major order) that receives the reconstruction a decompressor
  *    would produce (for a constant field: the field itself).
  *  - Device work: the points are taken in dependency wavefronts (1D: one
- *    chain; 2D: 32x128 tiles, one launch per anti-diagonal of tiles; 3D: one
- *    launch per point wavefront i+j+k = s), so the call is far slower than
+ *    chain; 2D and 3D: 32x32 tiles of a plane, one launch per wavefront of
+ *    tiles, plane + row tile + column tile = w), so the call is far slower than
  *    rd_ground_truth.  The context keeps an N-float reconstruction buffer,
  *    counted against its memory budget (RD_ERR_BUDGET when it would not fit).
  *  - Results are bit-identical for codes, histogram, escapes and bits; the

@@ -9,11 +9,11 @@
 // A point depends on the reconstruction of the points before it on its
 // stencil, so the field is walked in wavefronts:
 //  * 1D: one chain, one thread, the previous reconstruction in a register;
-//  * 2D: tiles of 32 rows x 128 columns, one warp each, lane r taking row r
-//    one step behind lane r-1 (its upper neighbours come by shuffle, the
-//    tile's halo row and column from the tiles before it); a launch per
-//    anti-diagonal of tiles;
-//  * 3D: a launch per wavefront i + j + k = s of points, a thread per (i, j).
+//  * 2D and 3D: tiles of 32 rows x 32 columns of one plane, one warp each,
+//    lane r taking row r one step behind lane r-1 (its upper neighbours come
+//    by shuffle, the tile's halo row and column and the previous plane from
+//    the tiles before it); a launch per wavefront of tiles, plane + row tile
+//    + column tile = w.
 // The reconstruction is kept in a field-sized buffer; a last pass sums the
 // squared errors in fixed order.
 #include <stdint.h>
@@ -24,7 +24,10 @@ namespace rdk {
 
 constexpr int kClassicThreads = 256;
 constexpr int kTileRows = 32;    // one warp: a lane per row
-constexpr int kTileCols = 128;
+constexpr int kTileWin = 256;   // per-tile shared histogram of the codes near zero
+constexpr int kTileCols = 32;   // the tile wavefront's critical path is
+                                 // (planes + row tiles + column tiles) x
+                                 // (rows + columns of a tile) steps
 
 // The code of one point with prediction pred: its symbol, and rec, the
 // value a decompressor reconstructs.
@@ -41,6 +44,17 @@ __device__ __forceinline__ int classic_code(float x, float pred, float w, float 
   }
   return 0;
 }
+
+// Four bytes from global to shared memory without a register round trip
+// (cp.async); zeros when !valid (source size 0: nothing is read, src only
+// has to be a valid address).  All of a tile's copies are in flight at once.
+__device__ __forceinline__ void copy4(float* dst, const float* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0)
+               : "memory");
+}
+
+__device__ __forceinline__ void copy_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // One histogram increment per active lane, equal codes of a warp merged
 // into one atomic.  Every lane of the warp calls it.
@@ -68,50 +82,92 @@ __global__ void k_classic_chain(FieldDev f, ParamsDev p, float* xh, Workspace* w
   }
 }
 
-// 2D tile (a, b) with a + b = u, a = a_lo + blockIdx.x.  The prediction of
-// (i, j) is 0 + xhat(i, j-1) + xhat(i-1, j) - xhat(i-1, j-1), in that order.
-// Lane r computes (i0 + r, j0 + t - r) at step t: its left neighbour is its
-// own result of step t-1, its upper neighbours lane r-1's results of steps
-// t-1 and t-2.
-__global__ void __launch_bounds__(kTileRows) k_classic_tile2(FieldDev f, ParamsDev p, int u, int a_lo,
-                                                             float* xh, Workspace* ws) {
-  __shared__ float s_t[kTileRows][kTileCols + 2];  // the tile (row pitch 130: the skewed
-                                                   // accesses of a step fall in 32 banks)
-  __shared__ float s_up[kTileCols + 1];             // xhat(i0-1, j0-1+c), c = 0..kTileCols
+// A tile of 32 rows x 32 columns of one plane (3D: plane p along axis 0,
+// rows along axis 1, columns along axis 2; 2D: the one plane), one warp.
+// Lane r computes (row i0 + r, column j0 + t - r) at step t: its left
+// neighbour is its own result of step t-1, its upper and upper-left
+// neighbours lane r-1's results of steps t-1 and t-2; the tile's halo row
+// and column, and in 3D the previous plane, come from tiles finished by
+// earlier launches.  The prediction adds the neighbours in the order of the
+// subsets e = 1 .. 2^D - 1 (bit b of e steps back along axis D-1-b): left,
+// up, -upper-left, and in 3D then +P, -P left, -P up, +P upper-left from
+// the previous plane.  The tiles of one launch are those with p + a + b = w
+// (2D: a = a_lo + blockIdx.x, b = w - a; 3D: (a, b) from blockIdx.x, the
+// others return at once).
+template <int D>
+__global__ void __launch_bounds__(kTileRows) k_classic_tile(FieldDev f, ParamsDev p, int w, int a_lo,
+                                                            float* xh, Workspace* ws) {
+  constexpr int kPitch = kTileCols + 2;  // 34: the skewed accesses of a step hit 32 banks
+  __shared__ float s_x[kTileRows][kPitch];                       // values, then reconstructions
+  __shared__ float s_prev[D == 3 ? kTileRows + 1 : 1][kPitch];   // 3D: plane p-1, rows i0-1..,
+                                                                 // columns j0-1..
+  __shared__ unsigned short s_sym[kTileRows][kPitch];
+  __shared__ float s_up[kTileCols + 1];  // xhat of row i0-1, columns j0-1 ..
+  __shared__ unsigned s_win[kTileWin];   // codes |q| < kTileWin / 2 of the tile
   const Scalars& sc = ws->sc;
   if (sc.status != RD_OK || sc.constant) return;
+  const int nr = f.n[D - 2], nc = f.n[D - 1];
+  int a, b, pl;
+  if (D == 3) {
+    const int nb = (nc + kTileCols - 1) / kTileCols;
+    a = blockIdx.x / nb;
+    b = blockIdx.x - a * nb;
+    pl = w - a - b;
+    if (pl < 0 || pl >= f.n[0]) return;  // uniform over the CTA
+  } else {
+    a = a_lo + blockIdx.x;
+    b = w - a;
+    pl = 0;
+  }
   const int lane = threadIdx.x;
-  const int a = a_lo + blockIdx.x, b = u - a;
-  const int n0 = f.n[0], n1 = f.n[1];
   const int i0 = a * kTileRows, j0 = b * kTileCols;
-  const float* __restrict__ x = f.x;
+  const long long plane = (long long)nr * nc;
+  const long long base = (long long)pl * plane;
+  const float* __restrict__ x = f.x + base;
+  float* xp = xh + base;
+  // the tile, its halo row and (3D) the previous plane: every copy issued
+  // before the first wait; out-of-field cells read as zero
   for (int r = 0; r < kTileRows; r++) {
     const int i = i0 + r;
-    if (i >= n0) break;
 #pragma unroll
     for (int q = 0; q < kTileCols / 32; q++) {
       const int c = lane + 32 * q, j = j0 + c;
-      s_t[r][c] = j < n1 ? x[(long long)i * n1 + j] : 0.0f;
+      const bool ok = i < nr && j < nc;
+      copy4(&s_x[r][c], ok ? x + (long long)i * nc + j : x, ok);
     }
   }
   for (int c = lane; c <= kTileCols; c += 32) {
     const int j = j0 - 1 + c;
-    s_up[c] = (i0 > 0 && j >= 0 && j < n1) ? xh[(long long)(i0 - 1) * n1 + j] : 0.0f;
+    const bool ok = i0 > 0 && j >= 0 && j < nc;
+    copy4(&s_up[c], ok ? xp + (long long)(i0 - 1) * nc + j : xp, ok);
+  }
+  if (D == 3) {
+    const float* pp = pl > 0 ? xp - plane : xp;
+    for (int r = 0; r <= kTileRows; r++) {
+      const int i = i0 - 1 + r;
+      for (int c = lane; c <= kTileCols; c += 32) {
+        const int j = j0 - 1 + c;
+        const bool ok = pl > 0 && i >= 0 && i < nr && j >= 0 && j < nc;
+        copy4(&s_prev[r][c], ok ? pp + (long long)i * nc + j : xp, ok);
+      }
+    }
   }
   const int i = i0 + lane;
-  const float left0 = (j0 > 0 && i < n0) ? xh[(long long)i * n1 + j0 - 1] : 0.0f;
+  const bool row_ok = i < nr;
+  const float left0 = (j0 > 0 && row_ok) ? xp[(long long)i * nc + j0 - 1] : 0.0f;
   float upleft0 = __shfl_up_sync(0xffffffffu, left0, 1);  // xhat(i-1, j0-1)
+  for (int k = lane; k < kTileWin; k += 32) s_win[k] = 0u;
+  copy_wait_all();
   __syncwarp();
   if (lane == 0) upleft0 = s_up[0];
-  const float w = sc.w, inv = sc.inv, tau = sc.tau, Rf = (float)p.R;
+  const float w_ = sc.w, inv = sc.inv, tau = sc.tau, Rf = (float)p.R;
   float last = 0.0f, last2 = 0.0f;  // this lane's results of the two steps before
   for (int t = 0; t < kTileCols + kTileRows - 1; t++) {
     const int c = t - lane;
     const float up_l = __shfl_up_sync(0xffffffffu, last, 1);
     const float ul_l = __shfl_up_sync(0xffffffffu, last2, 1);
-    const bool act = c >= 0 && c < kTileCols && i < n0 && j0 + c < n1;
+    const bool act = c >= 0 && c < kTileCols && row_ok && j0 + c < nc;
     float rec = 0.0f;
-    int sym = 0;
     if (act) {
       const float left = c > 0 ? last : left0;
       const float up = lane > 0 ? up_l : s_up[1 + c];
@@ -119,56 +175,47 @@ __global__ void __launch_bounds__(kTileRows) k_classic_tile2(FieldDev f, ParamsD
       float pred = __fadd_rn(0.0f, left);
       pred = __fadd_rn(pred, up);
       pred = __fsub_rn(pred, ul);
-      sym = classic_code(s_t[lane][c], pred, w, inv, tau, Rf, rec);
-      s_t[lane][c] = rec;
+      if (D == 3) {
+        pred = __fadd_rn(pred, s_prev[lane + 1][c + 1]);
+        pred = __fsub_rn(pred, s_prev[lane + 1][c]);
+        pred = __fsub_rn(pred, s_prev[lane][c + 1]);
+        pred = __fadd_rn(pred, s_prev[lane][c]);
+      }
+      const int sym = classic_code(s_x[lane][c], pred, w_, inv, tau, Rf, rec);
+      s_sym[lane][c] = (unsigned short)sym;
+      s_x[lane][c] = rec;
     }
     last2 = last;
     last = rec;
-    classic_hist(ws->hist[1], act, sym);
   }
   __syncwarp();
+  // reconstructions out, row by row; the codes: equal codes of 32 merged,
+  // those near zero counted in shared memory (every tile of a launch hits
+  // the same few hot codes), the rest with global atomics
+  constexpr int kWinLo = kCenter - kTileWin / 2;
   for (int r = 0; r < kTileRows; r++) {
     const int ii = i0 + r;
-    if (ii >= n0) break;
+    if (ii >= nr) break;
 #pragma unroll
     for (int q = 0; q < kTileCols / 32; q++) {
-      const int c = lane + 32 * q, j = j0 + c;
-      if (j < n1) xh[(long long)ii * n1 + j] = s_t[r][c];
+      const int c = lane + 32 * q;
+      const bool ok = j0 + c < nc;
+      if (ok) xp[(long long)ii * nc + j0 + c] = s_x[r][c];
+      const int sym = ok ? (int)s_sym[r][c] : 0;
+      const bool inw = ok && (unsigned)(sym - kWinLo) < (unsigned)kTileWin;
+      const unsigned mw = __ballot_sync(0xffffffffu, inw);
+      if (inw) {
+        const unsigned same = __match_any_sync(mw, sym);
+        if (lane == __ffs(same) - 1) atomicAdd(&s_win[sym - kWinLo], (unsigned)__popc(same));
+      }
+      classic_hist(ws->hist[1], ok && !inw, sym);
     }
   }
-}
-
-// 3D wavefront s: thread t takes (i, j) = (t / n1, t % n1) and k = s - i - j.
-// The seven neighbours idx - e for the nonzero subsets e of the axes (bit b
-// of e steps back along axis 2-b) are added when e has an odd number of axes
-// and subtracted when even, in increasing order of e; outside the field they
-// are zero.
-__global__ void __launch_bounds__(kClassicThreads) k_classic_wave3(FieldDev f, ParamsDev p, int s,
-                                                                   float* xh, Workspace* ws) {
-  const Scalars& sc = ws->sc;
-  if (sc.status != RD_OK || sc.constant) return;  // uniform over the grid
-  const int n0 = f.n[0], n1 = f.n[1], n2 = f.n[2];
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = (int)(t / n1), j = (int)(t % n1), k = s - i - j;
-  const bool act = i < n0 && k >= 0 && k < n2;
-  int sym = 0;
-  if (act) {
-    const long long pl = (long long)n1 * n2;
-    const long long l = (long long)i * pl + (long long)j * n2 + k;
-    float pred = 0.0f;
-#pragma unroll
-    for (int e = 1; e < 8; e++) {
-      const int di = (e >> 2) & 1, dj = (e >> 1) & 1, dk = e & 1;
-      const bool odd = ((di + dj + dk) & 1) != 0;
-      const bool inside = i >= di && j >= dj && k >= dk;
-      const float v = inside ? xh[l - di * pl - dj * n2 - dk] : 0.0f;
-      pred = odd ? __fadd_rn(pred, v) : __fsub_rn(pred, v);
-    }
-    float rec;
-    sym = classic_code(f.x[l], pred, sc.w, sc.inv, sc.tau, (float)p.R, rec);
-    xh[l] = rec;
+  __syncwarp();
+  for (int k = lane; k < kTileWin; k += 32) {
+    const unsigned v = s_win[k];
+    if (v) atomicAdd(&ws->hist[1][kWinLo + k], v);
   }
-  classic_hist(ws->hist[1], act, sym);
 }
 
 // Squared errors (the difference of two floats, exact in double) and the
@@ -214,8 +261,8 @@ int tiles(int n, int t) { return (n + t - 1) / t; }
 
 long long classic_launches(const FieldDev& f) {
   if (f.d == 1) return 1;
-  if (f.d == 2) return tiles(f.n[0], kTileRows) + tiles(f.n[1], kTileCols) - 1;
-  return (long long)f.n[0] + f.n[1] + f.n[2] - 2;
+  const int na = tiles(f.n[f.d - 2], kTileRows), nb = tiles(f.n[f.d - 1], kTileCols);
+  return (long long)(f.d == 3 ? f.n[0] : 1) + na + nb - 2;
 }
 
 cudaError_t launch_classic_waves(const FieldDev& f, const ParamsDev& p, float* xh, Workspace* ws,
@@ -224,25 +271,16 @@ cudaError_t launch_classic_waves(const FieldDev& f, const ParamsDev& p, float* x
     k_classic_chain<<<1, 1, 0, st>>>(f, p, xh, ws);
     return cudaGetLastError();
   }
-  if (f.d == 2) {
-    const int na = tiles(f.n[0], kTileRows), nb = tiles(f.n[1], kTileCols);
-    for (int u = 0; u < na + nb - 1; u++) {
-      const int a_lo = u - (nb - 1) > 0 ? u - (nb - 1) : 0;
-      const int a_hi = u < na - 1 ? u : na - 1;
-      k_classic_tile2<<<a_hi - a_lo + 1, kTileRows, 0, st>>>(f, p, u, a_lo, xh, ws);
-      cudaError_t e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
+  const int na = tiles(f.n[f.d - 2], kTileRows), nb = tiles(f.n[f.d - 1], kTileCols);
+  const long long waves = classic_launches(f);
+  for (long long w = 0; w < waves; w++) {
+    if (f.d == 2) {
+      const int a_lo = w - (nb - 1) > 0 ? (int)w - (nb - 1) : 0;
+      const int a_hi = w < na - 1 ? (int)w : na - 1;
+      k_classic_tile<2><<<a_hi - a_lo + 1, kTileRows, 0, st>>>(f, p, (int)w, a_lo, xh, ws);
+    } else {
+      k_classic_tile<3><<<na * nb, kTileRows, 0, st>>>(f, p, (int)w, 0, xh, ws);
     }
-    return cudaSuccess;
-  }
-  const int n0 = f.n[0], n1 = f.n[1];
-  const int waves = f.n[0] + f.n[1] + f.n[2] - 2;
-  for (int s = 0; s < waves; s++) {
-    // rows i <= s only
-    const long long rows = s + 1 < n0 ? s + 1 : n0;
-    const long long th = rows * n1;
-    const int g = (int)((th + kClassicThreads - 1) / kClassicThreads);
-    k_classic_wave3<<<g, kClassicThreads, 0, st>>>(f, p, s, xh, ws);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -60,7 +60,7 @@ def _fields():
     f = {}
     f["1d_ragged"] = (synth.grf_np((4097,), -2.0, 11) * 3).astype(np.float32)
     f["2d_ragged"] = (synth.grf_np((61, 58), -3.0, 12) * 50 + 7).astype(np.float32)
-    # 2D tiles of 32 x 128: several tiles with ragged tails on both axes
+    # 2D tiles of 32 x 32: several tiles with ragged tails on both axes
     f["2d_tiles"] = (synth.grf_np((100, 300), -3.0, 21) * 4).astype(np.float32)
     f["2d_flat"] = (synth.grf_np((5, 700), -2.5, 22)).astype(np.float32)
     f["2d_tall"] = (synth.grf_np((300, 7), -2.5, 23)).astype(np.float32)
@@ -68,6 +68,8 @@ def _fields():
     f["3d_tiles"] = synth.config2_field(seed=14, shape=(24, 40, 44))
     f["3d_noise"] = rng.standard_normal((12, 16, 20)).astype(np.float32)
     f["3d_thin"] = (synth.grf_np((1, 40, 33), -3.0, 24)).astype(np.float32)
+    # 3D tiles of one plane x 32 x 32: several in rows and columns, ragged
+    f["3d_multi_tile"] = (synth.grf_np((3, 70, 260), -3.0, 25) * 9).astype(np.float32)
     fill = synth.grf_np((48, 64), -3.0, 15)
     f["2d_fill"] = synth.fill_region_np(fill, seed=16)
     return f
@@ -107,7 +109,8 @@ def test_classic_matches_oracle(R, ctx, name, rel_eb, radius):
         assert o["sz_nesc_gt"] > 0  # the radius forces escapes
 
 
-@pytest.mark.parametrize("shape", [(1,), (3,), (2, 3), (1, 1, 5), (5, 1, 1), (4, 4, 4), (33, 129)])
+@pytest.mark.parametrize("shape", [(1,), (3,), (2, 3), (1, 1, 5), (5, 1, 1), (4, 4, 4), (33, 129),
+                                   (2, 33, 129), (4, 1, 300), (3, 300, 1)])
 def test_classic_tiny_and_edge_shapes(R, ctx, shape):
     rng = np.random.default_rng(sum(shape))
     x = rng.standard_normal(shape).astype(np.float32)
@@ -139,7 +142,7 @@ def test_classic_host_field_and_repeats(R, ctx):
     gp = _gp(R, op)
     first = ctx.ground_truth_classic(x, gp, 0.01)
     xd = torch.from_numpy(x).cuda()
-    waves = -(-100 // 32) + -(-300 // 128) - 1
+    waves = -(-100 // 32) + -(-300 // 32) - 1
     outs = []
     for _ in range(3):
         n0 = ctx.launch_count()
