@@ -333,7 +333,12 @@ def bench_classic(R, ctx, x, stream, reps: int = 3):
         p = R.params(eb=EB_REL, r_sp=R_SP)
         ms_c, tc = timed(lambda: ctx.ground_truth_classic(f, p, eb_sz, stream=stream))
         ms_d, td = timed(lambda: ctx.ground_truth(f, p, eb_sz, stream))
+        # the sampled estimate at the same bin: entropy + 0.5 (the paper's
+        # offset) against the classic stream's bit-rate
+        e = ctx.estimate_sz(f, p, 2.0 * eb_sz, stream)
         res[name] = {"eb_sz": eb_sz, "ms_classic": ms_c, "ms_prequantised": ms_d,
+                     "entropy_est": e["entropy"], "br_sz_est": e["br_sz"],
+                     "br_sz_huff_est": e["br_sz_huff"],
                      "br_sz_classic": tc["br_sz_gt"], "br_sz_prequantised": td["br_sz_gt"],
                      "psnr_classic": tc["psnr_sz_gt"], "psnr_prequantised": td["psnr_sz_gt"],
                      "nesc_classic": tc["sz_nesc_gt"], "nesc_prequantised": td["sz_nesc_gt"]}
