@@ -643,6 +643,8 @@ int ensure_batch_capacity(rd_context* c, int n) {
             cudaMallocHost(&c->h_bres, (size_t)n * sizeof(rd_result)) == cudaSuccess &&
             cudaMallocHost(&c->h_btruth, (size_t)n * sizeof(rd_truth)) == cudaSuccess &&
             cudaMallocHost(&c->h_bstatus, (size_t)n * sizeof(int32_t)) == cudaSuccess;
+  // zeroed once: every table clean (the batched passes keep them so)
+  if (ok) ok = cudaMemset(c->bws, 0, (size_t)n * sizeof(Workspace)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     free_batch_buffers(c);

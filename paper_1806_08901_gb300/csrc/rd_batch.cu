@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(kBatchRangeThreads) k_batch_range(const BatchF
     if (s_last && threadIdx.x == 0) {
       __threadfence();
       prepare_field(F.p, F.ws);
+      F.ws->sc.clean = 0u;  // the histogram pass writes the tables from here on
     }
     __syncthreads();
   }

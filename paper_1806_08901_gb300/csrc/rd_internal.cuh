@@ -28,7 +28,9 @@ struct Scalars {
   uint32_t flags;        // RD_F_*
   int32_t constant;      // value range is zero
   int32_t minexp;        // floor(log2 eb_abs)
-  uint32_t min_key, max_key, nonfinite, pad0;
+  uint32_t min_key, max_key, nonfinite;
+  uint32_t clean;        // batched estimate: kCleanTables while hist[0], count_of[0] and
+                         // present[0] are all zero (the passes that read them clear them)
   uint32_t done[2];       // batched passes: range / ZFP work items finished (last-CTA detection)
   float vmin, vmax, amax;  // amax = max(|vmin|, |vmax|)
   float w, inv, tau;       // SZ quantiser: bin, 1/bin, escape threshold
@@ -40,6 +42,8 @@ struct Scalars {
   unsigned long long mse_lo[kMseBins];  // 128-bit sums of d^2 per exponent
   unsigned long long mse_hi[kMseBins];
 };
+
+constexpr uint32_t kCleanTables = 0x6c65616eu;
 
 struct HuffOut {
   unsigned long long ns;    // total count

@@ -329,6 +329,9 @@ cudaError_t launch_init_tables(double* xlogx, cudaStream_t s) {
 // count values present, and the counts of 2^16 or more (at most N / 2^16 of
 // them) appended to a list, with their share c log2 c of the entropy sum.
 // ---------------------------------------------------------------------------
+// With kClear, every nonzero bin read is set back to zero, except bin 0 (the
+// escape count, read by the finish step).
+template <bool kClear>
 __device__ __forceinline__ void code_prep_slice(Workspace* ws, int which, int slice) {
   __shared__ double part[kPrepThreads / 32];
   if (ws->sc.status != RD_OK || ws->sc.constant) return;
@@ -340,7 +343,9 @@ __device__ __forceinline__ void code_prep_slice(Workspace* ws, int which, int sl
   double v = 0.0;
 #pragma unroll
   for (int k = 0; k < 1024 / kPrepThreads; k++) {
-    const uint32_t c = ws->hist[which][slice * 1024 + k * kPrepThreads + threadIdx.x];
+    const int bin = slice * 1024 + k * kPrepThreads + threadIdx.x;
+    const uint32_t c = ws->hist[which][bin];
+    if (kClear && c != 0u && bin != 0) ws->hist[which][bin] = 0u;
     const bool small = c != 0u && c < (uint32_t)kNsym;
     const bool large = c >= (uint32_t)kNsym;
     const unsigned ms = __ballot_sync(0xffffffffu, small);
@@ -373,7 +378,7 @@ __device__ __forceinline__ void code_prep_slice(Workspace* ws, int which, int sl
 
 __global__ void __launch_bounds__(kPrepThreads) k_code_prep(Workspace* ws, int which_mask) {
   const int first = (which_mask & 1) ? 0 : 1;
-  code_prep_slice(ws, first + blockIdx.x / kEntropyCtas, blockIdx.x % kEntropyCtas);
+  code_prep_slice<false>(ws, first + blockIdx.x / kEntropyCtas, blockIdx.x % kEntropyCtas);
 }
 
 // Block-wide scans and sums for kHuffThreads threads (32 warps); s_w holds
@@ -941,18 +946,25 @@ cudaError_t launch_finish(const ParamsDev& p, Workspace* ws, int passes, int zfp
 // then the rates, PSNRs and selection; the field's record and status are
 // gathered).
 // ---------------------------------------------------------------------------
+// The estimate's tables (hist[0], count_of[0], present[0]) are cleared only
+// when the call before left them dirty: the batched passes that read them
+// clear what they read (code prep: the histogram; the final pass: the
+// count-of-counts and the bitmap), and the final pass marks them clean.
 __global__ void k_batch_reset(const BatchField* __restrict__ bf, int need_gt) {
   const BatchField& F = bf[blockIdx.x];
-  reset_ws(F.ws, blockIdx.y * blockDim.x + threadIdx.x, gridDim.y * blockDim.x, need_gt ? 3 : 1);
+  const int est = F.ws->sc.clean == kCleanTables ? 0 : 1;
+  reset_ws(F.ws, threadIdx.x, blockDim.x, est | (need_gt ? 2 : 0));
 }
 
 cudaError_t launch_batch_reset(const BatchField* bf, int n, int need_gt, cudaStream_t s) {
-  k_batch_reset<<<dim3(n, 8), 256, 0, s>>>(bf, need_gt);
+  // one CTA per field: with clean tables only the scalars and the exponent
+  // bins are left to clear
+  k_batch_reset<<<n, 1024, 0, s>>>(bf, need_gt);
   return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(kPrepThreads) k_batch_code_prep(const BatchField* __restrict__ bf) {
-  code_prep_slice(bf[blockIdx.x / kEntropyCtas].ws, 0, blockIdx.x % kEntropyCtas);
+  code_prep_slice<true>(bf[blockIdx.x / kEntropyCtas].ws, 0, blockIdx.x % kEntropyCtas);
 }
 
 cudaError_t launch_batch_code_prep(const BatchField* bf, int n, cudaStream_t s) {
@@ -974,6 +986,24 @@ __global__ void __launch_bounds__(kHuffThreads) k_batch_final(const BatchField* 
   uint32_t* dst = reinterpret_cast<uint32_t*>(&res[blockIdx.x]);
   for (int i = threadIdx.x; i < (int)(sizeof(rd_result) / 4); i += blockDim.x) dst[i] = src[i];
   if (threadIdx.x == 0) status[blockIdx.x] = ws->sc.status;
+  // leave the tables zero for the next call: the count-of-counts entries of
+  // the present values, the bitmap and the escape bin (code prep cleared the
+  // other bins); a field that stopped early is left for the reset to clear
+  const bool used = ws->sc.status == RD_OK && !ws->sc.constant;  // uniform over the CTA
+  __syncthreads();
+  if (used) {
+    uint32_t* cc = ws->count_of[0];
+    uint32_t* pr = ws->present[0];
+    for (int i = threadIdx.x; i < kNsym / 32; i += blockDim.x) {
+      const uint32_t word = pr[i];
+      if (!word) continue;
+      for (uint32_t b = word; b; b &= b - 1u) cc[32 * i + __ffs(b) - 1] = 0u;
+      pr[i] = 0u;
+    }
+    if (threadIdx.x == 0) ws->hist[0][0] = 0u;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) ws->sc.clean = used ? kCleanTables : 0u;
 }
 
 cudaError_t launch_batch_final(const BatchField* bf, int n, const double* xlogx, rd_result* res,

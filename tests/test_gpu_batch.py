@@ -184,6 +184,30 @@ def test_failing_field_fails_alone(R, ctx, dev_fields, singles):
         assert res[i] == singles[i], i
 
 
+def test_workspaces_reused_across_batches(R, ctx, dev_fields, singles):
+    """The per-field tables are cleared by the passes that read them and
+    fully only after a field stopped early: batches that reuse the same
+    workspaces with other fields, after a failing field and after a
+    constant one, give the per-field records."""
+    ps = _params(R)
+    bad = torch.from_numpy(FIELDS[2].copy()).cuda()
+    bad[5, 7] = float("nan")
+    const = torch.full((40, 50), 3.0, dtype=torch.float32, device="cuda")
+    rounds = [
+        ([dev_fields[0], dev_fields[1], bad, dev_fields[3]], [0, 1, None, 3]),
+        ([dev_fields[0], dev_fields[1], dev_fields[2], dev_fields[3]], [0, 1, 2, 3]),
+        ([dev_fields[4], const, dev_fields[6], dev_fields[7]], [4, None, 6, 7]),
+        ([dev_fields[5], dev_fields[2], dev_fields[7], dev_fields[4]], [5, 2, 7, 4]),
+        ([dev_fields[0], dev_fields[1], dev_fields[2], dev_fields[3]], [0, 1, 2, 3]),
+    ]
+    for fs, idx in rounds:
+        pp = [ps[i] if i is not None else ps[0] for i in idx]
+        res, _, st = ctx.select_batch(fs, pp, check=False)
+        for k, i in enumerate(idx):
+            if i is not None:
+                assert st[k] == 0 and res[k] == singles[i], (idx, k)
+
+
 def test_host_fields_are_rejected(R, ctx):
     with pytest.raises(R.RdselError) as ei:
         ctx.select_batch([FIELDS[1]], R.params())
