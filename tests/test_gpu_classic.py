@@ -4,9 +4,12 @@ point-by-point walk in storage order.
 
 Codes, histogram, escapes, Huffman cost, stream bits and every
 reconstructed value must match bit for bit: both sides take each decision
-in float32 with the same operation order.  SSE is summed in a different
-order (relative 1e-12); the GPU keeps the largest error as a float32
-(relative 2^-24); PSNR within 1e-6 relative.
+in float32 with the same operation order.  SSE: both sides sum the same
+exactly computed float64 squares, the oracle in storage order and the GPU
+in a fixed per-CTA order, so they differ by rounding order only: at most
+the recursive-summation bound (N - 1) u relative (u = 2^-53) on the
+oracle's side, taken here as max(1e-12, N 2^-52).  The GPU keeps the
+largest error as a float32 (relative 2^-24); PSNR within 1e-6 relative.
 """
 import math
 
@@ -21,7 +24,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 REL_PSNR = 1e-6
-REL_SSE = 1e-12
+REL_SSE = 1e-12  # floor of the summation-order bound, see rel_sse()
 REL_MAXERR = 2.0 ** -24
 EXACT = ["delta", "eb_sz", "sz_huff_gt", "sz_nsym_gt", "sz_nesc_gt", "sz_bits_gt", "br_sz_gt",
          "flags"]
@@ -78,6 +81,10 @@ def _fields():
 FIELDS = _fields()
 
 
+def rel_sse(n):
+    return max(REL_SSE, n * 2.0 ** -52)
+
+
 def check(R, ctx, x, op, eb_sz):
     xd = torch.from_numpy(x).cuda()
     rec = torch.empty_like(xd)
@@ -86,7 +93,7 @@ def check(R, ctx, x, op, eb_sz):
     for k in EXACT:
         assert g[k] == o[k], (k, g[k], o[k])
     assert _rel(g["psnr_sz_gt"], o["psnr_sz_gt"]) <= REL_PSNR
-    assert _rel(g["sse_sz"], o["sse_sz"]) <= REL_SSE, (g["sse_sz"], o["sse_sz"])
+    assert _rel(g["sse_sz"], o["sse_sz"]) <= rel_sse(x.size), (g["sse_sz"], o["sse_sz"])
     assert _rel(g["maxerr_sz"], o["maxerr_sz"]) <= REL_MAXERR
     r = rec.cpu().numpy()
     if o["flags"] & R.RD_F_CONSTANT:
@@ -184,3 +191,17 @@ def test_classic_against_dual_quantization_truth(R, ctx):
     assert gc["delta"] == gd["delta"]
     assert gc["maxerr_sz"] <= eb_sz and gd["maxerr_sz"] <= eb_sz
     assert 0.5 <= gc["sz_bits_gt"] / gd["sz_bits_gt"] <= 2.0
+
+
+@pytest.mark.parametrize("kind", ["hurricane_100x500x500", "atm_1800x3600_fill"])
+def test_classic_full_size_fields(R, ctx, kind):
+    """The workload sizes of the bench: every code decision and reconstructed
+    value of the 25M-point 3D field and of a 6.5M-point 2D field with a
+    1e-20 fill region, against the oracle's sequential walk."""
+    if kind.startswith("hurricane"):
+        x = synth.config2_field()
+    else:
+        g = synth.grf_np((1800, 3600), -3.0, 41)
+        x = synth.fill_region_np(g, seed=42)
+    vr = float(x.max()) - float(x.min())
+    check(R, ctx, x, O.params(eb=1e-4), 1e-4 * vr)
