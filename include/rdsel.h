@@ -175,7 +175,9 @@ int32_t rd_ground_truth(rd_context* ctx, const rd_field* field,
  *  - eb_sz: the absolute bound, > 0 and finite (else RD_ERR_INVALID_ARG).
  *  - Fills the SZ fields of *out (delta = 2 eb_sz, eb_sz, sz_huff_gt,
  *    sz_nsym_gt, sz_nesc_gt, sz_bits_gt, br_sz_gt, sse_sz, maxerr_sz,
- *    psnr_sz_gt) and flags; the ZFP fields stay 0.
+ *    psnr_sz_gt) and flags; the ZFP fields stay 0.  A constant field has
+ *    nothing to quantise: flags RD_F_CONSTANT, psnr_sz_gt = +inf, every
+ *    other field 0.
  *  - recon: NULL, or DEVICE memory for N floats (caller-owned, the field's
  *    row-major order) that receives the reconstruction a decompressor
  *    would produce (for a constant field: the field itself).
@@ -184,8 +186,12 @@ int32_t rd_ground_truth(rd_context* ctx, const rd_field* field,
  *    tiles, plane + row tile + column tile = w), so the call is far slower than
  *    rd_ground_truth.  The context keeps an N-float reconstruction buffer,
  *    counted against its memory budget (RD_ERR_BUDGET when it would not fit).
- *  - Results are bit-identical for codes, histogram, escapes and bits; the
- *    SSE differs from a sequential sum by rounding order only. */
+ *  - Codes, histogram, escapes, bits and the reconstruction do not depend
+ *    on the launch shape (each decision is a fixed sequence of float32
+ *    operations); the SSE is a fixed-order float64 sum, so it differs from a
+ *    sequential sum by rounding order only.
+ *  - Returns once the work on `stream` has finished (the call synchronises
+ *    it). */
 int32_t rd_ground_truth_classic(rd_context* ctx, const rd_field* field,
                                 const rd_params* params, double eb_sz,
                                 rd_truth* out, float* recon, void* stream);
