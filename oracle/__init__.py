@@ -135,6 +135,9 @@ def lib():
             "rdo_mse_numerator": [i32p, i64p, C.c_int64, P(C.c_double)],
             "rdo_classic_sz": [f32p, C.c_int, i64p, P(Params), C.c_double, P(Truth), u32p, i32p,
                                f32p],
+            "rdo_sz_stream_encode": [i32p, f32p, C.c_int64, P(C.c_uint8), C.c_uint64, u64p],
+            "rdo_sz_stream_decode": [P(C.c_uint8), C.c_uint64, C.c_int64, i32p, u32p, C.c_uint64,
+                                     u64p],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -319,6 +322,39 @@ def sz_symbols(x: np.ndarray, delta: float, quant_radius: int = 32768, strides=N
     if rc:
         raise OracleError(rc, "rdo_sz_symbols")
     return {"est": est.reshape(x.shape), "gt": gt.reshape(x.shape), "recon": rec.reshape(x.shape)}
+
+
+def sz_stream(sym: np.ndarray, x: np.ndarray):
+    """The SZ stream of the symbols sym (0 = escape: x stored as its 32-bit
+    pattern), as the ground-truth bit counts cost it.  Returns (bytes, nbits)."""
+    sym = np.ascontiguousarray(sym, dtype=np.int32).ravel()
+    x = np.ascontiguousarray(x, dtype=np.float32).ravel()
+    if sym.size != x.size:
+        raise ValueError("one value per symbol")
+    nbits = C.c_uint64(0)
+    rc = lib().rdo_sz_stream_encode(_ptr(sym, C.c_int32), _ptr(x, C.c_float), sym.size, None, 0,
+                                    C.byref(nbits))
+    if rc:
+        raise OracleError(rc, "rdo_sz_stream_encode")
+    buf = np.zeros((nbits.value + 7) // 8, dtype=np.uint8)
+    rc = lib().rdo_sz_stream_encode(_ptr(sym, C.c_int32), _ptr(x, C.c_float), sym.size,
+                                    _ptr(buf, C.c_uint8), buf.size, C.byref(nbits))
+    if rc:
+        raise OracleError(rc, "rdo_sz_stream_encode")
+    return buf.tobytes(), nbits.value
+
+
+def sz_stream_decode(data: bytes, nbits: int, n: int):
+    """Symbols and escaped values (float32) read back from an SZ stream."""
+    buf = np.frombuffer(data, dtype=np.uint8).copy()
+    sym = np.zeros(n, np.int32)
+    esc = np.zeros(max(n, 1), np.uint32)
+    ne = C.c_uint64(0)
+    rc = lib().rdo_sz_stream_decode(_ptr(buf, C.c_uint8), int(nbits), int(n), _ptr(sym, C.c_int32),
+                                    _ptr(esc, C.c_uint32), esc.size, C.byref(ne))
+    if rc:
+        raise OracleError(rc, "rdo_sz_stream_decode")
+    return sym, esc[: ne.value].view(np.float32)
 
 
 def zfp_block(v: np.ndarray, ndim: int, minexp: int, ec_mode: int = EC_PAPER) -> dict:

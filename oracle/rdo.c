@@ -1259,3 +1259,266 @@ int rdo_classic_sz(const float* x, int ndim, const int64_t* shape, const rdo_par
   free(h);
   return RDO_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* SZ stream (the stream the ground-truth bit counts cost, readings 13 and  */
+/* 15 of the design notes: Huffman payload + 32 bits per escape + 22 bits   */
+/* per table entry + a 64-bit header).  Layout, bits written MSB first:     */
+/*   header   K (32 bits), number of escapes (32 bits)                      */
+/*   table    K entries in ascending symbol order: symbol (16), length (6)  */
+/*   payload  the canonical Huffman code of every point's symbol, in order */
+/*   escapes  the 32-bit pattern of every escaped value (symbol 0), in order*/
+/* Code lengths are the leaf depths of a Huffman tree built with a binary   */
+/* heap of (weight, node) pairs -- not the two-queue merge that computes    */
+/* the cost -- so that the payload length pins that cost.  One symbol alone */
+/* gets length 1 (the cost model's one bit per occurrence).                 */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  uint64_t w;
+  int32_t node;
+} heap_item;
+
+static int heap_less(const heap_item* a, const heap_item* b) {
+  return a->w < b->w || (a->w == b->w && a->node < b->node);
+}
+
+static void heap_push(heap_item* h, int64_t* n, heap_item v) {
+  int64_t i = (*n)++;
+  h[i] = v;
+  while (i > 0) {
+    int64_t p = (i - 1) / 2;
+    if (!heap_less(&h[i], &h[p])) break;
+    heap_item t = h[i];
+    h[i] = h[p];
+    h[p] = t;
+    i = p;
+  }
+}
+
+static heap_item heap_pop(heap_item* h, int64_t* n) {
+  heap_item top = h[0];
+  h[0] = h[--(*n)];
+  int64_t i = 0;
+  for (;;) {
+    int64_t l = 2 * i + 1, r = l + 1, m = i;
+    if (l < *n && heap_less(&h[l], &h[m])) m = l;
+    if (r < *n && heap_less(&h[r], &h[m])) m = r;
+    if (m == i) break;
+    heap_item t = h[i];
+    h[i] = h[m];
+    h[m] = t;
+    i = m;
+  }
+  return top;
+}
+
+/* len[s] for every symbol with h[s] > 0 (0 elsewhere); returns K, or -1 on
+ * allocation failure or a length above 63 (the table's 6-bit field). */
+static int64_t huffman_lengths(const uint32_t* h, uint8_t* len) {
+  int64_t K = 0;
+  for (int s = 0; s < RDO_NSYM; s++) {
+    len[s] = 0;
+    if (h[s]) K++;
+  }
+  if (K == 0) return 0;
+  if (K == 1) {
+    for (int s = 0; s < RDO_NSYM; s++)
+      if (h[s]) len[s] = 1;
+    return 1;
+  }
+  /* nodes 0..K-1 are leaves (symbol in leaf_sym), K..2K-2 internal */
+  int32_t* parent = (int32_t*)malloc((size_t)(2 * K) * sizeof(int32_t));
+  int32_t* leaf_sym = (int32_t*)malloc((size_t)K * sizeof(int32_t));
+  heap_item* heap = (heap_item*)malloc((size_t)K * sizeof(heap_item));
+  if (!parent || !leaf_sym || !heap) {
+    free(parent);
+    free(leaf_sym);
+    free(heap);
+    return -1;
+  }
+  int64_t hn = 0, k = 0;
+  for (int s = 0; s < RDO_NSYM; s++) {
+    if (!h[s]) continue;
+    leaf_sym[k] = s;
+    heap_item it = {h[s], (int32_t)k};
+    heap_push(heap, &hn, it);
+    k++;
+  }
+  int32_t next = (int32_t)K;
+  while (hn > 1) {
+    heap_item a = heap_pop(heap, &hn), b = heap_pop(heap, &hn);
+    parent[a.node] = next;
+    parent[b.node] = next;
+    heap_item c = {a.w + b.w, next};
+    heap_push(heap, &hn, c);
+    next++;
+  }
+  parent[next - 1] = -1; /* the root */
+  int ok = 1;
+  for (int64_t i = 0; i < K; i++) {
+    int d = 0;
+    for (int32_t v = (int32_t)i; parent[v] >= 0; v = parent[v]) d++;
+    if (d > 63) ok = 0;
+    len[leaf_sym[i]] = (uint8_t)d;
+  }
+  free(parent);
+  free(leaf_sym);
+  free(heap);
+  return ok ? K : -1;
+}
+
+/* Canonical codes: symbols in ascending (length, symbol) order take
+ * consecutive code values, shifted left whenever the length grows. */
+static void canonical_codes(const uint8_t* len, uint64_t* code) {
+  uint64_t c = 0;
+  int prev = 0, first = 1;
+  for (int L = 1; L <= 63; L++) {
+    for (int s = 0; s < RDO_NSYM; s++) {
+      if (len[s] != L) continue;
+      if (first) {
+        c = 0;
+        first = 0;
+      } else {
+        c = (c + 1) << (L - prev);
+      }
+      prev = L;
+      code[s] = c;
+    }
+  }
+}
+
+typedef struct {
+  uint8_t* buf;
+  uint64_t cap_bits, pos;
+} bit_writer;
+
+static void put_bits(bit_writer* w, uint64_t v, int nb) {
+  for (int i = nb - 1; i >= 0; i--) {
+    if (w->buf && w->pos < w->cap_bits) {
+      uint8_t bit = (uint8_t)((v >> i) & 1u);
+      w->buf[w->pos >> 3] |= (uint8_t)(bit << (7 - (w->pos & 7)));
+    }
+    w->pos++;
+  }
+}
+
+int rdo_sz_stream_encode(const int32_t* sym, const float* x, int64_t n, uint8_t* out,
+                         uint64_t cap_bytes, uint64_t* nbits) {
+  if (!sym || !x || n < 0 || !nbits) return RDO_ERR_INVALID_ARG;
+  uint32_t* h = (uint32_t*)calloc(RDO_NSYM, sizeof(uint32_t));
+  uint8_t* len = (uint8_t*)malloc(RDO_NSYM);
+  uint64_t* code = (uint64_t*)calloc(RDO_NSYM, sizeof(uint64_t));
+  if (!h || !len || !code) {
+    free(h);
+    free(len);
+    free(code);
+    return RDO_ERR_INVALID_ARG;
+  }
+  int rc = RDO_OK;
+  uint32_t nesc = 0;
+  for (int64_t i = 0; i < n; i++) {
+    if (sym[i] < 0 || sym[i] >= RDO_NSYM) {
+      rc = RDO_ERR_INVALID_ARG;
+      break;
+    }
+    h[sym[i]]++;
+    if (sym[i] == 0) nesc++;
+  }
+  int64_t K = rc ? 0 : huffman_lengths(h, len);
+  if (K < 0) rc = RDO_ERR_RANGE;
+  if (rc == RDO_OK) {
+    canonical_codes(len, code);
+    if (out) memset(out, 0, (size_t)cap_bytes);
+    bit_writer w = {out, out ? cap_bytes * 8u : 0u, 0u};
+    put_bits(&w, (uint64_t)K, 32);
+    put_bits(&w, nesc, 32);
+    for (int s = 0; s < RDO_NSYM; s++) {
+      if (!h[s]) continue;
+      put_bits(&w, (uint64_t)s, 16);
+      put_bits(&w, len[s], 6);
+    }
+    for (int64_t i = 0; i < n; i++) put_bits(&w, code[sym[i]], len[sym[i]]);
+    for (int64_t i = 0; i < n; i++) {
+      if (sym[i] != 0) continue;
+      uint32_t b;
+      memcpy(&b, &x[i], sizeof(b));
+      put_bits(&w, b, 32);
+    }
+    *nbits = w.pos;
+    if (out && w.pos > w.cap_bits) rc = RDO_ERR_RANGE; /* buffer too small */
+  }
+  free(h);
+  free(len);
+  free(code);
+  return rc;
+}
+
+static int get_bits(const uint8_t* buf, uint64_t nbits, uint64_t* pos, int nb, uint64_t* v) {
+  if (*pos + (uint64_t)nb > nbits) return 0;
+  uint64_t r = 0;
+  for (int i = 0; i < nb; i++, (*pos)++) r = (r << 1) | ((buf[*pos >> 3] >> (7 - (*pos & 7))) & 1u);
+  *v = r;
+  return 1;
+}
+
+/* Reads a stream of n symbols back: sym[n], and the escaped values' bit
+ * patterns into esc[] (capacity esc_cap; *n_esc their number).  Returns
+ * RDO_ERR_INVALID_ARG for a stream that does not parse or has bits left. */
+int rdo_sz_stream_decode(const uint8_t* in, uint64_t nbits, int64_t n, int32_t* sym,
+                         uint32_t* esc, uint64_t esc_cap, uint64_t* n_esc) {
+  if (!in || !sym || n < 0 || !n_esc) return RDO_ERR_INVALID_ARG;
+  uint64_t pos = 0, K, ne, v;
+  if (!get_bits(in, nbits, &pos, 32, &K) || !get_bits(in, nbits, &pos, 32, &ne)) return RDO_ERR_INVALID_ARG;
+  if (K > RDO_NSYM || (K == 0 && n > 0)) return RDO_ERR_INVALID_ARG;
+  uint8_t* len = (uint8_t*)calloc(RDO_NSYM, 1);
+  uint64_t* code = (uint64_t*)calloc(RDO_NSYM, sizeof(uint64_t));
+  if (!len || !code) {
+    free(len);
+    free(code);
+    return RDO_ERR_INVALID_ARG;
+  }
+  int rc = RDO_OK;
+  for (uint64_t k = 0; k < K && rc == RDO_OK; k++) {
+    uint64_t s, L;
+    if (!get_bits(in, nbits, &pos, 16, &s) || !get_bits(in, nbits, &pos, 6, &L) || L == 0)
+      rc = RDO_ERR_INVALID_ARG;
+    else
+      len[s] = (uint8_t)L;
+  }
+  if (rc == RDO_OK) canonical_codes(len, code);
+  /* decode by growing the code one bit at a time and looking it up among
+   * the symbols of that length (slow and plain) */
+  for (int64_t i = 0; i < n && rc == RDO_OK; i++) {
+    uint64_t c = 0;
+    int L = 0, found = -1;
+    while (found < 0 && rc == RDO_OK) {
+      if (!get_bits(in, nbits, &pos, 1, &v) || ++L > 63) {
+        rc = RDO_ERR_INVALID_ARG;
+        break;
+      }
+      c = (c << 1) | v;
+      for (int s = 0; s < RDO_NSYM; s++)
+        if (len[s] == L && code[s] == c) {
+          found = s;
+          break;
+        }
+    }
+    if (rc == RDO_OK) sym[i] = found;
+  }
+  uint64_t cnt = 0;
+  for (int64_t i = 0; i < n && rc == RDO_OK; i++) {
+    if (sym[i] != 0) continue;
+    if (!get_bits(in, nbits, &pos, 32, &v)) {
+      rc = RDO_ERR_INVALID_ARG;
+      break;
+    }
+    if (esc && cnt < esc_cap) esc[cnt] = (uint32_t)v;
+    cnt++;
+  }
+  if (rc == RDO_OK && (cnt != ne || pos != nbits)) rc = RDO_ERR_INVALID_ARG;
+  *n_esc = cnt;
+  free(len);
+  free(code);
+  return rc;
+}

@@ -138,6 +138,16 @@ int rdo_sz_symbols(const float* x, int ndim, const int64_t* shape,
 
 int rdo_zfp_block(const float* v, int ndim, int32_t minexp, int32_t ec_mode,
                   rdo_block_out* o);
+
+/* SZ stream of n symbols (0 = escape, stored as the 32-bit pattern of x[i]):
+ * header (K, escapes: 32 bits each), table (symbol 16 + code length 6 bits
+ * per used symbol, ascending), canonical Huffman payload, escaped values.
+ * encode: *nbits = its length; out (cap_bytes, zero-filled first) may be
+ * NULL to size it.  decode: sym[n] and the escaped values' bit patterns. */
+int rdo_sz_stream_encode(const int32_t* sym, const float* x, int64_t n, uint8_t* out,
+                         uint64_t cap_bytes, uint64_t* nbits);
+int rdo_sz_stream_decode(const uint8_t* in, uint64_t nbits, int64_t n, int32_t* sym,
+                         uint32_t* esc, uint64_t esc_cap, uint64_t* n_esc);
 int rdo_huffman_cost(const uint64_t* counts, int64_t n, uint64_t* cost);
 void rdo_fwd_lift(int32_t* v4);
 void rdo_inv_lift(int32_t* v4);

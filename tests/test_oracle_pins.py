@@ -631,3 +631,108 @@ def test_classic_sz_integer_ramp_closed_form():
     h = t["hist"]
     assert h[32768] == 1 and h[32769] == 999 and h.sum() == 1000
     assert np.array_equal(t["recon"], x) and t["maxerr_sz"] == 0.0
+
+
+def _parse_table(data: bytes):
+    """Header and code-length table of an SZ stream, parsed here from the
+    bytes (independently of the oracle's decoder)."""
+    bits = np.unpackbits(np.frombuffer(data, dtype=np.uint8))
+
+    def field(pos, nb):
+        return int("".join(str(b) for b in bits[pos:pos + nb]), 2), pos + nb
+
+    K, pos = field(0, 32)
+    ne, pos = field(pos, 32)
+    table = []
+    for _ in range(K):
+        s, pos = field(pos, 16)
+        L, pos = field(pos, 6)
+        table.append((s, L))
+    return K, ne, table
+
+
+@pytest.mark.parametrize("shape,radius", [((57,), 8), ((9, 13), 8), ((5, 6, 7), 32768),
+                                          ((20, 30), 32768)])
+def test_sz_stream_carries_the_classic_truth(shape, radius):
+    """The classic truth's bit count is the length of a stream that holds
+    everything a decompressor needs: written out (header, code-length table,
+    canonical Huffman payload, escaped values), read back symbol for symbol,
+    its table a complete prefix code, and the field rebuilt from the stream
+    alone by the independent decoder."""
+    rng = np.random.default_rng(sum(shape) + radius)
+    x = np.cumsum(rng.standard_normal(shape), axis=-1).astype(np.float32)
+    eb_sz = 0.05
+    t = O.classic_sz(x, O.params(eb=1e-3, quant_radius=radius), eb_sz, want_hist=True,
+                     want_recon=True, want_sym=True)
+    data, nbits = O.sz_stream(t["sym"], x)
+    assert nbits == t["sz_bits_gt"]
+    K, ne, table = _parse_table(data)
+    assert K == t["sz_nsym_gt"] and ne == t["sz_nesc_gt"]
+    assert [s for s, _ in table] == sorted(np.nonzero(t["hist"])[0].tolist())
+    if K >= 2:
+        assert sum(2.0 ** -L for _, L in table) == 1.0  # Kraft equality: a full tree
+    # payload = sum of count x length = the two-queue Huffman cost
+    assert sum(int(t["hist"][s]) * L for s, L in table) == t["sz_huff_gt"]
+    sym, esc = O.sz_stream_decode(data, nbits, x.size)
+    assert np.array_equal(sym, t["sym"].ravel())
+    assert np.array_equal(esc.view(np.uint32), x.ravel()[sym == 0].view(np.uint32))
+    held = np.full(x.size, np.nan, np.float32)
+    held[sym == 0] = esc
+    dec = _lorenzo_decode(sym.reshape(shape), held.reshape(shape), float(np.float32(2 * eb_sz)))
+    assert np.max(np.abs(dec - t["recon"].astype(np.float64))) < 1e-4
+
+
+@pytest.mark.parametrize("shape,radius", [((64,), 32768), ((12, 17), 8), ((6, 7, 9), 32768)])
+def test_sz_stream_carries_the_prequantised_truth(shape, radius):
+    """The same for the prequantised ground truth: the stream of its symbols
+    is exactly sz_bits_gt long, and the reconstruction comes back bit for bit
+    from the stream alone (integer Lorenzo of the decoded residuals gives
+    the codes; an escape's code is that of its stored value)."""
+    rng = np.random.default_rng(len(shape) * 7 + radius)
+    x = (np.cumsum(rng.standard_normal(shape), axis=-1) * 3).astype(np.float32)
+    eb_sz = 0.04
+    p = O.params(eb=1e-3, quant_radius=radius)
+    t = O.ground_truth(x, p, eb_sz)
+    s = O.sz_symbols(x, 2 * eb_sz, quant_radius=radius)
+    data, nbits = O.sz_stream(s["gt"], x)
+    assert nbits == t["sz_bits_gt"]
+    sym, esc = O.sz_stream_decode(data, nbits, x.size)
+    assert np.array_equal(sym, s["gt"].ravel())
+    w = np.float32(2 * eb_sz)
+    inv = np.float32(1.0) / w
+    sym = sym.reshape(shape)
+    held = np.zeros(x.size, np.float32)
+    held[sym.ravel() == 0] = esc
+    held = held.reshape(shape)
+    d = x.ndim
+    Q = np.zeros(shape, dtype=np.int64)
+    rec = np.zeros(shape, dtype=np.float32)
+    for idx in np.ndindex(*shape):
+        if sym[idx] == 0:
+            Q[idx] = int(np.rint(np.float32(held[idx] * inv)))
+            rec[idx] = held[idx]
+            continue
+        pred = 0
+        for sub in range(1, 1 << d):
+            off = [(sub >> (d - 1 - k)) & 1 for k in range(d)]
+            j = tuple(i - o for i, o in zip(idx, off))
+            if min(j) >= 0:
+                pred += (1 if sum(off) % 2 else -1) * int(Q[j])
+        Q[idx] = int(sym[idx]) - 32768 + pred
+        rec[idx] = np.float32(np.float32(Q[idx]) * w)
+    assert np.array_equal(rec.view(np.uint32), s["recon"].view(np.uint32))
+
+
+def test_sz_stream_single_symbol_and_rejects_bad_streams():
+    """One symbol alone costs one bit per point (the cost model's rule);
+    a truncated stream or one with bits left over does not parse."""
+    x = np.linspace(-1, 1, 100).astype(np.float32)
+    sym = np.full(100, 32768, np.int32)
+    data, nbits = O.sz_stream(sym, x)
+    assert nbits == 64 + 22 + 100
+    got, esc = O.sz_stream_decode(data, nbits, 100)
+    assert np.array_equal(got, sym) and esc.size == 0
+    with pytest.raises(O.OracleError):
+        O.sz_stream_decode(data, nbits - 1, 100)
+    with pytest.raises(O.OracleError):
+        O.sz_stream_decode(data + b"\x00", nbits + 8, 100)
