@@ -138,6 +138,8 @@ def lib():
             "rdo_sz_stream_encode": [i32p, f32p, C.c_int64, P(C.c_uint8), C.c_uint64, u64p],
             "rdo_sz_stream_decode": [P(C.c_uint8), C.c_uint64, C.c_int64, i32p, u32p, C.c_uint64,
                                      u64p],
+            "rdo_zfp_stream_encode": [f32p, C.c_int, i64p, C.c_double, P(C.c_uint8), C.c_uint64,
+                                      u64p],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -341,6 +343,23 @@ def sz_stream(sym: np.ndarray, x: np.ndarray):
                                     _ptr(buf, C.c_uint8), buf.size, C.byref(nbits))
     if rc:
         raise OracleError(rc, "rdo_sz_stream_encode")
+    return buf.tobytes(), nbits.value
+
+
+def zfp_stream(x: np.ndarray, eb_abs: float):
+    """The fixed-accuracy ZFP stream of the field at eb_abs (the stream the
+    ZFP ground-truth bit count costs).  Returns (bytes, nbits)."""
+    x, shape = _field(x)
+    nbits = C.c_uint64(0)
+    rc = lib().rdo_zfp_stream_encode(_ptr(x, C.c_float), x.ndim, _ptr(shape, C.c_int64),
+                                     float(eb_abs), None, 0, C.byref(nbits))
+    if rc:
+        raise OracleError(rc, "rdo_zfp_stream_encode")
+    buf = np.zeros((nbits.value + 7) // 8, dtype=np.uint8)
+    rc = lib().rdo_zfp_stream_encode(_ptr(x, C.c_float), x.ndim, _ptr(shape, C.c_int64),
+                                     float(eb_abs), _ptr(buf, C.c_uint8), buf.size, C.byref(nbits))
+    if rc:
+        raise OracleError(rc, "rdo_zfp_stream_encode")
     return buf.tobytes(), nbits.value
 
 

@@ -1522,3 +1522,73 @@ int rdo_sz_stream_decode(const uint8_t* in, uint64_t nbits, int64_t n, int32_t* 
   free(code);
   return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* ZFP stream (fixed accuracy; the stream the ZFP ground-truth bit count    */
+/* costs).  Blocks in the order of rdo_zfp_blocks; per block: one bit, 0    */
+/* for a block with no coded plane (P = 0); else 1, the exponent emax + 127 */
+/* (8 bits), and the group-test embedded coding of planes 31 .. kmin of the */
+/* negabinary coefficients in sequency order, bits written as the emitter  */
+/* above decides them.  The decoder needs the field's shape and eb_abs.     */
+/* ------------------------------------------------------------------------ */
+
+static void ec_emit(const uint32_t* u, int nb, int kmin, bit_writer* w) {
+  int n = 0;
+  for (int k = 31; k >= kmin; k--) {
+    int x[64];
+    for (int j = 0; j < nb; j++) x[j] = (int)(u[j] >> k & 1u);
+    for (int j = 0; j < n; j++) put_bits(w, (uint64_t)x[j], 1); /* verbatim */
+    int pos = n;
+    while (pos < nb) {
+      int any = 0;
+      for (int j = pos; j < nb; j++) any |= x[j];
+      put_bits(w, (uint64_t)any, 1); /* group test */
+      if (!any) break;
+      while (pos < nb - 1) {
+        put_bits(w, (uint64_t)x[pos], 1);
+        if (x[pos]) break;
+        pos++;
+      }
+      pos++;
+      n = pos;
+    }
+  }
+}
+
+int rdo_zfp_stream_encode(const float* x, int ndim, const int64_t* shape, double eb_abs,
+                          uint8_t* out, uint64_t cap_bytes, uint64_t* nbits) {
+  field_t f;
+  int rc = field_init(&f, x, ndim, shape);
+  if (rc) return rc;
+  if (!(eb_abs > 0.0) || !isfinite(eb_abs) || !nbits) return RDO_ERR_INVALID_ARG;
+  int minexp = floor_log2(eb_abs);
+  int nb = 1 << (2 * f.d);
+  if (out) memset(out, 0, (size_t)cap_bytes);
+  bit_writer w = {out, out ? cap_bytes * 8u : 0u, 0u};
+  int64_t b[3] = {0, 0, 0};
+  do {
+    float v[64];
+    for (int t = 0; t < nb; t++) {
+      int64_t idx[3];
+      int tt = t;
+      for (int k = f.d - 1; k >= 0; k--) {
+        int64_t g = 4 * b[k] + (tt & 3);
+        tt >>= 2;
+        idx[k] = g < f.n[k] ? g : f.n[k] - 1;
+      }
+      v[t] = f.x[lin_index(&f, idx)];
+    }
+    rdo_block_out o;
+    rdo_zfp_block(v, f.d, minexp, RDO_EC_PAPER, &o);
+    if (o.prec == 0) {
+      put_bits(&w, 0u, 1);
+    } else {
+      put_bits(&w, 1u, 1);
+      put_bits(&w, (uint64_t)(o.emax + 127), 8);
+      ec_emit(o.coeff_nb, nb, o.kmin, &w);
+    }
+  } while (next_block(&f, b));
+  *nbits = w.pos;
+  if (out && w.pos > w.cap_bits) return RDO_ERR_RANGE;
+  return RDO_OK;
+}

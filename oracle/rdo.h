@@ -146,6 +146,11 @@ int rdo_zfp_block(const float* v, int ndim, int32_t minexp, int32_t ec_mode,
  * NULL to size it.  decode: sym[n] and the escaped values' bit patterns. */
 int rdo_sz_stream_encode(const int32_t* sym, const float* x, int64_t n, uint8_t* out,
                          uint64_t cap_bytes, uint64_t* nbits);
+/* ZFP fixed-accuracy stream of a field at eb_abs: per block (the order of
+ * rdo_zfp_blocks) a flag bit, then for coded blocks emax + 127 (8 bits) and
+ * the group-test embedded coding of the coded planes. */
+int rdo_zfp_stream_encode(const float* x, int ndim, const int64_t* shape, double eb_abs,
+                          uint8_t* out, uint64_t cap_bytes, uint64_t* nbits);
 int rdo_sz_stream_decode(const uint8_t* in, uint64_t nbits, int64_t n, int32_t* sym,
                          uint32_t* esc, uint64_t esc_cap, uint64_t* n_esc);
 int rdo_huffman_cost(const uint64_t* counts, int64_t n, uint64_t* cost);

@@ -736,3 +736,78 @@ def test_sz_stream_single_symbol_and_rejects_bad_streams():
         O.sz_stream_decode(data, nbits - 1, 100)
     with pytest.raises(O.OracleError):
         O.sz_stream_decode(data + b"\x00", nbits + 8, 100)
+
+
+def _zfp_stream_decode(data, nbits, nblocks, d, minexp):
+    """Reads a fixed-accuracy ZFP stream back, written here from the stream's
+    description: per block a flag, emax + 127 in 8 bits, then per plane from
+    31 down to kmin = 32 - P (P = clamp(emax - minexp + 2(d+1), 0, 32)) the
+    verbatim bits of the coefficients already significant and the group
+    tests: a 1 means a one follows among the rest, found by scanning bits
+    (the last coefficient's one implied).  Returns per block (emax or None,
+    the coded planes of the negabinary coefficients)."""
+    bits = np.unpackbits(np.frombuffer(data, dtype=np.uint8))[:nbits]
+    nb = 4 ** d
+    pos = 0
+
+    def rd(k=1):
+        nonlocal pos
+        v = 0
+        for _ in range(k):
+            v = (v << 1) | int(bits[pos])
+            pos += 1
+        return v
+
+    out = []
+    for _ in range(nblocks):
+        if rd() == 0:
+            out.append((None, [0] * nb))
+            continue
+        emax = rd(8) - 127
+        kmin = 32 - min(32, max(0, emax - minexp + 2 * (d + 1)))
+        u = [0] * nb
+        n = 0
+        for k in range(31, kmin - 1, -1):
+            for j in range(n):
+                u[j] |= rd() << k
+            p = n
+            while p < nb:
+                if not rd():
+                    break
+                while p < nb - 1:
+                    if rd():
+                        break
+                    p += 1
+                u[p] |= 1 << k
+                p += 1
+                n = p
+        out.append((emax, u))
+    assert pos == nbits  # nothing left over
+    return out
+
+
+@pytest.mark.parametrize("shape,eb", [((37,), 1e-3), ((13, 18), 1e-4), ((9, 10, 11), 1e-2),
+                                      ((8, 8, 8), 1e-6)])
+def test_zfp_stream_carries_the_coded_planes(shape, eb):
+    """The ZFP truth's bit count is the length of an embedded stream from
+    which a decoder written from the description recovers every block's
+    exponent and exactly the coded bit planes of its coefficients (all
+    lower planes zero), block after block to the last bit."""
+    x = (synth.grf_np(shape, -3.0, seed=len(shape) * 31) * 25.0).astype(np.float32)
+    x.ravel()[::7] = 0.0
+    p = O.params(eb=eb, r_sp=1.0)
+    r = O.select(x, p)
+    t = O.ground_truth(x, p)
+    data, nbits = O.zfp_stream(x, r["eb_abs"])
+    assert nbits == t["zfp_bits_gt"]
+    zb = O.zfp_blocks(x, r["eb_abs"], want_coeffs=True)
+    d = x.ndim
+    minexp = math.frexp(r["eb_abs"])[1] - 1  # floor(log2 eb_abs), exactly
+    dec = _zfp_stream_decode(data, nbits, len(zb["emax"]), d, minexp)
+    for b, (emax, u) in enumerate(dec):
+        if emax is None:
+            assert zb["prec"][b] == 0
+            continue
+        assert emax == zb["emax"][b]
+        keep = (0xFFFFFFFF << (32 - int(zb["prec"][b]))) & 0xFFFFFFFF
+        assert u == [int(c) & keep for c in zb["coeffs"][b]], b
