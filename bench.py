@@ -23,6 +23,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -74,11 +75,35 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+# Translation units of the kernels that profiles/ and traffic.json describe
+# (range, ZFP, SZ, Huffman and batched passes, classic truth tiles).
+PROFILED_UNITS = ("rd_reduce.cu", "rd_zfp.cu", "rd_sz.cu", "rd_sz_tma.cu", "rd_batch.cu",
+                  "rd_sz_classic.cu")
+
+
 def kernel_source_hash() -> str:
-    h = hashlib.sha256()
+    """Hash of the sources the profiled kernels are compiled from: their
+    translation units and every header they include, followed through the
+    package's own headers (the public header included)."""
     csrc = os.path.join(ROOT, "paper_1806_08901_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, fn), "rb") as f:
+    inc = os.path.join(ROOT, "include")
+    seen, todo = [], list(PROFILED_UNITS)
+    while todo:
+        fn = todo.pop(0)
+        if fn in seen:
+            continue
+        seen.append(fn)
+        path = os.path.join(csrc, fn)
+        if not os.path.exists(path):
+            path = os.path.join(inc, fn)
+        with open(path, encoding="utf-8") as f:
+            todo += re.findall(r'#include "([^"]+)"', f.read())
+    h = hashlib.sha256()
+    for fn in sorted(seen):
+        path = os.path.join(csrc, fn)
+        if not os.path.exists(path):
+            path = os.path.join(inc, fn)
+        with open(path, "rb") as f:
             h.update(fn.encode() + f.read())
     return h.hexdigest()[:16]
 

@@ -1,0 +1,60 @@
+/* rdsel_stream.h -- compressed streams of the selected compressor
+ * (Algorithm 1, the step after the selection: each field is compressed by
+ * the compressor chosen for it).  Types and error codes are those of
+ * rdsel.h.
+ */
+#ifndef RDSEL_STREAM_H
+#define RDSEL_STREAM_H
+
+#include <stdint.h>
+
+#include "rdsel.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* The SZ stream of the prequantised ground truth at the absolute bound
+ * eb_sz (the stream whose size rd_ground_truth reports as sz_bits_gt).
+ * Layout, bits most significant first within each byte:
+ *   header   K, the number of distinct symbols (32 bits); the number of
+ *            escapes (32 bits)
+ *   table    K entries in ascending symbol order: symbol (16 bits), code
+ *            length (6 bits)
+ *   payload  the canonical Huffman code of every point's symbol in the
+ *            field's row-major order (canonical: symbols in ascending
+ *            (length, symbol) order take consecutive code values)
+ *   escapes  the 32-bit pattern of every escaped value (symbol 0), in order
+ * A decoder rebuilds the field from the stream, the shape, eb_sz and
+ * quant_radius: a non-escaped point's code Q is its residual (symbol -
+ * 32768) plus the integer Lorenzo prediction from the codes of its decoded
+ * neighbours, its value float(Q) * float(2 eb_sz); an escaped point's value
+ * is the stored one and its code rint(value / w) as in the quantiser.
+ *  - field, params: as for rd_ground_truth (params->quant_radius is R).
+ *  - eb_sz > 0 and finite; a constant field has nothing to quantise
+ *    (RD_ERR_INVALID_ARG).
+ *  - out: DEVICE memory, 8-byte aligned, cap_bytes >= 8 * ceil(*nbits / 64)
+ *    (RD_ERR_RANGE otherwise); the bytes past the stream's last bit are
+ *    zero.  out = NULL: only *nbits is computed (the ground truth's bit
+ *    count), nothing is written.
+ *  - *nbits: the stream's length in bits.
+ *  - Device work: the ground truth (histogram, quantiser, status), the
+ *    per-point symbols, per-CTA sums of code lengths and escapes, one scan
+ *    over the CTAs, then each CTA writes its points' codes and escaped values
+ *    at their offsets (64-bit ORs).  The code lengths (a Huffman tree over
+ *    at most 65536 symbols) and the header are built on the host from the
+ *    device histogram.  The context keeps a scratch of 4 N bytes + 0.6 MB,
+ *    counted against its memory budget.
+ *  - Equal-weight ties in the Huffman tree may be broken either way: the
+ *    code lengths are those of one optimal code, and the payload length is
+ *    the same for every optimal code.
+ *  - Returns once the work on `stream` has finished. */
+int32_t rd_sz_compress(rd_context* ctx, const rd_field* field, const rd_params* params,
+                       double eb_sz, void* out, uint64_t cap_bytes, uint64_t* nbits,
+                       void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RDSEL_STREAM_H */

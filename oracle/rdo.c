@@ -1487,8 +1487,25 @@ int rdo_sz_stream_decode(const uint8_t* in, uint64_t nbits, int64_t n, int32_t* 
       len[s] = (uint8_t)L;
   }
   if (rc == RDO_OK) canonical_codes(len, code);
-  /* decode by growing the code one bit at a time and looking it up among
-   * the symbols of that length (slow and plain) */
+  /* the symbols of each length in ascending order hold consecutive codes
+   * from the length's smallest: a code c of length L is symbol
+   * bylen[first[L] + c - lo[L]] when c - lo[L] < nlen[L] */
+  int32_t bylen[RDO_NSYM];
+  int64_t first[64], nlen[64];
+  uint64_t lo[64];
+  int64_t m = 0;
+  for (int L = 0; L < 64; L++) {
+    first[L] = m;
+    nlen[L] = 0;
+    lo[L] = 0;
+    for (int s = 0; s < RDO_NSYM; s++)
+      if (L > 0 && len[s] == L) {
+        if (nlen[L] == 0) lo[L] = code[s];
+        bylen[m++] = s;
+        nlen[L]++;
+      }
+  }
+  /* decode by growing the code one bit at a time */
   for (int64_t i = 0; i < n && rc == RDO_OK; i++) {
     uint64_t c = 0;
     int L = 0, found = -1;
@@ -1498,11 +1515,7 @@ int rdo_sz_stream_decode(const uint8_t* in, uint64_t nbits, int64_t n, int32_t* 
         break;
       }
       c = (c << 1) | v;
-      for (int s = 0; s < RDO_NSYM; s++)
-        if (len[s] == L && code[s] == c) {
-          found = s;
-          break;
-        }
+      if (nlen[L] > 0 && c >= lo[L] && c - lo[L] < (uint64_t)nlen[L]) found = bylen[first[L] + (int64_t)(c - lo[L])];
     }
     if (rc == RDO_OK) sym[i] = found;
   }

@@ -8,11 +8,15 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
 #include <new>
+#include <queue>
 #include <utility>
 #include <vector>
 
 #include "rd_internal.cuh"
+#include "rd_sz_stream.cuh"
+#include "rdsel_stream.h"
 
 using namespace rdk;
 
@@ -114,6 +118,8 @@ struct rd_context {
   size_t staging_bytes = 0;
   float* xhat = nullptr;  // reconstruction of the classic SZ truth
   size_t xhat_bytes = 0;
+  void* enc = nullptr;  // SZ stream encoder: symbols, code table, per-CTA offsets
+  size_t enc_bytes = 0;
   int num_sms = 0;
   int range_ctas = 0;
   int zfp_ctas[4] = {0, 0, 0, 0};
@@ -1102,6 +1108,7 @@ int32_t rd_context_destroy(rd_context* c) {
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->staging) cudaFree(c->staging);
   if (c->xhat) cudaFree(c->xhat);
+  if (c->enc) cudaFree(c->enc);
   if (c->ws) cudaFree(c->ws);
   if (c->xlogx) cudaFree(c->xlogx);
   if (c->out) cudaFreeHost(c->out);
@@ -1150,6 +1157,158 @@ int32_t rd_ground_truth_classic(rd_context* c, const rd_field* f, const rd_param
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaMemcpyAsync(recon, src, n * sizeof(float), kind, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return cuda_status(e);
+}
+
+namespace {
+
+// Code lengths of an optimal prefix code for the histogram h (the leaf
+// depths of a Huffman tree merged from a min-heap of (weight, node)); one
+// symbol alone gets length 1.  Returns the number of symbols, or -1 when a
+// length would exceed 63 (the table's 6-bit field).
+long long stream_code_lengths(const std::vector<uint32_t>& h, std::vector<uint8_t>& len) {
+  len.assign(kNsym, 0);
+  std::vector<int> sym;
+  for (int s = 0; s < kNsym; s++)
+    if (h[s]) sym.push_back(s);
+  const long long K = (long long)sym.size();
+  if (K == 1) len[sym[0]] = 1;
+  if (K <= 1) return K;
+  typedef std::pair<unsigned long long, int> Item;
+  std::priority_queue<Item, std::vector<Item>, std::greater<Item>> pq;
+  std::vector<int> up((size_t)(2 * K), -1);
+  for (long long i = 0; i < K; i++) pq.push(Item(h[sym[i]], (int)i));
+  int next = (int)K;
+  while (pq.size() > 1) {
+    const Item a = pq.top();
+    pq.pop();
+    const Item b = pq.top();
+    pq.pop();
+    up[a.second] = next;
+    up[b.second] = next;
+    pq.push(Item(a.first + b.first, next++));
+  }
+  for (long long i = 0; i < K; i++) {
+    int d = 0;
+    for (int v = (int)i; up[v] >= 0; v = up[v]) d++;
+    if (d > 63) return -1;
+    len[sym[i]] = (uint8_t)d;
+  }
+  return K;
+}
+
+struct StreamBits {
+  std::vector<uint8_t> b;
+  unsigned long long pos = 0;
+  void put(unsigned long long v, int nb) {
+    for (int i = nb - 1; i >= 0; i--, pos++) {
+      if ((pos >> 3) >= b.size()) b.push_back(0);
+      b[pos >> 3] |= (uint8_t)(((v >> i) & 1ull) << (7 - (pos & 7)));
+    }
+  }
+};
+
+}  // namespace
+
+int32_t rd_sz_compress(rd_context* c, const rd_field* fld, const rd_params* prm, double eb_sz, void* out,
+                       uint64_t cap_bytes, uint64_t* nbits, void* stream) {
+  if (!c || !nbits || !(eb_sz > 0.0) || !isfinite(eb_sz)) return RD_ERR_INVALID_ARG;
+  if (out && ((uintptr_t)out & 7u)) return RD_ERR_INVALID_ARG;
+  // the prequantised truth: status checks, histogram, quantiser, bit count
+  rd_truth t;
+  int rc = run(c, fld, prm, P_SZ_GT, DELTA_FROM_EB_SZ, eb_sz, nullptr, &t, stream);
+  if (rc) return rc;
+  if (t.flags & RD_F_CONSTANT) return RD_ERR_INVALID_ARG;  // nothing to quantise
+  *nbits = t.sz_bits_gt;
+  if (!out) return RD_OK;
+  const unsigned long long words = (t.sz_bits_gt + 63ull) / 64ull;
+  if (cap_bytes < words * 8ull) return RD_ERR_RANGE;
+  CallGuard guard(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  Geometry g;
+  if ((rc = make_geometry(c, fld, nullptr, prm->r_sp, s, &g))) return rc;
+  const long long n = g.f.N;
+  std::vector<uint32_t> h(kNsym);
+  float q[3];
+  cudaError_t e = cudaMemcpy(h.data(), c->ws->hist[1], sizeof(uint32_t) * kNsym, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(q, &c->ws->sc.w, sizeof(q), cudaMemcpyDeviceToHost);  // w, inv, tau
+  if (e != cudaSuccess) return cuda_status(e);
+  std::vector<uint8_t> len;
+  const long long K = stream_code_lengths(h, len);
+  if (K < 0) return RD_ERR_RANGE;
+  unsigned long long payload = 0ull, nesc = h[0];
+  for (int v = 0; v < kNsym; v++) payload += (unsigned long long)h[v] * len[v];
+  // an optimal code's payload is the Huffman cost the truth reported
+  if ((unsigned long long)K != t.sz_nsym_gt || payload != t.sz_huff_gt || nesc != t.sz_nesc_gt)
+    return RD_ERR_CUDA;
+  // canonical codes: ascending (length, symbol) take consecutive values
+  std::vector<unsigned long long> code(kNsym, 0ull);
+  {
+    unsigned long long cv = 0ull;
+    int prev = 0;
+    bool first = true;
+    for (int L = 1; L <= 63; L++)
+      for (int v = 0; v < kNsym; v++) {
+        if (len[v] != L) continue;
+        cv = first ? 0ull : (cv + 1ull) << (L - prev);
+        first = false;
+        prev = L;
+        code[v] = cv;
+      }
+  }
+  // header and table, written here; the payload starts right after them
+  StreamBits hb;
+  hb.put((unsigned long long)K, 32);
+  hb.put(nesc, 32);
+  for (int v = 0; v < kNsym; v++)
+    if (h[v]) {
+      hb.put((unsigned long long)v, 16);
+      hb.put(len[v], 6);
+    }
+  const unsigned long long payload_base = hb.pos;
+  // device scratch: symbols, lengths, codes, per-CTA bit and escape offsets
+  const int nctas = stream_ctas(n);
+  const size_t off_len = (size_t)n * sizeof(int32_t);
+  const size_t off_code = (off_len + kNsym + 15) / 16 * 16;
+  const size_t off_cb = off_code + sizeof(unsigned long long) * kNsym;
+  const size_t off_ce = off_cb + sizeof(unsigned long long) * (size_t)nctas;
+  const size_t off_tot = (off_ce + sizeof(unsigned) * (size_t)nctas + 15) / 16 * 16;
+  const size_t bytes = off_tot + 2 * sizeof(unsigned long long);
+  if (bytes > c->enc_bytes) {
+    if (c->budget && c->held + (bytes - c->enc_bytes) > c->budget) return RD_ERR_BUDGET;
+    if (c->enc) cudaFree(c->enc);
+    c->held -= c->enc_bytes;
+    c->enc = nullptr;
+    c->enc_bytes = 0;
+    if (cudaMalloc(&c->enc, bytes) != cudaSuccess) return RD_ERR_OOM;
+    c->enc_bytes = bytes;
+    c->held += bytes;
+  }
+  unsigned char* base = static_cast<unsigned char*>(c->enc);
+  int32_t* dsym = reinterpret_cast<int32_t*>(base);
+  uint8_t* dlen = base + off_len;
+  unsigned long long* dcode = reinterpret_cast<unsigned long long*>(base + off_code);
+  unsigned long long* dcb = reinterpret_cast<unsigned long long*>(base + off_cb);
+  unsigned* dce = reinterpret_cast<unsigned*>(base + off_ce);
+  unsigned long long* dtot = reinterpret_cast<unsigned long long*>(base + off_tot);
+  e = cudaMemcpyAsync(dlen, len.data(), kNsym, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dcode, code.data(), sizeof(unsigned long long) * kNsym, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(out, 0, words * 8ull, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, hb.b.data(), hb.b.size(), cudaMemcpyHostToDevice, s);
+  // the symbols of the truth's quantiser, then the offsets
+  if (e == cudaSuccess) e = launch_sz_inspect_q(g.f, q[0], q[1], q[2], prm->quant_radius, nullptr, dsym, nullptr, 0, s);
+  if (e == cudaSuccess) e = launch_stream_count(dsym, n, dlen, dcb, dce, s);
+  if (e == cudaSuccess) e = launch_stream_scan(dcb, dce, nctas, dtot, s);
+  unsigned long long tot[2] = {0ull, 0ull};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tot, dtot, sizeof(tot), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e);
+  c->launches += 3;
+  if (tot[0] != payload || tot[1] != nesc) return RD_ERR_CUDA;  // symbols differ from the histogram
+  e = launch_stream_pack(dsym, g.f.x, n, dlen, dcode, dcb, dce, dtot, payload_base,
+                         static_cast<unsigned long long*>(out), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  c->launches += 1;
   return cuda_status(e);
 }
 

@@ -118,6 +118,8 @@ _SIGNATURES = {
                                     _P(rd_truth), C.c_void_p]),
     "rd_ground_truth_classic": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), C.c_double,
                                             _P(rd_truth), C.c_void_p, C.c_void_p]),
+    "rd_sz_compress": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), C.c_double, C.c_void_p,
+                                   C.c_uint64, _P(C.c_uint64), C.c_void_p]),
     "rd_rd_curve": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), _P(C.c_double), C.c_int32,
                                 _P(rd_rd_point), C.c_void_p]),
     "rd_evaluate": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), _P(rd_result),
@@ -315,6 +317,25 @@ def rd_ground_truth_classic(ctx, field, prm: rd_params, eb_sz: float, recon=None
     _check(lib().rd_ground_truth_classic(ctx, C.byref(f), C.byref(prm), float(eb_sz), C.byref(t),
                                          rp, _stream(stream)), "rd_ground_truth_classic")
     return _todict(t)
+
+
+def rd_sz_compress(ctx, field, prm: rd_params, eb_sz: float, out=None, stream=None) -> int:
+    """The SZ stream of the prequantised ground truth at eb_sz (layout in
+    include/rdsel_stream.h) into out, a uint8 CUDA tensor of at least
+    8 * ceil(nbits / 64) bytes (8-byte aligned); out=None only sizes it.
+    Returns the stream's length in bits."""
+    f, keep = make_field(field)
+    nbits = C.c_uint64(0)
+    ptr, cap = None, 0
+    if out is not None:
+        import torch
+        if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.uint8
+                and out.is_contiguous()):
+            raise ValueError("out must be a contiguous uint8 CUDA tensor")
+        ptr, cap = C.c_void_p(out.data_ptr()), out.numel()
+    _check(lib().rd_sz_compress(ctx, C.byref(f), C.byref(prm), float(eb_sz), ptr, cap,
+                                C.byref(nbits), _stream(stream)), "rd_sz_compress")
+    return nbits.value
 
 
 def rd_rd_curve(ctx, field, prm: rd_params, ebs, stream=None) -> list:
@@ -583,6 +604,9 @@ class Context:
 
     def ground_truth(self, x, p, eb_sz=0.0, stream=None):
         return rd_ground_truth(self.h, x, p, eb_sz, stream)
+
+    def sz_compress(self, x, p, eb_sz, out=None, stream=None):
+        return rd_sz_compress(self.h, x, p, eb_sz, out, stream)
 
     def ground_truth_classic(self, x, p, eb_sz, recon=None, stream=None):
         return rd_ground_truth_classic(self.h, x, p, eb_sz, recon, stream)

@@ -1,4 +1,4 @@
-"""The C-ABI library loads and exports every symbol include/rdsel.h declares,
+"""The C-ABI library loads and exports every symbol include/*.h declares,
 and the binding's structs match the header's layout.  No GPU is needed: no
 test here launches a kernel."""
 import ctypes as C
@@ -23,7 +23,8 @@ def rdsel():
 
 
 def _declared_functions():
-    text = open(HEADER).read()
+    inc = os.path.join(ROOT, "include")
+    text = "".join(open(os.path.join(inc, h)).read() for h in sorted(os.listdir(inc)) if h.endswith(".h"))
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(rd_[a-z0-9_]+)\s*\(", text)))
 
