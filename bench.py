@@ -371,6 +371,34 @@ def bench_classic(R, ctx, x, stream, reps: int = 3):
     return res
 
 
+def bench_sz_stream(R, ctx, x, stream, reps: int = 5):
+    """rd_sz_compress on the benchmark field at eb_sz = EB_REL * VR: the SZ
+    stream of the prequantised truth written on the device (truth, symbols,
+    offsets, packing; the code lengths built on the host), timed with CUDA
+    events per call; its size and compression ratio."""
+    import torch
+
+    vr = float(x.max()) - float(x.min())
+    eb_sz = EB_REL * vr
+    p = R.params(eb=EB_REL, r_sp=R_SP)
+    nbits = ctx.sz_compress(x, p, eb_sz, stream=stream)
+    out = torch.empty(8 * ((nbits + 63) // 64), dtype=torch.uint8, device=x.device)
+    ctx.sz_compress(x, p, eb_sz, out, stream)
+    ms = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.sz_compress(x, p, eb_sz, out, stream)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    return {"workload": WORKLOAD, "eb_sz": eb_sz, "ms_per_call": statistics.median(ms),
+            "stream_bits": nbits, "bits_per_value": nbits / x.numel(),
+            "compression_ratio": 32.0 * x.numel() / nbits,
+            "GB_s": x.numel() * 4 / (statistics.median(ms) / 1e3) / 1e9}
+
+
 def bench_serving(R, population: int, n_req: int, rates, budget: int = 120 << 30):
     """The serving loop under Poisson arrivals: requests name fields of a
     population held in pinned host memory (2D ny ~ logU[512, 1800], nx ~
@@ -637,6 +665,7 @@ def main():
         line["rd_curve"] = bench_rd_curve(R, ctx, x, stream)
     if not args.no_classic and world == 1:
         line["classic_truth"] = bench_classic(R, ctx, x, stream)
+        line["sz_stream"] = bench_sz_stream(R, ctx, x, stream)
     if not args.no_batch and world == 1:
         line["batched"] = bench_snapshot(R, ctx, stream, args.batch_steps, peak, peak_kind,
                                          args.batch_subset)
