@@ -140,6 +140,7 @@ def lib():
                                      u64p],
             "rdo_zfp_stream_encode": [f32p, C.c_int, i64p, C.c_double, P(C.c_uint8), C.c_uint64,
                                       u64p],
+            "rdo_zfp_stream_decode": [P(C.c_uint8), C.c_uint64, C.c_int, i64p, C.c_double, f32p],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -361,6 +362,19 @@ def zfp_stream(x: np.ndarray, eb_abs: float):
     if rc:
         raise OracleError(rc, "rdo_zfp_stream_encode")
     return buf.tobytes(), nbits.value
+
+
+def zfp_stream_decode(data: bytes, nbits: int, shape, eb_abs: float) -> np.ndarray:
+    """The field a fixed-accuracy ZFP stream encodes."""
+    buf = np.frombuffer(data, dtype=np.uint8).copy()
+    shape = tuple(int(s) for s in shape)
+    sh = np.array(list(shape) + [1] * (3 - len(shape)), dtype=np.int64)
+    rec = np.zeros(shape, np.float32)
+    rc = lib().rdo_zfp_stream_decode(_ptr(buf, C.c_uint8), int(nbits), len(shape),
+                                     _ptr(sh, C.c_int64), float(eb_abs), _ptr(rec, C.c_float))
+    if rc:
+        raise OracleError(rc, "rdo_zfp_stream_decode")
+    return rec
 
 
 def sz_stream_decode(data: bytes, nbits: int, n: int):

@@ -1605,3 +1605,80 @@ int rdo_zfp_stream_encode(const float* x, int ndim, const int64_t* shape, double
   if (out && w.pos > w.cap_bits) return RDO_ERR_RANGE;
   return RDO_OK;
 }
+
+/* Reads a fixed-accuracy ZFP stream back into the field it encodes: per
+ * block the flag, the exponent and the coded planes (the group tests read
+ * as the emitter wrote them), then the block's reconstruction -- the
+ * truncated coefficients through the inverse steps of rdo_zfp_block --
+ * written to recon at the block's in-field points.  Returns
+ * RDO_ERR_INVALID_ARG for a stream that does not parse or has bits left. */
+int rdo_zfp_stream_decode(const uint8_t* in, uint64_t nbits, int ndim, const int64_t* shape,
+                          double eb_abs, float* recon) {
+  if (!in || !recon || !shape || ndim < 1 || ndim > 3) return RDO_ERR_INVALID_ARG;
+  if (!(eb_abs > 0.0) || !isfinite(eb_abs)) return RDO_ERR_INVALID_ARG;
+  field_t f;
+  int rc = field_init(&f, recon, ndim, shape); /* geometry only; recon is written */
+  if (rc) return rc;
+  const int minexp = floor_log2(eb_abs);
+  const int nb = 1 << (2 * f.d);
+  int32_t perm[64];
+  rdo_sequency(f.d, perm);
+  uint64_t pos = 0, v;
+  int64_t b[3] = {0, 0, 0};
+  do {
+    uint32_t u[64];
+    for (int j = 0; j < nb; j++) u[j] = 0u;
+    int emax = 0, coded = 0;
+    if (!get_bits(in, nbits, &pos, 1, &v)) return RDO_ERR_INVALID_ARG;
+    if (v) {
+      coded = 1;
+      if (!get_bits(in, nbits, &pos, 8, &v)) return RDO_ERR_INVALID_ARG;
+      emax = (int)v - 127;
+      int prec = emax - minexp + 2 * (f.d + 1);
+      if (prec < 0) prec = 0;
+      if (prec > 32) prec = 32;
+      const int kmin = 32 - prec;
+      int n = 0;
+      for (int k = 31; k >= kmin; k--) {
+        for (int j = 0; j < n; j++) {
+          if (!get_bits(in, nbits, &pos, 1, &v)) return RDO_ERR_INVALID_ARG;
+          u[j] |= (uint32_t)v << k;
+        }
+        int p = n;
+        while (p < nb) {
+          if (!get_bits(in, nbits, &pos, 1, &v)) return RDO_ERR_INVALID_ARG;
+          if (!v) break;
+          while (p < nb - 1) {
+            if (!get_bits(in, nbits, &pos, 1, &v)) return RDO_ERR_INVALID_ARG;
+            if (v) break;
+            p++;
+          }
+          u[p] |= 1u << k;
+          p++;
+          n = p;
+        }
+      }
+    }
+    float xr[64];
+    if (!coded) {
+      for (int t = 0; t < nb; t++) xr[t] = 0.0f;
+    } else {
+      int32_t rb[64];
+      for (int p = 0; p < nb; p++) rb[perm[p]] = rdo_nb2int(u[p]);
+      for (int a = 0; a < f.d; a++) lift_axis(rb, f.d, a, 1);
+      for (int t = 0; t < nb; t++) xr[t] = (float)ldexp((double)(float)rb[t], emax - 30);
+    }
+    for (int t = 0; t < nb; t++) {
+      int64_t idx[3];
+      int tt = t, in_field = 1;
+      for (int k = f.d - 1; k >= 0; k--) {
+        int64_t g = 4 * b[k] + (tt & 3);
+        tt >>= 2;
+        if (g >= f.n[k]) in_field = 0;
+        idx[k] = g;
+      }
+      if (in_field) recon[lin_index(&f, idx)] = xr[t];
+    }
+  } while (next_block(&f, b));
+  return pos == nbits ? RDO_OK : RDO_ERR_INVALID_ARG;
+}

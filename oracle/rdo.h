@@ -151,6 +151,10 @@ int rdo_sz_stream_encode(const int32_t* sym, const float* x, int64_t n, uint8_t*
  * the group-test embedded coding of the coded planes. */
 int rdo_zfp_stream_encode(const float* x, int ndim, const int64_t* shape, double eb_abs,
                           uint8_t* out, uint64_t cap_bytes, uint64_t* nbits);
+/* The field a ZFP stream encodes (recon: N floats), from the stream, the
+ * shape and eb_abs. */
+int rdo_zfp_stream_decode(const uint8_t* in, uint64_t nbits, int ndim, const int64_t* shape,
+                          double eb_abs, float* recon);
 int rdo_sz_stream_decode(const uint8_t* in, uint64_t nbits, int64_t n, int32_t* sym,
                          uint32_t* esc, uint64_t esc_cap, uint64_t* n_esc);
 int rdo_huffman_cost(const uint64_t* counts, int64_t n, uint64_t* cost);

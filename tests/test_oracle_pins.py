@@ -811,3 +811,23 @@ def test_zfp_stream_carries_the_coded_planes(shape, eb):
         assert emax == zb["emax"][b]
         keep = (0xFFFFFFFF << (32 - int(zb["prec"][b]))) & 0xFFFFFFFF
         assert u == [int(c) & keep for c in zb["coeffs"][b]], b
+
+
+@pytest.mark.parametrize("shape,eb", [((37,), 1e-3), ((13, 18), 1e-4), ((9, 10, 11), 1e-2),
+                                      ((20, 24, 28), 1e-5)])
+def test_zfp_stream_rebuilds_the_field_within_the_bound(shape, eb):
+    """The field read back from the ZFP stream alone is within eb_abs of the
+    original at every point, and its squared and largest errors are those
+    the ZFP ground truth reports."""
+    x = (synth.grf_np(shape, -3.0, seed=len(shape) * 17) * 25.0).astype(np.float32)
+    p = O.params(eb=eb, r_sp=1.0)
+    r = O.select(x, p)
+    t = O.ground_truth(x, p)
+    data, nbits = O.zfp_stream(x, r["eb_abs"])
+    rec = O.zfp_stream_decode(data, nbits, x.shape, r["eb_abs"])
+    e = np.abs(x.astype(np.float64) - rec.astype(np.float64))
+    assert e.max() <= r["eb_abs"]
+    assert float(e.max()) == pytest.approx(t["maxerr_zfp"], rel=2.0 ** -23)
+    assert float((e * e).sum()) == pytest.approx(t["sse_zfp"], rel=1e-12)
+    with pytest.raises(O.OracleError):
+        O.zfp_stream_decode(data, nbits - 1, x.shape, r["eb_abs"])
