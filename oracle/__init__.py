@@ -113,48 +113,52 @@ class BlockOut(C.Structure):
 _lib = None
 
 
+def load(path: str):
+    """Open a build of the oracle at `path` and declare its signatures."""
+    L = C.CDLL(path)
+    P = C.POINTER
+    f32p, i64p, i32p = P(C.c_float), P(C.c_int64), P(C.c_int32)
+    u32p, u64p = P(C.c_uint32), P(C.c_uint64)
+    sig = {
+        "rdo_select": [f32p, C.c_int, i64p, P(Params), P(Result), u32p],
+        "rdo_ground_truth": [f32p, C.c_int, i64p, P(Params), C.c_double, P(Truth), u32p],
+        "rdo_estimate_sz": [f32p, C.c_int, i64p, P(Params), C.c_double, P(Result), u32p],
+        "rdo_zfp_blocks": [f32p, C.c_int, i64p, C.c_double, i32p, i32p, u64p, u32p],
+        "rdo_sz_symbols": [f32p, C.c_int, i64p, C.c_double, C.c_int32, i32p, i32p, i32p, f32p],
+        "rdo_zfp_block": [f32p, C.c_int, C.c_int32, C.c_int32, P(BlockOut)],
+        "rdo_huffman_cost": [u64p, C.c_int64, u64p],
+        "rdo_sequency": [C.c_int, i32p],
+        "rdo_ec_positions": [C.c_int, C.c_int32, i32p, i32p],
+        "rdo_sampling": [C.c_int, i64p, C.c_double, i32p, u64p, u64p],
+        "rdo_mse_numerator": [i32p, i64p, C.c_int64, P(C.c_double)],
+        "rdo_classic_sz": [f32p, C.c_int, i64p, P(Params), C.c_double, P(Truth), u32p, i32p,
+                           f32p],
+        "rdo_sz_stream_encode": [i32p, f32p, C.c_int64, P(C.c_uint8), C.c_uint64, u64p],
+        "rdo_sz_stream_decode": [P(C.c_uint8), C.c_uint64, C.c_int64, i32p, u32p, C.c_uint64,
+                                 u64p],
+        "rdo_zfp_stream_encode": [f32p, C.c_int, i64p, C.c_double, P(C.c_uint8), C.c_uint64,
+                                  u64p],
+        "rdo_zfp_stream_decode": [P(C.c_uint8), C.c_uint64, C.c_int, i64p, C.c_double, f32p],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    L.rdo_fwd_lift.argtypes = [i32p]
+    L.rdo_fwd_lift.restype = None
+    L.rdo_inv_lift.argtypes = [i32p]
+    L.rdo_inv_lift.restype = None
+    L.rdo_int2nb.argtypes = [C.c_int32]
+    L.rdo_int2nb.restype = C.c_uint32
+    L.rdo_nb2int.argtypes = [C.c_uint32]
+    L.rdo_nb2int.restype = C.c_int32
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
-        L = C.CDLL(path)
-        P = C.POINTER
-        f32p, i64p, i32p = P(C.c_float), P(C.c_int64), P(C.c_int32)
-        u32p, u64p = P(C.c_uint32), P(C.c_uint64)
-        sig = {
-            "rdo_select": [f32p, C.c_int, i64p, P(Params), P(Result), u32p],
-            "rdo_ground_truth": [f32p, C.c_int, i64p, P(Params), C.c_double, P(Truth), u32p],
-            "rdo_estimate_sz": [f32p, C.c_int, i64p, P(Params), C.c_double, P(Result), u32p],
-            "rdo_zfp_blocks": [f32p, C.c_int, i64p, C.c_double, i32p, i32p, u64p, u32p],
-            "rdo_sz_symbols": [f32p, C.c_int, i64p, C.c_double, C.c_int32, i32p, i32p, i32p, f32p],
-            "rdo_zfp_block": [f32p, C.c_int, C.c_int32, C.c_int32, P(BlockOut)],
-            "rdo_huffman_cost": [u64p, C.c_int64, u64p],
-            "rdo_sequency": [C.c_int, i32p],
-            "rdo_ec_positions": [C.c_int, C.c_int32, i32p, i32p],
-            "rdo_sampling": [C.c_int, i64p, C.c_double, i32p, u64p, u64p],
-            "rdo_mse_numerator": [i32p, i64p, C.c_int64, P(C.c_double)],
-            "rdo_classic_sz": [f32p, C.c_int, i64p, P(Params), C.c_double, P(Truth), u32p, i32p,
-                               f32p],
-            "rdo_sz_stream_encode": [i32p, f32p, C.c_int64, P(C.c_uint8), C.c_uint64, u64p],
-            "rdo_sz_stream_decode": [P(C.c_uint8), C.c_uint64, C.c_int64, i32p, u32p, C.c_uint64,
-                                     u64p],
-            "rdo_zfp_stream_encode": [f32p, C.c_int, i64p, C.c_double, P(C.c_uint8), C.c_uint64,
-                                      u64p],
-            "rdo_zfp_stream_decode": [P(C.c_uint8), C.c_uint64, C.c_int, i64p, C.c_double, f32p],
-        }
-        for name, args in sig.items():
-            fn = getattr(L, name)
-            fn.argtypes = args
-            fn.restype = C.c_int
-        L.rdo_fwd_lift.argtypes = [i32p]
-        L.rdo_fwd_lift.restype = None
-        L.rdo_inv_lift.argtypes = [i32p]
-        L.rdo_inv_lift.restype = None
-        L.rdo_int2nb.argtypes = [C.c_int32]
-        L.rdo_int2nb.restype = C.c_uint32
-        L.rdo_nb2int.argtypes = [C.c_uint32]
-        L.rdo_nb2int.restype = C.c_int32
-        _lib = L
+        _lib = load(_build.build())
     return _lib
 
 

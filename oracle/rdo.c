@@ -11,9 +11,12 @@
  * Numerics: every floating-point step is written in the order stated here, in
  * IEEE round-to-nearest-even, with contraction disabled (-ffp-contract=off).
  * Quantisation decisions (SZ codes, escape tests) are taken in float32, the
- * precision the GPU path computes them in; sums of squared errors, value
- * range and PSNR are in float64.  Integer work (ZFP coefficients, bit counts,
- * histograms) is exact.
+ * precision of the data (the paper fixes none): the plain definition is
+ * q = floor(v / delta + 0.5), and the tests bound this evaluation against
+ * it in float64 (a code may differ by one bin, only within float32 rounding
+ * of a bin edge).  Sums of squared errors, value range and PSNR are in
+ * float64.  Integer work (ZFP coefficients, bit counts, histograms) is
+ * exact.
  *
  * Parity unpinned (no implementation to compare against): bit-compatibility
  * with zfp-0.5.0 and SZ-1.4.11 themselves.  The ZFP rules marked (Z) are
@@ -1261,9 +1264,10 @@ int rdo_classic_sz(const float* x, int ndim, const int64_t* shape, const rdo_par
 }
 
 /* ------------------------------------------------------------------------ */
-/* SZ stream (the stream the ground-truth bit counts cost, readings 13 and  */
-/* 15 of the design notes: Huffman payload + 32 bits per escape + 22 bits   */
-/* per table entry + a 64-bit header).  Layout, bits written MSB first:     */
+/* SZ stream: the stream whose size both SZ ground truths report (the      */
+/* paper does not lay out SZ's stream; this project's reading costs it as   */
+/* Huffman payload + 32 bits per escaped value + 22 bits per table entry +  */
+/* a 64-bit header).  Layout, bits written MSB first:                       */
 /*   header   K (32 bits), number of escapes (32 bits)                      */
 /*   table    K entries in ascending symbol order: symbol (16), length (6)  */
 /*   payload  the canonical Huffman code of every point's symbol, in order */

@@ -126,6 +126,24 @@ def test_zfp_transform_is_half_an_orthonormal_one():
     assert not np.allclose((2 * M) @ (2 * M).T, np.eye(4))
 
 
+def test_zfp_matrix_has_the_parametric_form_at_half_scale():
+    """2 x zfp's matrix has the row pattern of T(t) = (1/2)[[1,1,1,1],
+    [c,s,-s,-c],[1,-1,-1,1],[s,-c,c,-s]]: rows 0 and 2 are T's (row 2 up to
+    sign), rows 1 and 3 follow the (c, s) pattern with c^2 + s^2 = 26/16 and
+    40/16 instead of 2.  So one zfp step computes half a T-form coefficient,
+    and d steps 2^-d of it: the scale the MSE_sp estimate undoes before
+    Theorem 1 applies."""
+    M = [[Fraction(int(v), 16) for v in row] for row in _zfp_matrix()]
+    T2 = [[2 * v for v in row] for row in M]  # 2 x zfp = (1/2) x pattern
+    half = Fraction(1, 2)
+    assert T2[0] == [half] * 4
+    assert T2[2] == [-half, half, half, -half]
+    c, s = 2 * T2[1][0], 2 * T2[1][1]
+    assert T2[1] == [c / 2, s / 2, -s / 2, -c / 2] and c * c + s * s == Fraction(26, 16)
+    s3, c3 = 2 * T2[3][0], -2 * T2[3][1]
+    assert T2[3] == [s3 / 2, -c3 / 2, c3 / 2, -s3 / 2] and c3 * c3 + s3 * s3 == Fraction(40, 16)
+
+
 def test_bot_orthogonality_and_l2_invariance():
     """Lemma 1 / Theorem 1: T(t) T(t)^T = I for the named transforms, and
     applying T along every axis of a 4^3 block (unfold/fold) preserves the
