@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
     ap.add_argument("--no-curve", action="store_true",
                     help="skip the rate-distortion sweep (error bounds 1e-2 .. 1e-6)")
+    ap.add_argument("--no-nyx", action="store_true",
+                    help="skip the four 512^3 fields at eb_rel 1e-3 and 1e-5")
     ap.add_argument("--no-classic", action="store_true",
                     help="skip the classic SZ truth beside the prequantised one")
     ap.add_argument("--serve-population", type=int, default=64)
@@ -371,6 +373,67 @@ def bench_classic(R, ctx, x, stream, reps: int = 3):
     return res
 
 
+NYX_WORKLOAD = "nyx_512^3_density_exp2G_velocity_grf_f32"
+
+
+def bench_nyx(R, ctx, stream, peak: float, peak_kind: str, reps: int = 10):
+    """rd_evaluate (estimate + full ground truth) on the four 512^3 NYX-shaped
+    fields (log-normal density exp(2 G), three velocity GRFs) at eb_rel 1e-3
+    and 1e-5, r_sp 5%: device time per call with CUDA events (inputs of
+    512 MB, four times L2, so no flush), and the two full passes' fractions of
+    the HBM peak (one 4-byte read per value each) from their live events."""
+    import torch
+
+    import synth
+
+    fields = synth.config3_fields_torch()
+    torch.cuda.synchronize()
+    names = ("density", "vx", "vy", "vz")
+    cases = []
+    for name, x in zip(names, fields):
+        nbytes = 4 * x.numel()
+        for eb in (1e-3, 1e-5):
+            p = R.params(eb=eb, r_sp=R_SP)
+            for _ in range(3):
+                e, t = ctx.evaluate(x, p, stream)
+            ms = []
+            for _ in range(reps):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ctx.evaluate(x, p, stream)
+                b.record(stream)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+            ctx.set_profiling(True)
+            for _ in range(3):
+                ctx.evaluate(x, p, stream)
+            ctx.reset_profile()
+            for _ in range(reps):
+                ctx.evaluate(x, p, stream)
+            st = ctx.kernel_stats()
+            ctx.set_profiling(False)
+            kms = {k: v[0] / v[1] for k, v in st.items() if v[1]}
+            step = statistics.median(ms)
+            case = {"field": name, "eb_rel": eb, "ms": step,
+                    "GB_s": nbytes / (step / 1e3) / 1e9,
+                    "frac_hbm_step": 3 * nbytes / (step / 1e3) / 1e9 / peak,
+                    "kernel_ms": kms, "selection": e["selection"], "best_gt": t["best_gt"],
+                    "br_sz": e["br_sz"], "br_zfp": e["br_zfp"],
+                    "br_sz_gt": t["br_sz_gt"], "br_zfp_gt": t["br_zfp_gt"]}
+            for k in ("zfp_pass", "sz_pass", "range"):
+                if k in kms:
+                    case["frac_" + k] = nbytes / (kms[k] / 1e3) / 1e9 / peak
+            cases.append(case)
+    del fields
+    torch.cuda.empty_cache()
+    tot_ms = sum(c["ms"] for c in cases)
+    return {"workload": NYX_WORKLOAD, "r_sp": R_SP, "peak": peak, "peak_kind": peak_kind,
+            "l2": "inputs 512 MB per field, larger than L2",
+            "value": sum(4 * 512 ** 3 for _ in cases) / (tot_ms / 1e3) / 1e9, "unit": "GB/s",
+            "cases": cases}
+
+
 def bench_sz_stream(R, ctx, x, stream, reps: int = 5):
     """rd_sz_compress on the benchmark field at eb_sz = EB_REL * VR: the SZ
     stream of the prequantised truth written on the device (truth, symbols,
@@ -463,8 +526,41 @@ def bench_serving(R, population: int, n_req: int, rates, budget: int = 120 << 30
     return out
 
 
-def cpu_baseline(x_host, planes: int, steps: int = 1):
-    """Time the oracle (select + ground truth) on the first `planes` planes."""
+def host_cpu() -> dict:
+    """The host's logical core count and CPU model (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Vendor ID") and ":" in line:
+                val = line.split(":", 1)[1].strip()
+                model = val if model is None else model + " / " + val
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
+def _oracle_step(O, s, p):
+    O.select(s, p)
+    O.ground_truth(s, p)
+
+
+def cpu_baseline(x_host, planes: int, steps: int = 1, all_cores: bool = False):
+    """Time the oracle (select + ground truth) on the first `planes` planes,
+    on one core; with all_cores, also one sample per host core at once in
+    threads (the oracle releases the interpreter lock inside its C calls),
+    each thread on its own slab of planes."""
+    from concurrent.futures import ThreadPoolExecutor
+
     import oracle as O
 
     s = x_host[:planes].copy()
@@ -472,13 +568,30 @@ def cpu_baseline(x_host, planes: int, steps: int = 1):
     t = []
     for _ in range(steps):
         t0 = time.perf_counter()
-        O.select(s, p)
-        O.ground_truth(s, p)
+        _oracle_step(O, s, p)
         t.append(time.perf_counter() - t0)
     sec = statistics.mean(t)
-    return {"value": 4.0 * s.size / sec / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {planes} of {SHAPE[0]} planes ({s.size} points), "
-                      f"select + ground truth, {steps} run(s), {sec:.2f} s each"}
+    out = {"value": 4.0 * s.size / sec / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+           "sample": f"first {planes} of {SHAPE[0]} planes ({s.size} points), "
+                     f"select + ground truth, {steps} run(s), {sec:.2f} s each",
+           **host_cpu()}
+    if all_cores:
+        n = os.cpu_count() or 1
+        n0 = x_host.shape[0]
+        slabs = []
+        for i in range(n):
+            lo = (i * planes) % max(1, n0 - planes + 1)
+            slabs.append(x_host[lo:lo + planes].copy())
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(max_workers=n) as ex:
+            list(ex.map(lambda a: _oracle_step(O, a, p), slabs))
+        wall = time.perf_counter() - t0
+        tot = sum(a.size for a in slabs)
+        out["all_cores"] = {"value": 4.0 * tot / wall / 1e9, "unit": "GB/s", "cores": n,
+                            "wall_s": wall,
+                            "sample": f"{n} slabs of {planes} planes, one per thread, "
+                                      f"select + ground truth"}
+    return out
 
 
 def run_reference(args):
@@ -663,6 +776,8 @@ def main():
     }
     if not args.no_curve and world == 1:
         line["rd_curve"] = bench_rd_curve(R, ctx, x, stream)
+    if not args.no_nyx and world == 1:
+        line["nyx_512"] = bench_nyx(R, ctx, stream, peak, peak_kind)
     if not args.no_classic and world == 1:
         line["classic_truth"] = bench_classic(R, ctx, x, stream)
         line["sz_stream"] = bench_sz_stream(R, ctx, x, stream)
@@ -673,7 +788,7 @@ def main():
         rates = [float(v) for v in args.serve_rates.split(",") if v]
         line["serving"] = bench_serving(R, args.serve_population, args.serve_requests, rates)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(x.cpu().numpy(), args.cpu_planes, 1)
+        line["cpu_baseline"] = cpu_baseline(x.cpu().numpy(), args.cpu_planes, 1, all_cores=True)
     if rank == 0:
         print(json.dumps(line))
     ctx.close()

@@ -21,8 +21,9 @@
  *    reported in the `flags` word of the outputs (RD_F_*).
  *  - One context per host thread; calls on one context must not overlap.
  *  - Every numeric output equals the CPU oracle's bit for bit, except the
- *    float64 sums (PSNR, entropy, SSE) which agree to the tolerances stated
- *    in the project's design notes (PSNR within 1e-6 relative).
+ *    float64 sums, which are added in another order: PSNR within 1e-6
+ *    relative, entropy and BR_sz within 1e-10 relative, SSE within 1e-6
+ *    relative, the largest error within 2^-22 relative.
  */
 #ifndef RDSEL_H
 #define RDSEL_H
@@ -219,11 +220,16 @@ int32_t rd_evaluate(rd_context* ctx, const rd_field* field,
  *  - The first call on a device (the current device) resolves the array's
  *    device address, sizes the grids and fills a constant table in the
  *    array (one kernel on the legacy default stream, then a wait for it);
- *    make that first call before any stream capture.
+ *    make that first call before any stream capture.  The first call in a
+ *    new CUDA context of the device (after cudaDeviceReset, say) does this
+ *    set-up again, since the library's device code is loaded afresh there.
+ *  - Synchronous: the call waits for its work on `stream` and copies the
+ *    record back before it returns.
  *  - Every call shares the array and leaves its contents behind; each call
  *    clears what must start at zero.  Calls that overlap on the GPU (other
  *    streams or host threads) race on the array: serialise them.
- *  - Results equal rd_select's on the same field and parameters. */
+ *  - Results equal rd_select's on the same field and parameters (the same
+ *    kernels, lattice and record fix-up code). */
 int32_t rd_select_static(const rd_field* field, const rd_params* params,
                          rd_result* out, void* stream);
 
@@ -350,7 +356,11 @@ typedef struct {
   double p50_ms, p99_ms, mean_ms, max_ms;  /* latency of completed requests */
 } rd_server_stats;
 
-/* Start the slots.  Errors: RD_ERR_INVALID_ARG, RD_ERR_CUDA, RD_ERR_OOM. */
+/* Start the slots; returns once every slot has reported whether it could
+ * create its context and stream.  A slot that could not takes no work (and
+ * rd_server_poll then returns RD_ERR_CUDA beside the completions); when no
+ * slot could start, the server is torn down and RD_ERR_CUDA returned.
+ * Errors: RD_ERR_INVALID_ARG, RD_ERR_CUDA, RD_ERR_OOM. */
 int32_t rd_server_create(const rd_server_config* cfg, rd_server** out);
 /* Queue a request.  The field memory (host or device) must stay valid and
  * unchanged until the request completes; field_key != 0 names a host field

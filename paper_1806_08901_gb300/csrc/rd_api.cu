@@ -68,11 +68,7 @@ struct GraphEntry {
 constexpr size_t kMaxGraphs = 16;
 constexpr size_t kMaxSeen = 32;
 
-struct Geometry {
-  FieldDev f;
-  unsigned long long npoints_sampled;  // valid points of sampled blocks
-  int partial;
-};
+using Geometry = FieldGeom;
 
 // A batch of fields as planned once: device tables of fields and work items
 // for one work split, and the CUDA graph of its launches once captured.
@@ -255,72 +251,14 @@ struct CallGuard {
   }
 };
 
-int check_params(const rd_params* p) {
-  if (!p) return RD_ERR_INVALID_ARG;
-  if (!(p->eb > 0.0) || !isfinite(p->eb)) return RD_ERR_INVALID_ARG;
-  if (p->eb_mode != RD_EB_REL && p->eb_mode != RD_EB_ABS) return RD_ERR_INVALID_ARG;
-  if (p->ec_mode != RD_EC_PAPER && p->ec_mode != RD_EC_ALL) return RD_ERR_INVALID_ARG;
-  if (!(p->r_sp >= 1e-6 && p->r_sp <= 1.0)) return RD_ERR_INVALID_ARG;
-  if (p->quant_radius < 1 || p->quant_radius > 32768) return RD_ERR_INVALID_ARG;
-  if (p->sel_rule != RD_SEL_PAPER && p->sel_rule != RD_SEL_HUFFMAN) return RD_ERR_INVALID_ARG;
-  if (!isfinite(p->sz_offset)) return RD_ERR_INVALID_ARG;
-  return RD_OK;
-}
-
-ParamsDev to_dev(const rd_params* p) {
-  ParamsDev d;
-  d.eb = p->eb;
-  d.eb_mode = p->eb_mode;
-  d.ec_mode = p->ec_mode;
-  d.R = p->quant_radius;
-  d.sel_rule = p->sel_rule;
-  d.sz_offset = p->sz_offset;
-  return d;
-}
-
-// Block sampling lattice (Section "Data Sampling"): S = round(1/r_sp) is
-// factored into primes; each prime, largest first, multiplies the stride of
-// the axis with the smallest stride so far (ties: the faster axis).
-void sampling_strides(int d, double r_sp, int* s) {
-  long long S = (long long)floor(1.0 / r_sp + 0.5);
-  if (S < 1) S = 1;
-  long long f[64];
-  int nf = 0;
-  long long m = S;
-  for (long long q = 2; q * q <= m; q++)
-    while (m % q == 0) {
-      f[nf++] = q;
-      m /= q;
-    }
-  if (m > 1) f[nf++] = m;
-  for (int k = 0; k < 3; k++) s[k] = 1;
-  for (int i = nf - 1; i >= 0; i--) {
-    int a = d - 1;
-    for (int k = d - 2; k >= 0; k--)
-      if (s[k] < s[a]) a = k;
-    s[a] = (int)(s[a] * f[i]);
-  }
-}
-
 int make_geometry(rd_context* c, const rd_field* fld, const int* strides_or_null, double r_sp,
                   cudaStream_t s, Geometry* g) {
-  if (!fld || fld->ndim < 1 || fld->ndim > 3 || !fld->data) return RD_ERR_INVALID_ARG;
+  if (!fld || !fld->data) return RD_ERR_INVALID_ARG;
   if (fld->location != RD_LOC_DEVICE && fld->location != RD_LOC_HOST) return RD_ERR_INVALID_ARG;
-  FieldDev& f = g->f;
-  memset(&f, 0, sizeof(f));
-  f.d = fld->ndim;
-  long long N = 1;
-  for (int k = 0; k < 3; k++) f.n[k] = 1;
-  for (int k = 0; k < f.d; k++) {
-    if (fld->shape[k] < 1 || fld->shape[k] > 2147483647LL) return RD_ERR_INVALID_ARG;
-    f.n[k] = (int)fld->shape[k];
-    N *= fld->shape[k];
-    if (N > 2147483647LL) return RD_ERR_INVALID_ARG;
-  }
-  f.N = N;
-  const float* x = fld->data;
+  int rc = field_geometry(fld, fld->data, strides_or_null, r_sp, g);
+  if (rc) return rc;
   if (fld->location == RD_LOC_HOST) {
-    size_t bytes = (size_t)N * sizeof(float);
+    size_t bytes = (size_t)g->f.N * sizeof(float);
     if (bytes > c->staging_bytes) {
       size_t grow = bytes - c->staging_bytes;
       if (c->budget && c->held + grow > c->budget) return RD_ERR_BUDGET;
@@ -332,42 +270,13 @@ int make_geometry(rd_context* c, const rd_field* fld, const int* strides_or_null
       c->staging_bytes = bytes;
       c->held += bytes;
     }
-    cudaError_t e = cudaMemcpyAsync(c->staging, x, bytes, cudaMemcpyHostToDevice, s);
+    cudaError_t e = cudaMemcpyAsync(c->staging, fld->data, bytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return RD_ERR_CUDA;
-    x = c->staging;
-  }
-  f.x = x;
-  f.vec_ok = (((uintptr_t)x & 15u) == 0) && (f.n[f.d - 1] % 4 == 0);
-  int st[3] = {1, 1, 1};
-  if (strides_or_null) {
-    for (int k = 0; k < f.d; k++) {
-      if (strides_or_null[k] < 1) return RD_ERR_INVALID_ARG;
-      st[k] = strides_or_null[k];
-    }
-  } else {
-    sampling_strides(f.d, r_sp, st);
-  }
-  f.nblocks = 1;
-  f.nsampled = 1;
-  g->npoints_sampled = 1;
-  g->partial = 0;
-  for (int k = 0; k < f.d; k++) {
-    f.B[k] = (f.n[k] + 3) / 4;
-    f.s[k] = st[k];
-    f.L[k] = (f.B[k] + st[k] - 1) / st[k];
-    f.nblocks *= f.B[k];
-    f.nsampled *= f.L[k];
-    unsigned long long pts = 0;
-    for (int b = 0; b < f.B[k]; b += st[k]) pts += (unsigned long long)(f.n[k] - 4 * b < 4 ? f.n[k] - 4 * b : 4);
-    g->npoints_sampled *= pts;
-    if (f.n[k] % 4) g->partial = 1;
+    // the device copy: the same geometry at the staging buffer's address
+    rc = field_geometry(fld, c->staging, strides_or_null, r_sp, g);
+    if (rc) return rc;
   }
   return RD_OK;
-}
-
-int ec_count(int d, int ec_mode) {
-  if (ec_mode == RD_EC_ALL) return 1 << (2 * d);
-  return d == 1 ? 3 : d == 2 ? 9 : 16;
 }
 
 // Issue the launch sequence of one call and the copy of its result records
@@ -510,7 +419,7 @@ int run(rd_context* c, const rd_field* fld, const rd_params* prm, int passes, in
   CallKey k;
   memset(&k, 0, sizeof(k));
   k.f = g.f;
-  k.p = to_dev(prm);
+  k.p = params_dev(prm);
   k.passes = passes;
   k.delta_mode = delta_mode;
   k.delta_arg = delta_arg;
@@ -572,16 +481,7 @@ int run(rd_context* c, const rd_field* fld, const rd_params* prm, int passes, in
   }
   rd_result r = c->out->res;
   rd_truth t = c->out->truth;
-  for (int k = 0; k < d; k++) r.strides[k] = f.s[k];
-  for (int k = d; k < 3; k++) r.strides[k] = 0;
-  r.n_blocks = (uint64_t)f.nblocks;
-  if (!(r.flags & RD_F_CONSTANT)) {
-    r.n_sampled_blocks = (uint64_t)f.nsampled;
-    r.r_sp_eff = (double)f.nsampled / (double)f.nblocks;
-    r.zfp_npoints = g.npoints_sampled;
-    if (passes & P_ZFP_EST) r.zfp_ncoeff = ncoeff;
-  }
-  if (g.partial) r.flags |= RD_F_PARTIAL_BLOCKS;
+  record_geometry(&r, g, (passes & P_ZFP_EST) != 0, prm->ec_mode);
   if (est) *est = r;
   if (truth) *truth = t;
   return RD_OK;
@@ -894,7 +794,7 @@ int batch_call(rd_context* c, const rd_field* fields, const rd_params* params, i
   if (forced) put(&c->batch_force, sizeof(rd_batch_config));
   std::vector<ParamsDev> pdev((size_t)n);
   for (int i = 0; i < n; i++) {
-    pdev[i] = to_dev(&params[i]);
+    pdev[i] = params_dev(&params[i]);
     put(&geo[i].f, sizeof(FieldDev));
     put(&pdev[i], sizeof(ParamsDev));
   }
@@ -1019,17 +919,8 @@ int batch_call(rd_context* c, const rd_field* fields, const rd_params* params, i
       if (first == RD_OK) first = st;
       continue;
     }
-    const FieldDev& f = b->hbf[i].f;
     rd_result r = c->h_bres[i];
-    for (int k = 0; k < 3; k++) r.strides[k] = k < f.d ? f.s[k] : 0;
-    r.n_blocks = (uint64_t)f.nblocks;
-    if (!(r.flags & RD_F_CONSTANT)) {
-      r.n_sampled_blocks = (uint64_t)f.nsampled;
-      r.r_sp_eff = (double)f.nsampled / (double)f.nblocks;
-      r.zfp_npoints = b->hbf[i].npoints;
-      r.zfp_ncoeff = b->hbf[i].ncoeff;
-    }
-    if (b->geo[i].partial) r.flags |= RD_F_PARTIAL_BLOCKS;
+    record_geometry(&r, b->geo[i], true, b->hbf[i].p.ec_mode);
     results[i] = r;
     if (truths) truths[i] = c->h_btruth[i];
   }

@@ -4,8 +4,10 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stddef.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "rdsel.h"
 
@@ -87,6 +89,10 @@ struct FieldDev {
   long long N;          // points
   long long nblocks;    // blocks
   long long nsampled;   // sampled blocks
+  // b is a multiple of s[k] iff b == s[k] * (umulhi(b, smag[k]) >> ssh[k])
+  // for 0 <= b < 2^31 (ssh[k] < 0: s[k] == 1, every b)
+  uint32_t smag[3];
+  int32_t ssh[3];
 };
 
 struct ParamsDev {
@@ -225,6 +231,10 @@ cudaError_t prepare_sz_march();
 cudaError_t launch_sz_march(const FieldDev& f, const ParamsDev& p, int with_est, Workspace* ws,
                             int num_sms, cudaStream_t s, int* grid_used);
 int zfp_occupancy(int d, int num_sms);
+// the 3D ZFP pass, four lanes per block (launch_zfp dispatches to it)
+cudaError_t launch_zfp3(const FieldDev& f, const ParamsDev& p, int passes, const DeltaArgs& da,
+                        Workspace* ws, int ctas, cudaStream_t s, int* grid_used);
+int zfp3_occupancy(int num_sms);
 
 // ---- batched estimate (rd_select_batch) ----
 cudaError_t launch_batch_reset(const BatchField* bf, int n, int need_gt, cudaStream_t s);
@@ -251,5 +261,150 @@ cudaError_t launch_batch_truth(const BatchField* bf, int n, rd_truth* truth, int
                                cudaStream_t s);
 
 int sz_occupancy(int d, int num_sms);
+
+// ---------------------------------------------------------------------------
+// Host-side argument checks and field geometry, shared by every entry point
+// (the context calls, the batch and the static-scratch estimate), so that
+// each derives the same lattice and result fields from the same code.
+// ---------------------------------------------------------------------------
+
+inline int check_params(const rd_params* p) {
+  if (!p) return RD_ERR_INVALID_ARG;
+  if (!(p->eb > 0.0) || !isfinite(p->eb)) return RD_ERR_INVALID_ARG;
+  if (p->eb_mode != RD_EB_REL && p->eb_mode != RD_EB_ABS) return RD_ERR_INVALID_ARG;
+  if (p->ec_mode != RD_EC_PAPER && p->ec_mode != RD_EC_ALL) return RD_ERR_INVALID_ARG;
+  if (!(p->r_sp >= 1e-6 && p->r_sp <= 1.0)) return RD_ERR_INVALID_ARG;
+  if (p->quant_radius < 1 || p->quant_radius > 32768) return RD_ERR_INVALID_ARG;
+  if (p->sel_rule != RD_SEL_PAPER && p->sel_rule != RD_SEL_HUFFMAN) return RD_ERR_INVALID_ARG;
+  if (!isfinite(p->sz_offset)) return RD_ERR_INVALID_ARG;
+  return RD_OK;
+}
+
+inline ParamsDev params_dev(const rd_params* p) {
+  ParamsDev d;
+  d.eb = p->eb;
+  d.eb_mode = p->eb_mode;
+  d.ec_mode = p->ec_mode;
+  d.R = p->quant_radius;
+  d.sel_rule = p->sel_rule;
+  d.sz_offset = p->sz_offset;
+  return d;
+}
+
+// Block sampling lattice (Section "Data Sampling"): S = round(1/r_sp) is
+// factored into primes; each prime, largest first, multiplies the stride of
+// the axis with the smallest stride so far (ties: the faster axis).
+inline void sampling_strides(int d, double r_sp, int* s) {
+  long long S = (long long)floor(1.0 / r_sp + 0.5);
+  if (S < 1) S = 1;
+  long long f[64];
+  int nf = 0;
+  long long m = S;
+  for (long long q = 2; q * q <= m; q++)
+    while (m % q == 0) {
+      f[nf++] = q;
+      m /= q;
+    }
+  if (m > 1) f[nf++] = m;
+  for (int k = 0; k < 3; k++) s[k] = 1;
+  for (int i = nf - 1; i >= 0; i--) {
+    int a = d - 1;
+    for (int k = d - 2; k >= 0; k--)
+      if (s[k] < s[a]) a = k;
+    s[a] = (int)(s[a] * f[i]);
+  }
+}
+
+// EC-sampled coefficients per block: 3/9/16 for 1D/2D/3D, or all 4^d.
+inline int ec_count(int d, int ec_mode) {
+  if (ec_mode == RD_EC_ALL) return 1 << (2 * d);
+  return d == 1 ? 3 : d == 2 ? 9 : 16;
+}
+
+// Multiplier and shift that divide any 0 <= b < 2^31 by d exactly:
+// with l = ceil(log2 d) and m = floor(2^(31+l) / d) + 1 < 2^32,
+// floor(b / d) = floor(b m / 2^(31+l)) = umulhi(b, m) >> (l - 1).
+inline void stride_magic(int d, uint32_t* m, int32_t* sh) {
+  if (d <= 1) {
+    *m = 0u;
+    *sh = -1;
+    return;
+  }
+  int l = 0;
+  while ((1LL << l) < d) l++;
+  *m = (uint32_t)(((unsigned long long)1 << (31 + l)) / (unsigned long long)d + 1ull);
+  *sh = l - 1;
+}
+
+// Geometry of a field whose values are at x (device): extents (at most
+// 2^31 - 1 points), blocks, sampling strides (given, or from r_sp) and
+// the valid points of the sampled blocks.
+struct FieldGeom {
+  FieldDev f;
+  unsigned long long npoints_sampled;  // valid points of sampled blocks
+  int partial;                         // some extent is not a multiple of 4
+};
+
+inline int field_geometry(const rd_field* fld, const float* x, const int* strides_or_null,
+                          double r_sp, FieldGeom* g) {
+  if (!fld || fld->ndim < 1 || fld->ndim > 3 || !x) return RD_ERR_INVALID_ARG;
+  FieldDev& f = g->f;
+  memset(&f, 0, sizeof(f));
+  f.d = fld->ndim;
+  long long N = 1;
+  for (int k = 0; k < 3; k++) f.n[k] = 1;
+  for (int k = 0; k < f.d; k++) {
+    if (fld->shape[k] < 1 || fld->shape[k] > 2147483647LL) return RD_ERR_INVALID_ARG;
+    f.n[k] = (int)fld->shape[k];
+    N *= fld->shape[k];
+    if (N > 2147483647LL) return RD_ERR_INVALID_ARG;
+  }
+  f.N = N;
+  f.x = x;
+  f.vec_ok = (((uintptr_t)x & 15u) == 0) && (f.n[f.d - 1] % 4 == 0);
+  int st[3] = {1, 1, 1};
+  if (strides_or_null) {
+    for (int k = 0; k < f.d; k++) {
+      if (strides_or_null[k] < 1) return RD_ERR_INVALID_ARG;
+      st[k] = strides_or_null[k];
+    }
+  } else {
+    sampling_strides(f.d, r_sp, st);
+  }
+  f.nblocks = 1;
+  f.nsampled = 1;
+  g->npoints_sampled = 1;
+  g->partial = 0;
+  for (int k = 0; k < f.d; k++) {
+    f.B[k] = (f.n[k] + 3) / 4;
+    f.s[k] = st[k];
+    f.L[k] = (f.B[k] + st[k] - 1) / st[k];
+    f.nblocks *= f.B[k];
+    f.nsampled *= f.L[k];
+    stride_magic(st[k], &f.smag[k], &f.ssh[k]);
+    unsigned long long pts = 0;
+    for (int b = 0; b < f.B[k]; b += st[k])
+      pts += (unsigned long long)(f.n[k] - 4 * b < 4 ? f.n[k] - 4 * b : 4);
+    g->npoints_sampled *= pts;
+    if (f.n[k] % 4) g->partial = 1;
+  }
+  return RD_OK;
+}
+
+// The geometry fields of a result record, which the host fills in after the
+// device wrote the rest: strides, block counts, sampling rate and sample
+// sizes (a constant field keeps its zeros), and the partial-block flag.
+inline void record_geometry(rd_result* r, const FieldGeom& g, bool zfp_est, int ec_mode) {
+  const FieldDev& f = g.f;
+  for (int k = 0; k < 3; k++) r->strides[k] = k < f.d ? f.s[k] : 0;
+  r->n_blocks = (uint64_t)f.nblocks;
+  if (!(r->flags & RD_F_CONSTANT)) {
+    r->n_sampled_blocks = (uint64_t)f.nsampled;
+    r->r_sp_eff = (double)f.nsampled / (double)f.nblocks;
+    r->zfp_npoints = g.npoints_sampled;
+    if (zfp_est) r->zfp_ncoeff = (unsigned long long)f.nsampled * ec_count(f.d, ec_mode);
+  }
+  if (g.partial) r->flags |= RD_F_PARTIAL_BLOCKS;
+}
 
 }  // namespace rdk

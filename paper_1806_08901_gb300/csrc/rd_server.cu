@@ -67,6 +67,7 @@ struct rd_server {
   std::vector<double> latencies;  // ms, completed requests
   uint64_t next_id = 1, submitted = 0, completed = 0, rejected = 0, hits = 0;
   int worker_errors = 0;
+  int started = 0, ready = 0;  // workers that reported their start-up, and those ready
   bool stop = false;
 };
 
@@ -82,7 +83,17 @@ void serve(rd_server* s) {
   // latency; slots launch directly
   if (ctx) rdk_set_graph_capture(ctx, false);
   std::unique_lock<std::mutex> lk(s->mu);
-  if (!ready) s->worker_errors++;
+  s->started++;
+  if (ready) s->ready++;
+  else s->worker_errors++;
+  s->cv_done.notify_all();
+  if (!ready) {
+    // a slot without a context or stream takes no work: it leaves at once
+    lk.unlock();
+    if (st) cudaStreamDestroy(st);
+    if (ctx) rd_context_destroy(ctx);
+    return;
+  }
   for (;;) {
     // take the first admissible request of the window
     ServerRequest req;
@@ -91,7 +102,7 @@ void serve(rd_server* s) {
     while (!taken) {
       if (s->stop && s->pending.empty()) break;
       const size_t lim = std::min(s->pending.size(), (size_t)s->window);
-      for (size_t i = 0; i < lim && ready; i++) {
+      for (size_t i = 0; i < lim; i++) {
         const ServerRequest& r = s->pending[i];
         if (r.host) {
           dec = s->policy.admit(r.key, r.bytes);
@@ -200,6 +211,17 @@ int32_t rd_server_create(const rd_server_config* cfg, rd_server** out) {
   s->device = cfg->device;
   s->window = cfg->window;
   for (int i = 0; i < cfg->slots; i++) s->workers.emplace_back(serve, s);
+  // wait until every slot has reported whether it could start
+  int ready = 0;
+  {
+    std::unique_lock<std::mutex> lk(s->mu);
+    s->cv_done.wait(lk, [&] { return s->started == cfg->slots; });
+    ready = s->ready;
+  }
+  if (ready == 0) {
+    rd_server_destroy(s);
+    return RD_ERR_CUDA;
+  }
   *out = s;
   return RD_OK;
 }

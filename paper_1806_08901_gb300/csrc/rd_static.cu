@@ -14,6 +14,7 @@
 // call's contents; each call clears what must start at zero before its
 // passes run.  Calls whose work overlaps on the GPU (different streams or
 // host threads) race on it and must be serialised by the caller.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -40,6 +41,7 @@ constexpr int kMaxDevices = 64;
 
 struct DeviceSlot {
   bool ready;
+  unsigned long long ctx_id;  // the CUDA context the set-up was done in
   Workspace* ws;  // device address of g_select_scratch on that device
   double* xlogx;  // device address of g_xlogx
   int range_ctas;
@@ -51,13 +53,49 @@ struct DeviceSlot {
 std::mutex g_mu;
 DeviceSlot g_slots[kMaxDevices];
 
-// Once per device, with that device current: resolve the array's device
-// address (host code sees only a host-side stand-in for the symbol) and size
-// the grids from the occupancy calculator.
+// The unique ID of the calling thread's current CUDA context (0 when it
+// cannot be read).  A context destroyed and created again (cudaDeviceReset,
+// then a new call) gets a new ID: the module is loaded afresh, so the
+// array's address, the filled table and the kernels' shared-memory
+// attributes must be set up again.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(f);
+  });
+  if (!get_current || !get_id) return 0;
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// With the device current: resolve the array's device address (host code
+// sees only a host-side stand-in for the symbol), fill the entropy table and
+// size the grids from the occupancy calculator.  Done on the first call on
+// the device, and again on the first call in a new context of the device.
 int setup_device(int dev, DeviceSlot** out) {
   if (dev < 0 || dev >= kMaxDevices) return RD_ERR_INVALID_ARG;
+  // any runtime call first makes the device's primary context current
+  void* p0 = nullptr;
+  if (cudaGetSymbolAddress(&p0, g_select_scratch) != cudaSuccess || !p0) return RD_ERR_CUDA;
+  const unsigned long long id = current_context_id();
   std::lock_guard<std::mutex> lock(g_mu);
   DeviceSlot& s = g_slots[dev];
+  if (s.ready && (id == 0 || id != s.ctx_id || p0 != (void*)s.ws)) s.ready = false;
   if (!s.ready) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_select_scratch) != cudaSuccess || !p) return RD_ERR_CUDA;
@@ -76,23 +114,10 @@ int setup_device(int dev, DeviceSlot** out) {
       s.sz_ctas[d] = sz_occupancy(d, sms);
       s.sz_est_ctas[d] = sz_est_occupancy(d, sms);
     }
+    s.ctx_id = id;
     s.ready = true;
   }
   *out = &s;
-  return RD_OK;
-}
-
-int check(const rd_field* fld, const rd_params* p) {
-  if (!fld || !p || !fld->data) return RD_ERR_INVALID_ARG;
-  if (fld->location != RD_LOC_DEVICE) return RD_ERR_INVALID_ARG;  // no staging copy
-  if (fld->ndim < 1 || fld->ndim > 3) return RD_ERR_INVALID_ARG;
-  if (!(p->eb > 0.0) || !isfinite(p->eb)) return RD_ERR_INVALID_ARG;
-  if (p->eb_mode != RD_EB_REL && p->eb_mode != RD_EB_ABS) return RD_ERR_INVALID_ARG;
-  if (p->ec_mode != RD_EC_PAPER && p->ec_mode != RD_EC_ALL) return RD_ERR_INVALID_ARG;
-  if (!(p->r_sp >= 1e-6 && p->r_sp <= 1.0)) return RD_ERR_INVALID_ARG;
-  if (p->quant_radius < 1 || p->quant_radius > 32768) return RD_ERR_INVALID_ARG;
-  if (p->sel_rule != RD_SEL_PAPER && p->sel_rule != RD_SEL_HUFFMAN) return RD_ERR_INVALID_ARG;
-  if (!isfinite(p->sz_offset)) return RD_ERR_INVALID_ARG;
   return RD_OK;
 }
 
@@ -100,25 +125,15 @@ int check(const rd_field* fld, const rd_params* p) {
 
 extern "C" int32_t rd_select_static(const rd_field* fld, const rd_params* prm, rd_result* out,
                                     void* stream) {
-  if (!out) return RD_ERR_INVALID_ARG;
-  int rc = check(fld, prm);
+  if (!out || !fld || !fld->data) return RD_ERR_INVALID_ARG;
+  if (fld->location != RD_LOC_DEVICE) return RD_ERR_INVALID_ARG;  // no staging copy
+  int rc = check_params(prm);
   if (rc) return rc;
   // the largest field: 2^31 - 1 points (the scratch itself does not grow
   // with the field: fixed alphabet, fixed exponent bins)
-  FieldDev f;
-  memset(&f, 0, sizeof(f));
-  f.d = fld->ndim;
-  long long N = 1;
-  for (int k = 0; k < 3; k++) f.n[k] = 1;
-  for (int k = 0; k < f.d; k++) {
-    if (fld->shape[k] < 1 || fld->shape[k] > 2147483647LL) return RD_ERR_INVALID_ARG;
-    f.n[k] = (int)fld->shape[k];
-    N *= fld->shape[k];
-    if (N > 2147483647LL) return RD_ERR_INVALID_ARG;
-  }
-  f.N = N;
-  f.x = fld->data;
-  f.vec_ok = (((uintptr_t)f.x & 15u) == 0) && (f.n[f.d - 1] % 4 == 0);
+  FieldGeom g;
+  if ((rc = field_geometry(fld, fld->data, nullptr, prm->r_sp, &g))) return rc;
+  const FieldDev& f = g.f;
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return RD_ERR_CUDA;
@@ -127,62 +142,21 @@ extern "C" int32_t rd_select_static(const rd_field* fld, const rd_params* prm, r
   Workspace* ws = slot->ws;
   cudaStream_t s = (cudaStream_t)stream;
 
-  // block sampling lattice: S = round(1/r_sp) split into primes, each prime
-  // (largest first) on the axis with the smallest stride (ties: faster axis)
-  long long S = (long long)floor(1.0 / prm->r_sp + 0.5);
-  if (S < 1) S = 1;
-  long long fac[64];
-  int nf = 0;
-  for (long long q = 2; q * q <= S; q++)
-    while (S % q == 0) {
-      fac[nf++] = q;
-      S /= q;
-    }
-  if (S > 1) fac[nf++] = S;
-  int st[3] = {1, 1, 1};
-  for (int i = nf - 1; i >= 0; i--) {
-    int a = f.d - 1;
-    for (int k = f.d - 2; k >= 0; k--)
-      if (st[k] < st[a]) a = k;
-    st[a] = (int)(st[a] * fac[i]);
-  }
-  f.nblocks = 1;
-  f.nsampled = 1;
-  unsigned long long npts = 1;
-  bool partial = false;
-  for (int k = 0; k < f.d; k++) {
-    f.B[k] = (f.n[k] + 3) / 4;
-    f.s[k] = st[k];
-    f.L[k] = (f.B[k] + st[k] - 1) / st[k];
-    f.nblocks *= f.B[k];
-    f.nsampled *= f.L[k];
-    unsigned long long pk = 0;
-    for (int b = 0; b < f.B[k]; b += st[k]) pk += (unsigned long long)(f.n[k] - 4 * b < 4 ? f.n[k] - 4 * b : 4);
-    npts *= pk;
-    partial = partial || (f.n[k] % 4) != 0;
-  }
-  ParamsDev p;
-  p.eb = prm->eb;
-  p.eb_mode = prm->eb_mode;
-  p.ec_mode = prm->ec_mode;
-  p.R = prm->quant_radius;
-  p.sel_rule = prm->sel_rule;
-  p.sz_offset = prm->sz_offset;
+  const ParamsDev p = params_dev(prm);
   const int d = f.d;
-  const int m = prm->ec_mode == RD_EC_ALL ? (1 << (2 * d)) : (d == 1 ? 3 : d == 2 ? 9 : 16);
-  const unsigned long long ncoeff = (unsigned long long)f.nsampled * m;
+  const unsigned long long ncoeff = (unsigned long long)f.nsampled * ec_count(d, prm->ec_mode);
   const int passes = P_ZFP_EST | P_SZ_EST;
   int zparts = 0;
 
   // the same launch sequence as rd_select, on the static scratch; the reset
   // kernel clears accumulators, histograms and result records first
   cudaError_t e = launch_reset(ws, s);
-  const DeltaArgs da{1, DELTA_FROM_MSE, 0.0, 1, 0, ncoeff, npts};
+  const DeltaArgs da{1, DELTA_FROM_MSE, 0.0, 1, 0, ncoeff, g.npoints_sampled};
   if (e == cudaSuccess) e = launch_range(f, p, ws, slot->range_ctas, s);
   if (e == cudaSuccess) e = launch_zfp(f, p, P_ZFP_EST, da, ws, slot->zfp_ctas[d], s, &zparts);
   if (e == cudaSuccess) e = launch_sz_est(f, p, ws, slot->sz_est_ctas[d], s);
   if (e == cudaSuccess) e = launch_code_stats(ws, 1, slot->xlogx, s);
-  if (e == cudaSuccess) e = launch_finish(p, ws, passes, zparts, 0, f.N, npts, s);
+  if (e == cudaSuccess) e = launch_finish(p, ws, passes, zparts, 0, f.N, g.npoints_sampled, s);
   rd_result r;
   int32_t status = RD_OK;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&r, &ws->res, sizeof(rd_result), cudaMemcpyDeviceToHost, s);
@@ -193,15 +167,7 @@ extern "C" int32_t rd_select_static(const rd_field* fld, const rd_params* prm, r
     memset(out, 0, sizeof(*out));
     return status;
   }
-  for (int k = 0; k < 3; k++) r.strides[k] = k < d ? f.s[k] : 0;
-  r.n_blocks = (uint64_t)f.nblocks;
-  if (!(r.flags & RD_F_CONSTANT)) {
-    r.n_sampled_blocks = (uint64_t)f.nsampled;
-    r.r_sp_eff = (double)f.nsampled / (double)f.nblocks;
-    r.zfp_npoints = npts;
-    r.zfp_ncoeff = ncoeff;
-  }
-  if (partial) r.flags |= RD_F_PARTIAL_BLOCKS;
+  record_geometry(&r, g, true, prm->ec_mode);
   *out = r;
   return RD_OK;
 }

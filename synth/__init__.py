@@ -100,14 +100,19 @@ def config2_field(seed: int | None = None, shape=(100, 500, 500)) -> np.ndarray:
     return rescale(g, 0.0, 300.0)
 
 
-def config3_fields(seed: int | None = None, shape=(512, 512, 512)) -> list:
-    """Log-normal density exp(2 G), G a unit GRF with k^-2, and three velocity
-    components: unit GRFs with k^-11/3 (a NYX-shaped snapshot)."""
+def config3_field(i: int, seed: int | None = None, shape=(512, 512, 512)) -> np.ndarray:
+    """Field i of the NYX-shaped snapshot: 0 is the log-normal density
+    exp(2 G), G a unit GRF with k^-2; 1..3 are velocity components, unit
+    GRFs with k^-11/3."""
     seed = seed_for(3) if seed is None else seed
-    out = [np.exp(2.0 * grf_np(shape, -2.0, seed).astype(np.float64)).astype(np.float32)]
-    for i in range(3):
-        out.append(grf_np(shape, -11.0 / 3.0, seed + 1 + i))
-    return out
+    if i == 0:
+        return np.exp(2.0 * grf_np(shape, -2.0, seed).astype(np.float64)).astype(np.float32)
+    return grf_np(shape, -11.0 / 3.0, seed + i)
+
+
+def config3_fields(seed: int | None = None, shape=(512, 512, 512)) -> list:
+    """The density and the three velocity components (a NYX-shaped snapshot)."""
+    return [config3_field(i, seed, shape) for i in range(4)]
 
 
 def fill_region_np(x: np.ndarray, seed: int, fill: float = 1e-20) -> np.ndarray:

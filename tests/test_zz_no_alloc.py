@@ -98,3 +98,25 @@ def test_static_select_refuses_what_needs_allocation(R):
     r = R.rd_result()
     rc = R.lib().rd_select_static(C.byref(f), C.byref(p), C.byref(r), None)
     assert rc == R.RD_ERR_INVALID_ARG
+
+
+def test_static_select_leaves_device_memory_untouched(R):
+    """The device's free memory is the same before and after a run of calls
+    on a large field (after one warm-up call): nothing was allocated.  The
+    reading is repeated a few times, since another process on the GPU could
+    move it; a slack of 2 MiB covers the driver's own bookkeeping."""
+    x = torch.from_numpy(synth.config2_field(seed=26, shape=(64, 256, 256))).cuda()
+    p = R.params(eb=1e-4, r_sp=0.05)
+    R.rd_select_static(x, p)
+    torch.cuda.synchronize()
+    ok = False
+    for _ in range(3):
+        free0, _total = torch.cuda.mem_get_info()
+        for _ in range(8):
+            R.rd_select_static(x, p)
+        torch.cuda.synchronize()
+        free1, _total = torch.cuda.mem_get_info()
+        if abs(free1 - free0) <= (2 << 20):
+            ok = True
+            break
+    assert ok, (free0, free1)
