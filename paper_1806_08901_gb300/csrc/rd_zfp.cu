@@ -197,18 +197,21 @@ static cudaError_t launch_zfp_d(const FieldDev& f, const ParamsDev& p, int passe
   return cudaGetLastError();
 }
 
+// 3D fields go to the four-lanes-per-block pass (rd_zfp3.cu); 1D and 2D
+// blocks (4 and 16 values) fit one thread each.
 cudaError_t launch_zfp(const FieldDev& f, const ParamsDev& p, int passes, const DeltaArgs& da,
                        Workspace* ws, int ctas, cudaStream_t s, int* grid_used) {
   switch (f.d) {
     case 1: return launch_zfp_d<1>(f, p, passes, da, ws, ctas, s, grid_used);
     case 2: return launch_zfp_d<2>(f, p, passes, da, ws, ctas, s, grid_used);
-    default: return launch_zfp_d<3>(f, p, passes, da, ws, ctas, s, grid_used);
+    default: return launch_zfp3(f, p, passes, da, ws, ctas, s, grid_used);
   }
 }
 
 // Number of CTAs of the pass that the SMs hold at once (a grid-stride pass
 // is sized to that; extra CTAs only add tail).
 int zfp_occupancy(int d, int num_sms) {
+  if (d == 3) return zfp3_occupancy(num_sms);
   int per = 0;
   const void* fn = nullptr;
   if (d == 1) fn = (const void*)k_zfp<1, true, true>;

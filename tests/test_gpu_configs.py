@@ -89,3 +89,19 @@ def test_512_cubed_fields(R, ctx, nyx, name, eb):
     check_result(ctx.select(xd, _gp(R, op)), o, 3)
     del xd
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("shape", [(13, 18, 22), (8, 12, 16)])
+def test_zfp_truth_with_every_plane_coded(R, ctx, shape):
+    """A bound far below the values' spacing makes every block code all 32
+    planes (P = 32, no plane left out): the embedded-coding cost then has no
+    floor below the planes, a case the moderate bounds never reach.  ZFP at
+    an absolute bound of 1e-9 on values of order 10^3, SZ at 1e-2."""
+    x = (synth.grf_np(shape, -3.0, 31) * 200 + 1000).astype(np.float32)
+    op = O.params(eb=1e-9, eb_mode=O.EB_ABS, r_sp=1.0)
+    xd = torch.from_numpy(x).cuda()
+    g = ctx.ground_truth(xd, _gp(R, op), eb_sz=1e-2)
+    o = O.ground_truth(x, op, eb_sz=1e-2)
+    check_truth(g, o)
+    blk = O.zfp_blocks(x, 1e-9)
+    assert np.all(blk["prec"] == 32)
