@@ -93,6 +93,25 @@ class Truth(C.Structure):
     ]
 
 
+class LogResult(C.Structure):
+    _fields_ = [
+        ("vr", C.c_double),
+        ("eb_abs", C.c_double),
+        ("unit", C.c_double),
+        ("max_abs", C.c_double),
+        ("base", C.c_double),
+        ("entropy", C.c_double),
+        ("br_log", C.c_double),
+        ("br_log_huff", C.c_double),
+        ("mse_log", C.c_double),
+        ("psnr_log", C.c_double),
+        ("ns", C.c_uint64),
+        ("huff_bits", C.c_uint64),
+        ("nsym", C.c_uint32),
+        ("flags", C.c_uint32),
+    ]
+
+
 class BlockOut(C.Structure):
     _fields_ = [
         ("emax", C.c_int32),
@@ -123,6 +142,8 @@ def load(path: str):
         "rdo_select": [f32p, C.c_int, i64p, P(Params), P(Result), u32p],
         "rdo_ground_truth": [f32p, C.c_int, i64p, P(Params), C.c_double, P(Truth), u32p],
         "rdo_estimate_sz": [f32p, C.c_int, i64p, P(Params), C.c_double, P(Result), u32p],
+        "rdo_estimate_sz_log": [f32p, C.c_int, i64p, P(Params), P(LogResult), u32p,
+                                P(C.c_double)],
         "rdo_zfp_blocks": [f32p, C.c_int, i64p, C.c_double, i32p, i32p, u64p, u32p],
         "rdo_sz_symbols": [f32p, C.c_int, i64p, C.c_double, C.c_int32, i32p, i32p, i32p, f32p],
         "rdo_zfp_block": [f32p, C.c_int, C.c_int32, C.c_int32, P(BlockOut)],
@@ -223,6 +244,26 @@ def estimate_sz(x: np.ndarray, p: Params, delta: float = 0.0, want_hist: bool = 
     if want_hist:
         d["hist"] = h
     return d
+
+
+def estimate_sz_log(x: np.ndarray, p: Params, want_hist: bool = False, want_edges: bool = False):
+    """Log-scale quantisation estimate; edges: A[1..n] (n = quant_radius)."""
+    x, shape = _field(x)
+    r = LogResult()
+    h = np.zeros(NSYM, dtype=np.uint32) if want_hist else None
+    e = np.zeros(p.quant_radius, dtype=np.float64) if want_edges else None
+    rc = lib().rdo_estimate_sz_log(_ptr(x, C.c_float), x.ndim, _ptr(shape, C.c_int64),
+                                   C.byref(p), C.byref(r),
+                                   _ptr(h, C.c_uint32) if h is not None else None,
+                                   _ptr(e, C.c_double) if e is not None else None)
+    if rc:
+        raise OracleError(rc, "rdo_estimate_sz_log")
+    out = _todict(r)
+    if want_hist:
+        out["hist"] = h
+    if want_edges:
+        out["edges"] = e
+    return out
 
 
 def ground_truth(x: np.ndarray, p: Params, eb_sz: float = 0.0, want_hist: bool = False):

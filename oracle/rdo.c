@@ -826,6 +826,155 @@ int rdo_estimate_sz(const float* x, int ndim, const int64_t* shape,
   return RDO_OK;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Section "Estimation Based on Static Quantization", log-scale case.  The   */
+/* paper's bins: the central bin n (width 2b) holds the values the rule     */
+/* floor(log_b |x|) sends there, bin n +- i the values with                 */
+/* floor(log_b |x|) = i, up to bin 2n-1, so b must carry the largest        */
+/* magnitude into the outermost bin.  Its formula for b is garbled; reading: */
+/* magnitudes in units of u = eb_abs (so the central bin (-b u, b u) is     */
+/* SZ's zero bin (-eb_abs, eb_abs) widened by b, and its width 2b in units   */
+/* of u is the paper's delta_n), b the smallest double >= 1 whose edge      */
+/* u b^n lies above max|r|, the edges taken                                 */
+/* as the doubles u * pow(b, k), and bin n +- k spanning [u b^k, u b^(k+1))  */
+/* (the printed width b^i - b^(i-1) is read as the width of the bin that    */
+/* floor(log_b) reaches, one index on).                                     */
+/* ------------------------------------------------------------------------ */
+
+static double log_edge(double u, double b, int k) { return u * pow(b, (double)k); }
+
+static double log_base(double u, double M, int n) {
+  double b = 1.0;
+  if (M >= u) {
+    b = pow(M / u, 1.0 / (double)n);
+    if (!(b >= 1.0)) b = 1.0;
+  }
+  while (!(log_edge(u, b, n) > M)) b = nextafter(b, INFINITY);
+  while (b > 1.0 && log_edge(u, nextafter(b, 0.0), n) > M) b = nextafter(b, 0.0);
+  return b;
+}
+
+/* Code of residual r: 0 in the central bin, else sign(r) times the number of
+ * edges A[1..n-1] at or below |r| (A[0] unused), found by bisection over the
+ * non-decreasing table. */
+static int32_t log_code(float r, const double* A, int n) {
+  double a = fabs((double)r);
+  int lo = 0, hi = n - 1; /* answer in [0, n-1] */
+  while (lo < hi) {
+    int mid = (lo + hi + 1) / 2;
+    if (A[mid] <= a)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return r < 0.0f ? -lo : lo;
+}
+
+int rdo_estimate_sz_log(const float* x, int ndim, const int64_t* shape,
+                        const rdo_params* p, rdo_log_result* r, uint32_t* hist,
+                        double* edges) {
+  field_t f;
+  int rc = field_init(&f, x, ndim, shape);
+  if (rc) return rc;
+  if ((rc = check_params(p))) return rc;
+  if (!r) return RDO_ERR_INVALID_ARG;
+  memset(r, 0, sizeof(*r));
+  if (hist) memset(hist, 0, RDO_NSYM * sizeof(uint32_t));
+  float vmin, vmax;
+  if ((rc = value_range(&f, &vmin, &vmax))) return rc;
+  r->vr = (double)vmax - (double)vmin;
+  r->eb_abs = (p->eb_mode == RDO_EB_REL) ? p->eb * r->vr : p->eb;
+  for (int k = 0; k < f.d; k++)
+    if (f.n[k] % 4) r->flags |= RDO_F_PARTIAL_BLOCKS;
+  if (r->vr == 0.0) {
+    r->flags |= RDO_F_CONSTANT;
+    r->psnr_log = INFINITY;
+    return RDO_OK;
+  }
+  if (!(r->eb_abs > 0.0) || !isfinite(r->eb_abs)) return RDO_ERR_INVALID_ARG;
+  const int n = p->quant_radius;
+  int32_t strides[3];
+  sampling_strides(f.d, p->r_sp, strides);
+  /* the residuals of every valid point of every sampled block, as the
+   * linear estimate computes them */
+  int nb = 1 << (2 * f.d);
+  float* res = NULL;
+  int64_t nres = 0, cap = 0;
+  int64_t bb[3] = {0, 0, 0};
+  do {
+    if (!block_is_sampled(&f, bb, strides)) continue;
+    for (int t = 0; t < nb; t++) {
+      if (!block_has_valid(&f, bb, t)) continue;
+      int64_t idx[3];
+      int tt = t;
+      for (int k = f.d - 1; k >= 0; k--) {
+        idx[k] = 4 * bb[k] + (tt & 3);
+        tt >>= 2;
+      }
+      if (nres == cap) {
+        cap = cap ? 2 * cap : 4096;
+        float* nr = (float*)realloc(res, (size_t)cap * sizeof(float));
+        if (!nr) {
+          free(res);
+          return RDO_ERR_INVALID_ARG;
+        }
+        res = nr;
+      }
+      res[nres++] = est_residual(&f, idx);
+    }
+  } while (next_block(&f, bb));
+  double M = 0.0;
+  for (int64_t i = 0; i < nres; i++)
+    if (fabs((double)res[i]) > M) M = fabs((double)res[i]);
+  const double u = r->eb_abs;
+  const double b = log_base(u, M, n);
+  double* A = (double*)malloc((size_t)(n + 1) * sizeof(double));
+  uint32_t* h = (uint32_t*)calloc(RDO_NSYM, sizeof(uint32_t));
+  if (!A || !h) {
+    free(A);
+    free(h);
+    free(res);
+    return RDO_ERR_INVALID_ARG;
+  }
+  A[0] = u;
+  for (int k = 1; k <= n; k++) A[k] = log_edge(u, b, k);
+  for (int k = 2; k <= n; k++)
+    if (A[k] < A[k - 1]) { /* a table the bisection cannot use */
+      free(A);
+      free(h);
+      free(res);
+      return RDO_ERR_RANGE;
+    }
+  for (int64_t i = 0; i < nres; i++) h[log_code(res[i], A, n) + 32768]++;
+  uint64_t ns = 0;
+  for (int s = 0; s < RDO_NSYM; s++) ns += h[s];
+  /* Eq. (mse-pdf) with P(m_i) = h_i / (N delta_i): sum h_i delta_i^2 / (12 N) */
+  double sum = 0.0;
+  for (int s = 0; s < RDO_NSYM; s++) {
+    if (!h[s]) continue;
+    int k = s >= 32768 ? s - 32768 : 32768 - s;
+    double w = k == 0 ? 2.0 * A[1] : A[k + 1] - A[k];
+    sum += (double)h[s] * (w * w);
+  }
+  r->unit = u;
+  r->max_abs = M;
+  r->base = b;
+  r->ns = ns;
+  r->entropy = entropy_bits(h, ns);
+  r->br_log = r->entropy + p->sz_offset;
+  huffman_of_hist(h, &r->huff_bits, &r->nsym);
+  r->br_log_huff = ns ? (double)r->huff_bits / (double)ns : 0.0;
+  r->mse_log = ns ? sum / (12.0 * (double)ns) : 0.0;
+  r->psnr_log = psnr_of(r->vr, r->mse_log);
+  if (hist) memcpy(hist, h, RDO_NSYM * sizeof(uint32_t));
+  if (edges)
+    for (int k = 1; k <= n; k++) edges[k - 1] = A[k];
+  free(A);
+  free(h);
+  free(res);
+  return RDO_OK;
+}
+
 static uint64_t u128_lt(uint64_t a_hi, uint64_t a_lo, uint64_t b_hi,
                         uint64_t b_lo) {
   return a_hi < b_hi || (a_hi == b_hi && a_lo < b_lo);

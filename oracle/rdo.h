@@ -99,6 +99,32 @@ typedef struct {
   float recon[64];             /* reconstructed block, block order */
 } rdo_block_out;
 
+/* Log-scale quantisation estimate (Section "Estimation Based on Static
+ * Quantization", log-scale case), on the same residuals as the linear
+ * estimate.  Magnitudes are measured against the unit u = eb_abs (the
+ * half-width of SZ's zero bin); with n = quant_radius, the edges are
+ * A[k] = u * pow(b, k), k = 1..n, where b is the smallest double >= 1 with
+ * A[n] > max |r|.  A residual r gets code 0 when |r| < A[1] (the central bin,
+ * width 2 A[1]) and otherwise sign(r) k with k = the number of edges
+ * A[1..n-1] at or below |r| (the bin [A[k], A[k+1]), width A[k+1] - A[k]).
+ * Symbol = code + 32768 (2n-1 bins, no escapes). */
+typedef struct {
+  double vr, eb_abs, unit;     /* unit u = eb_abs */
+  double max_abs;              /* largest |r| over the sampled points */
+  double base;                 /* b */
+  double entropy;              /* Eq. (bit-rate-pdf) with P(m_i) = h_i / (N delta_i) */
+  double br_log;               /* entropy + sz_offset */
+  double br_log_huff;          /* Huffman-coded bits per point */
+  double mse_log;              /* Eq. (mse-pdf): sum h_i delta_i^2 / (12 N) */
+  double psnr_log;             /* Eq. (psnr-pdf) */
+  uint64_t ns, huff_bits;
+  uint32_t nsym, flags;
+} rdo_log_result;
+
+int rdo_estimate_sz_log(const float* x, int ndim, const int64_t* shape,
+                        const rdo_params* p, rdo_log_result* r, uint32_t* hist,
+                        double* edges);
+
 /* Algorithm 1 lines 2-12 for one field. hist_est: 65536 counts or NULL. */
 int rdo_select(const float* x, int ndim, const int64_t* shape,
                const rdo_params* p, rdo_result* r, uint32_t* hist_est);

@@ -182,3 +182,38 @@ def check_entropy_unequal_bins(O):
     H = -math.fsum((v / n) * math.log2(v / n) for v in h[h > 0])
     assert abs(r["entropy"] - H) <= 1e-14 * H, (r["entropy"], H)
     assert abs((r["br_sz"] - 0.5) - H) <= 1e-14 * H, (r["br_sz"], H)
+
+
+def check_log_bins_and_mse(O):
+    """Log-scale estimate on known residuals (a skewed, mostly positive set):
+    every residual's code against the exact edges u b^k (rationals) away
+    from rounding of an edge, and the MSE of Eq. (mse-pdf) summed exactly."""
+    from fractions import Fraction
+
+    rng = np.random.default_rng(91)
+    codes = np.rint(np.abs(rng.standard_normal(3000)) * 400 - 40).astype(np.int64)
+    x = _ramp_field(codes)
+    n = 64
+    p = O.params(eb=0.5, eb_mode=1, r_sp=1.0, quant_radius=n)
+    r = O.estimate_sz_log(x, p, want_hist=True, want_edges=True)
+    u, b = Fraction(r["unit"]), Fraction(r["base"])
+    exact = [u]
+    for _ in range(n):
+        exact.append(exact[-1] * b)
+    want = np.zeros(65536, np.int64)
+    near = 0
+    for c in codes:
+        a = Fraction(abs(int(c)))
+        k = sum(1 for j in range(1, n) if exact[j] <= a)
+        near += any(abs(a - exact[j]) <= a * Fraction(1, 2 ** 48) for j in range(1, n))
+        want[32768 + (k if c >= 0 else -k)] += 1
+    got = r["hist"].astype(np.int64)
+    assert np.abs(got - want).sum() <= 2 * near, "codes differ from the exact bins"
+    A = [r["unit"]] + list(r["edges"])
+    tot = Fraction(0)
+    for s in np.nonzero(got)[0]:
+        k = abs(int(s) - 32768)
+        w = Fraction(2 * A[1]) if k == 0 else Fraction(A[k + 1]) - Fraction(A[k])
+        tot += int(got[s]) * w * w
+    mse = tot / (12 * int(got.sum()))
+    assert abs(Fraction(r["mse_log"]) - mse) <= mse * Fraction(1, 10 ** 13), "MSE of the bins"

@@ -50,6 +50,14 @@ MUTANTS = {
           "Q[i] = (int32_t)rintf(f.x[i] * qz.inv * 2.0f);"),
          ("float xh = (float)Q[i] * qz.w;", "float xh = (float)Q[i] * (qz.w * 0.5f);")],
         ["truth"]),
+    "log_code_sign_flip": (
+        [("return r < 0.0f ? -lo : lo;", "return r < 0.0f ? lo : -lo;")], ["log"]),
+    "log_width_one_bin_down": (
+        [("double w = k == 0 ? 2.0 * A[1] : A[k + 1] - A[k];",
+          "double w = k == 0 ? 2.0 * A[1] : A[k] - A[k - 1];")], ["log"]),
+    "log_edge_off_by_one_power": (
+        [("for (int k = 1; k <= n; k++) A[k] = log_edge(u, b, k);",
+          "for (int k = 1; k <= n; k++) A[k] = log_edge(u, b, k + 1);")], ["log"]),
     "truth_residual_sign": (
         [("r += odd ? -q_at(f, Q, j) : q_at(f, Q, j);", "r += odd ? q_at(f, Q, j) : -q_at(f, Q, j);")],
         ["truth"]),
@@ -65,6 +73,9 @@ def _fields():
 
 
 def _run_pin(kind):
+    if kind == "log":
+        C.check_log_bins_and_mse(O)
+        return
     if kind == "entropy":
         C.check_entropy_equal_bins(O)
         C.check_entropy_unequal_bins(O)
@@ -109,7 +120,7 @@ def test_unmutated_copy_passes_every_pin(tmp_path):
     """The harness itself: a copy built the same way with no edit passes."""
     lib = _build_mutant(tmp_path, [])
     with _oracle_build(lib):
-        for kind in ("entropy", "estimator", "truth"):
+        for kind in ("entropy", "estimator", "truth", "log"):
             _run_pin(kind)
 
 
