@@ -233,6 +233,42 @@ int32_t rd_evaluate(rd_context* ctx, const rd_field* field,
 int32_t rd_select_static(const rd_field* field, const rd_params* params,
                          rd_result* out, void* stream);
 
+/* ---- log-scale quantisation ------------------------------------------ */
+
+/* Section "Estimation Based on Static Quantization", the log-scale case: the
+ * residuals of the linear SZ estimate (the points of the sampled blocks at
+ * r_sp, Lorenzo prediction from the original neighbours) binned on a
+ * logarithmic scale of 2n-1 bins, n = quant_radius.  The paper's base
+ * formula is garbled; the reading taken: magnitudes in units of
+ * u = eb_abs, edges A[k] = u * pow(b, k) (float64, k = 1..n) with b the
+ * smallest double >= 1 for which A[n] exceeds the largest |r|; code 0 for
+ * |r| < A[1] (width 2 A[1]), else sign(r) * k with k the number of edges
+ * A[1..n-1] at or below |r| (the bin [A[k], A[k+1])).  No value escapes. */
+typedef struct {
+  double vr, eb_abs;
+  double unit;        /* u = eb_abs */
+  double max_abs;     /* largest |r| over the sampled points */
+  double base;        /* b */
+  double entropy;     /* Eq. (bit-rate-pdf) with the histogram as the PDF */
+  double br_log;      /* entropy + params->sz_offset */
+  double br_log_huff; /* Huffman-coded bits per sampled point */
+  double mse_log;     /* Eq. (mse-pdf): sum h_i delta_i^2 / (12 N_s) */
+  double psnr_log;    /* Eq. (psnr-pdf) */
+  uint64_t ns, huff_bits;
+  uint32_t nsym, flags;
+} rd_log_result;
+
+/* The log-scale estimate of one field.  The edge table is derived on the
+ * host from the largest residual (one device-to-host copy and wait in the
+ * middle of the call); the binning compares each residual with it exactly,
+ * so codes, histogram, base and edges equal the CPU oracle's.  A constant
+ * field returns RD_F_CONSTANT and an infinite PSNR.  The histogram is left
+ * in the context (rd_copy_histograms, the estimate's slot).  Errors as
+ * rd_estimate_sz. */
+int32_t rd_estimate_sz_log(rd_context* ctx, const rd_field* field,
+                           const rd_params* params, rd_log_result* out,
+                           void* stream);
+
 /* ---- rate-distortion sweep ------------------------------------------- */
 
 /* One error bound of a sweep (rd_rd_curve). */

@@ -26,7 +26,7 @@ const char* kKernelNames[K_COUNT] = {
     "reset", "range", "zfp_pass", "delta", "sz_est", "sz_pass",
     "code_prep", "huffman", "finish", "zfp_inspect", "sz_inspect",
     "batch_reset", "batch_range", "batch_blocks", "batch_sz_hist", "batch_code_prep",
-    "batch_final", "batch_truth", "sz_classic", "sz_classic_err"};
+    "batch_final", "batch_truth", "sz_classic", "sz_classic_err", "sz_log"};
 
 struct KStat {
   double ms;
@@ -42,6 +42,15 @@ struct HostOut {
   rd_result res;
   rd_truth truth;
   int32_t status;
+};
+
+// What the log-scale estimate reads back: the range pass's scalars, the
+// largest residual, and at the end the record.
+struct LogHost {
+  int32_t status, constant;
+  uint32_t maxabs_bits, flags;
+  double vr, eb_abs;
+  rd_log_result res;
 };
 
 // Everything a call's launch sequence depends on.  Two calls with equal keys
@@ -116,6 +125,11 @@ struct rd_context {
   size_t xhat_bytes = 0;
   void* enc = nullptr;  // SZ stream encoder: symbols, code table, per-CTA offsets
   size_t enc_bytes = 0;
+  // log-scale estimate: float64 edges A[0..n], float edges F[0..n-2], record
+  double* log_a = nullptr;
+  float* log_f = nullptr;
+  rd_log_result* log_dev = nullptr;
+  LogHost* log_host = nullptr;  // pinned
   int num_sms = 0;
   int range_ctas = 0;
   int zfp_ctas[4] = {0, 0, 0, 0};
@@ -927,6 +941,128 @@ int batch_call(rd_context* c, const rd_field* fields, const rd_params* params, i
   return first;
 }
 
+// ---------------------------------------------------------------------------
+// Log-scale quantisation estimate (rd_estimate_sz_log)
+// ---------------------------------------------------------------------------
+// The base of the log scale: the smallest double b >= 1 whose edge
+// u * pow(b, n) lies above M, found from the n-th root and stepped by one
+// double at a time to the boundary.
+double log_scale_base(double u, double M, int n) {
+  auto edge = [&](double b) { return u * pow(b, (double)n); };
+  double b = 1.0;
+  if (M >= u) {
+    b = pow(M / u, 1.0 / (double)n);
+    if (!(b >= 1.0)) b = 1.0;
+  }
+  while (!(edge(b) > M)) b = nextafter(b, INFINITY);
+  while (b > 1.0 && edge(nextafter(b, 0.0)) > M) b = nextafter(b, 0.0);
+  return b;
+}
+
+int estimate_sz_log(rd_context* c, const rd_field* fld, const rd_params* prm, rd_log_result* out,
+                    void* stream) {
+  if (!c || !out) return RD_ERR_INVALID_ARG;
+  int rc = check_params(prm);
+  if (rc) return rc;
+  CallGuard guard(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  Geometry g;
+  if ((rc = make_geometry(c, fld, nullptr, prm->r_sp, s, &g))) return rc;
+  const int n = prm->quant_radius;
+  if (!c->log_a) {  // tables for the largest n, once per context
+    const size_t bytes =
+        (kCenter + 1) * sizeof(double) + kCenter * sizeof(float) + sizeof(rd_log_result);
+    if (c->budget && c->held + bytes > c->budget) return RD_ERR_BUDGET;
+    if (cudaMalloc(&c->log_a, (kCenter + 1) * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->log_f, kCenter * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&c->log_dev, sizeof(rd_log_result)) != cudaSuccess ||
+        cudaMallocHost(&c->log_host, sizeof(LogHost)) != cudaSuccess) {
+      cudaGetLastError();
+      if (c->log_a) cudaFree(c->log_a);
+      if (c->log_f) cudaFree(c->log_f);
+      if (c->log_dev) cudaFree(c->log_dev);
+      c->log_a = nullptr;
+      c->log_f = nullptr;
+      c->log_dev = nullptr;
+      c->log_host = nullptr;
+      return RD_ERR_OOM;
+    }
+    c->held += bytes;
+  }
+  const FieldDev& f = g.f;
+  const ParamsDev p = params_dev(prm);
+  Workspace* ws = c->ws;
+  LogHost* hb = c->log_host;
+  const int ctas = c->num_sms * 8;
+  // range and the largest residual, then their scalars to the host
+  if ((rc = launch(c, K_RESET, s, [&] { return launch_reset(ws, s); }))) return rc;
+  if ((rc = launch(c, K_RANGE, s, [&] { return launch_range(f, p, ws, c->range_ctas, s); })))
+    return rc;
+  if ((rc = launch(c, K_SZ_LOG, s, [&] { return launch_sz_log_max(f, ws, ctas, s); }))) return rc;
+  const cudaMemcpyKind d2h = cudaMemcpyDeviceToHost;
+  cudaError_t e = cudaMemcpyAsync(&hb->status, &ws->sc.status, sizeof(int32_t), d2h, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hb->constant, &ws->sc.constant, sizeof(int32_t), d2h, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hb->maxabs_bits, &ws->sc.log_maxabs, sizeof(uint32_t), d2h, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hb->flags, &ws->sc.flags, sizeof(uint32_t), d2h, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hb->vr, &ws->sc.vr, sizeof(double), d2h, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hb->eb_abs, &ws->sc.eb_abs, sizeof(double), d2h, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (c->profiling) collect_profile(c);
+  if (e != cudaSuccess) return cuda_status(e);
+  memset(out, 0, sizeof(*out));
+  if (hb->status != RD_OK) return hb->status;
+  const uint32_t partial = g.partial ? RD_F_PARTIAL_BLOCKS : 0u;
+  if (hb->constant) {
+    out->vr = hb->vr;
+    out->eb_abs = hb->eb_abs;
+    out->flags = hb->flags | partial | RD_F_CONSTANT;
+    out->psnr_log = INFINITY;
+    return RD_OK;
+  }
+  // the edge tables: float64 edges, and the smallest float at or above each
+  float mf;
+  memcpy(&mf, &hb->maxabs_bits, sizeof(mf));
+  const double M = (double)mf;
+  const double u = hb->eb_abs;
+  if (!(u > 0.0) || !isfinite(u)) return RD_ERR_INVALID_ARG;
+  const double b = log_scale_base(u, M, n);
+  std::vector<double> A((size_t)n + 1);
+  std::vector<float> F((size_t)(n > 1 ? n - 1 : 1), 0.0f);
+  A[0] = u;
+  for (int k = 1; k <= n; k++) A[k] = u * pow(b, (double)k);
+  for (int k = 2; k <= n; k++)
+    if (A[k] < A[k - 1]) return RD_ERR_RANGE;  // a table the binary search cannot use
+  for (int k = 1; k < n; k++) {
+    float v = (float)A[k];
+    if ((double)v < A[k]) v = nextafterf(v, INFINITY);
+    F[k - 1] = v;
+  }
+  e = cudaMemcpyAsync(c->log_a, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->log_f, F.data(), F.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  if ((rc = launch(c, K_SZ_LOG, s, [&] { return launch_sz_log_hist(f, n, c->log_f, ws, ctas, s); })))
+    return rc;
+  if ((rc = launch(c, K_CODE_PREP, s, [&] { return launch_code_prep(ws, 1, s); }))) return rc;
+  if ((rc = launch(c, K_HUFFMAN, s, [&] { return launch_huffman(ws, 1, c->xlogx, s); }))) return rc;
+  if ((rc = launch(c, K_FINISH, s,
+                   [&] { return launch_sz_log_finish(p, c->log_a, ws, c->log_dev, s); })))
+    return rc;
+  e = cudaMemcpyAsync(&hb->res, c->log_dev, sizeof(rd_log_result), d2h, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hb->status, &ws->sc.status, sizeof(int32_t), d2h, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host tables live until here
+  if (c->profiling) collect_profile(c);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (hb->status != RD_OK) return hb->status;
+  rd_log_result r = hb->res;
+  r.unit = u;
+  r.max_abs = M;
+  r.base = b;
+  r.flags |= partial;
+  *out = r;
+  return RD_OK;
+}
+
 }  // namespace
 
 // Off: every per-field call launches its kernels directly (the serving
@@ -1000,6 +1136,10 @@ int32_t rd_context_destroy(rd_context* c) {
   if (c->staging) cudaFree(c->staging);
   if (c->xhat) cudaFree(c->xhat);
   if (c->enc) cudaFree(c->enc);
+  if (c->log_a) cudaFree(c->log_a);
+  if (c->log_f) cudaFree(c->log_f);
+  if (c->log_dev) cudaFree(c->log_dev);
+  if (c->log_host) cudaFreeHost(c->log_host);
   if (c->ws) cudaFree(c->ws);
   if (c->xlogx) cudaFree(c->xlogx);
   if (c->out) cudaFreeHost(c->out);
@@ -1011,6 +1151,11 @@ int32_t rd_estimate_zfp(rd_context* c, const rd_field* f, const rd_params* p, rd
                         void* stream) {
   if (!out) return RD_ERR_INVALID_ARG;
   return run(c, f, p, P_ZFP_EST, DELTA_FROM_MSE, 0.0, out, nullptr, stream);
+}
+
+int32_t rd_estimate_sz_log(rd_context* c, const rd_field* f, const rd_params* p,
+                           rd_log_result* out, void* stream) {
+  return estimate_sz_log(c, f, p, out, stream);
 }
 
 int32_t rd_estimate_sz(rd_context* c, const rd_field* f, const rd_params* p, double delta,

@@ -41,6 +41,7 @@ struct Scalars {
   unsigned long long zfp_bits;   // exact ZFP fixed-accuracy bits
   unsigned int zfp_maxerr;       // float bits of max |x - xhat|
   unsigned int sz_maxerr;
+  unsigned int log_maxabs;       // float bits of max |residual| (log-scale estimate)
   unsigned long long mse_lo[kMseBins];  // 128-bit sums of d^2 per exponent
   unsigned long long mse_hi[kMseBins];
 };
@@ -155,6 +156,7 @@ enum KernelId {
   K_B_TRUTH,
   K_SZ_CLASSIC,
   K_SZ_CLASSIC_ERR,
+  K_SZ_LOG,
   K_COUNT
 };
 
@@ -235,6 +237,13 @@ int zfp_occupancy(int d, int num_sms);
 cudaError_t launch_zfp3(const FieldDev& f, const ParamsDev& p, int passes, const DeltaArgs& da,
                         Workspace* ws, int ctas, cudaStream_t s, int* grid_used);
 int zfp3_occupancy(int num_sms);
+
+// ---- log-scale quantisation estimate (rd_sz_log.cu) ----
+cudaError_t launch_sz_log_max(const FieldDev& f, Workspace* ws, int ctas, cudaStream_t s);
+cudaError_t launch_sz_log_hist(const FieldDev& f, int n, const float* F, Workspace* ws, int ctas,
+                               cudaStream_t s);
+cudaError_t launch_sz_log_finish(const ParamsDev& p, const double* A, Workspace* ws,
+                                 rd_log_result* out, cudaStream_t s);
 
 // ---- batched estimate (rd_select_batch) ----
 cudaError_t launch_batch_reset(const BatchField* bf, int n, int need_gt, cudaStream_t s);

@@ -51,6 +51,7 @@ __device__ void reset_ws(Workspace* ws, int tid, int nth, int which_mask) {
     s.zfp_bits = 0ull;
     s.zfp_maxerr = 0u;
     s.sz_maxerr = 0u;
+    s.log_maxabs = 0u;
     for (int w = 0; w < 2; w++) {
       ws->nbig[w] = 0u;
       ws->huff[w].ns = 0ull;

@@ -134,11 +134,12 @@ __device__ __forceinline__ void sampled_block_origin(const FieldDev& f, long lon
   }
 }
 
-// add(sym) counts one code; for 3D blocks round_end() runs after each of
-// the four planes, in every thread of the CTA (active or not).
-template <int D, class Add, class RoundEnd>
-__device__ __forceinline__ void sz_est_block(const FieldDev& f, long long sb, bool active, float inv,
-                                             int R, Add&& add, RoundEnd&& round_end) {
+// res(r) receives the residual of every valid point of the block; for 3D
+// blocks round_end() runs after each of the four planes, in every thread of
+// the CTA (active or not).
+template <int D, class Res, class RoundEnd>
+__device__ __forceinline__ void sz_block_residuals(const FieldDev& f, long long sb, bool active,
+                                                   Res&& res, RoundEnd&& round_end) {
   int o[3] = {0, 0, 0};
   if (active) sampled_block_origin<D>(f, sb, o);
   if constexpr (D == 1) {
@@ -147,7 +148,7 @@ __device__ __forceinline__ void sz_est_block(const FieldDev& f, long long sb, bo
 #pragma unroll
     for (int k = 0; k < 4; k++) {
       const bool ok = active && o[0] + k < f.n[0];
-      if (ok) add(est_symbol(__fsub_rn(v[k + 1], v[k]), inv, R));
+      if (ok) res(__fsub_rn(v[k + 1], v[k]));
     }
   } else {
     const int ny = f.n[D - 2], nx = f.n[D - 1];
@@ -184,7 +185,7 @@ __device__ __forceinline__ void sz_est_block(const FieldDev& f, long long sb, bo
         const int j = t >> 2, k = t & 3;
         const bool ok = z_ok && y0 + j < ny && x0 + k < nx;
         const float r = D == 3 ? __fsub_rn(cur[t], prev[t]) : cur[t];
-        if (ok) add(est_symbol(r, inv, R));
+        if (ok) res(r);
       }
       if (D == 3) {
 #pragma unroll
@@ -193,6 +194,13 @@ __device__ __forceinline__ void sz_est_block(const FieldDev& f, long long sb, bo
       }
     }
   }
+}
+
+// add(sym) counts the linear code of every valid point of the block.
+template <int D, class Add, class RoundEnd>
+__device__ __forceinline__ void sz_est_block(const FieldDev& f, long long sb, bool active, float inv,
+                                             int R, Add&& add, RoundEnd&& round_end) {
+  sz_block_residuals<D>(f, sb, active, [&](float r) { add(est_symbol(r, inv, R)); }, round_end);
 }
 
 }  // namespace rdk

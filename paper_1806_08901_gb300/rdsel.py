@@ -76,6 +76,14 @@ class rd_truth(C.Structure):
     ]
 
 
+class rd_log_result(C.Structure):
+    _fields_ = [("vr", C.c_double), ("eb_abs", C.c_double), ("unit", C.c_double),
+                ("max_abs", C.c_double), ("base", C.c_double), ("entropy", C.c_double),
+                ("br_log", C.c_double), ("br_log_huff", C.c_double), ("mse_log", C.c_double),
+                ("psnr_log", C.c_double), ("ns", C.c_uint64), ("huff_bits", C.c_uint64),
+                ("nsym", C.c_uint32), ("flags", C.c_uint32)]
+
+
 class rd_rd_point(C.Structure):
     _fields_ = [("eb", C.c_double), ("est", rd_result), ("truth", rd_truth), ("est_eb", rd_result),
                 ("truth_eb", rd_truth), ("selection_eb", C.c_int32), ("best_eb_gt", C.c_int32)]
@@ -111,6 +119,8 @@ _SIGNATURES = {
     "rd_context_create": (C.c_int32, [C.c_int32, C.c_size_t, _P(C.c_void_p)]),
     "rd_context_destroy": (C.c_int32, [C.c_void_p]),
     "rd_estimate_zfp": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), _P(rd_result), C.c_void_p]),
+    "rd_estimate_sz_log": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), _P(rd_log_result),
+                                       C.c_void_p]),
     "rd_estimate_sz": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), C.c_double,
                                    _P(rd_result), C.c_void_p]),
     "rd_select": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), _P(rd_result), C.c_void_p]),
@@ -270,6 +280,15 @@ def rd_estimate_sz(ctx, field, prm: rd_params, delta: float = 0.0, stream=None) 
     r = rd_result()
     _check(lib().rd_estimate_sz(ctx, C.byref(f), C.byref(prm), float(delta), C.byref(r),
                                 _stream(stream)), "rd_estimate_sz")
+    return _todict(r)
+
+
+def rd_estimate_sz_log(ctx, field, prm: rd_params, stream=None) -> dict:
+    """The log-scale quantisation estimate of one field."""
+    f, keep = make_field(field)
+    r = rd_log_result()
+    _check(lib().rd_estimate_sz_log(ctx, C.byref(f), C.byref(prm), C.byref(r), _stream(stream)),
+           "rd_estimate_sz_log")
     return _todict(r)
 
 
@@ -598,6 +617,9 @@ class Context:
 
     def estimate_sz(self, x, p, delta=0.0, stream=None):
         return rd_estimate_sz(self.h, x, p, delta, stream)
+
+    def estimate_sz_log(self, x, p, stream=None):
+        return rd_estimate_sz_log(self.h, x, p, stream)
 
     def select(self, x, p, stream=None):
         return rd_select(self.h, x, p, stream)

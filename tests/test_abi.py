@@ -50,6 +50,7 @@ def test_struct_layout_matches_header(rdsel, tmp_path):
                "rd_result": rdsel.rd_result, "rd_truth": rdsel.rd_truth,
                "rd_batch_config": rdsel.rd_batch_config,
                "rd_rd_point": rdsel.rd_rd_point,
+               "rd_log_result": rdsel.rd_log_result,
                "rd_server_config": rdsel.rd_server_config,
                "rd_server_completion": rdsel.rd_server_completion,
                "rd_server_stats": rdsel.rd_server_stats}
