@@ -53,6 +53,49 @@ int32_t rd_sz_compress(rd_context* ctx, const rd_field* field, const rd_params* 
                        double eb_sz, void* out, uint64_t cap_bytes, uint64_t* nbits,
                        void* stream);
 
+/* The ZFP fixed-accuracy stream of the field at eb_abs (from params: eb and
+ * eb_mode), the stream whose size rd_ground_truth reports as zfp_bits_gt.
+ * Layout, bits most significant first within each byte, one block after
+ * another in row-major block order (the last axis fastest):
+ *   flag      1 bit: 0 when the block codes no plane (precision 0: the
+ *             block is all zero, or far below the bound), and nothing more;
+ *   exponent  the block exponent emax + 127 (8 bits);
+ *   planes    planes 31 .. 32-P of the block's negabinary coefficients in
+ *             sequency order (P = clamp(emax - floor(log2 eb_abs) + 2(d+1),
+ *             0, 32)), each as: the bits of the coefficients already
+ *             significant, verbatim; then group tests, a 1 when a one remains
+ *             among the others followed by their bits up to and including
+ *             that one (the last coefficient's bit implied), until a test
+ *             reads 0 or no coefficient is left.
+ * A decoder rebuilds the field from the stream, the shape and eb_abs (the
+ * truncated coefficients through the inverse transform).
+ *  - out: DEVICE memory, 8-byte aligned, cap_bytes >= 8 * ceil(*nbits /
+ *    64) (RD_ERR_RANGE otherwise); the bytes past the last bit are zero.
+ *    out = NULL: only *nbits is computed.
+ *  - A constant field under a value-range-relative bound has no bound to
+ *    code at: RD_ERR_INVALID_ARG.
+ *  - Device work: the ZFP truth (bit count), then every block's bits and
+ *    their sums per chunk of 1024 blocks, one scan over the chunks, and
+ *    each block written at its offset by 64-bit ORs.  The context keeps a
+ *    scratch of 4 bytes per block, counted against its memory budget.
+ *  - Returns once the work on `stream` has finished. */
+int32_t rd_zfp_compress(rd_context* ctx, const rd_field* field, const rd_params* params,
+                        void* out, uint64_t cap_bytes, uint64_t* nbits, void* stream);
+
+/* Algorithm 1 for one field, to the end: the selection s_i (rd_select),
+ * then the compressed bytes C_i of the compressor it picks -- SZ's stream
+ * (rd_sz_compress) at eb_sz = delta / 2 when s_i = 0, ZFP's stream
+ * (rd_zfp_compress) at eb_abs when s_i = 1.
+ *  - *selection: s_i (0 = SZ, 1 = ZFP); *nbits: the length of C_i; est:
+ *    the selection's record, or NULL.
+ *  - out = NULL: the selection and the length only; otherwise as the two
+ *    stream calls (device memory, 8-byte aligned, large enough).
+ *  - A constant field: RD_ERR_INVALID_ARG (est, when given, holds its
+ *    record). */
+int32_t rd_compress(rd_context* ctx, const rd_field* field, const rd_params* params, void* out,
+                    uint64_t cap_bytes, uint64_t* nbits, int32_t* selection, rd_result* est,
+                    void* stream);
+
 #ifdef __cplusplus
 }
 #endif

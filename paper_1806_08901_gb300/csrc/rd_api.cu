@@ -1277,20 +1277,23 @@ int32_t rd_sz_compress(rd_context* c, const rd_field* fld, const rd_params* prm,
   // an optimal code's payload is the Huffman cost the truth reported
   if ((unsigned long long)K != t.sz_nsym_gt || payload != t.sz_huff_gt || nesc != t.sz_nesc_gt)
     return RD_ERR_CUDA;
-  // canonical codes: ascending (length, symbol) take consecutive values
+  // canonical codes: ascending (length, symbol) take consecutive values;
+  // the first code of each length from the count of shorter codes
   std::vector<unsigned long long> code(kNsym, 0ull);
   {
+    unsigned long long nlen[65] = {0ull}, next[65] = {0ull};
+    for (int v = 0; v < kNsym; v++) nlen[len[v]]++;
+    nlen[0] = 0ull;
     unsigned long long cv = 0ull;
     int prev = 0;
-    bool first = true;
-    for (int L = 1; L <= 63; L++)
-      for (int v = 0; v < kNsym; v++) {
-        if (len[v] != L) continue;
-        cv = first ? 0ull : (cv + 1ull) << (L - prev);
-        first = false;
-        prev = L;
-        code[v] = cv;
-      }
+    for (int L = 1; L <= 63; L++) {
+      if (!nlen[L]) continue;
+      cv = prev ? (cv + nlen[prev]) << (L - prev) : 0ull;
+      next[L] = cv;
+      prev = L;
+    }
+    for (int v = 0; v < kNsym; v++)
+      if (len[v]) code[v] = next[len[v]]++;
   }
   // header and table, written here; the payload starts right after them
   StreamBits hb;
@@ -1346,6 +1349,68 @@ int32_t rd_sz_compress(rd_context* c, const rd_field* fld, const rd_params* prm,
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   c->launches += 1;
   return cuda_status(e);
+}
+
+int32_t rd_zfp_compress(rd_context* c, const rd_field* fld, const rd_params* prm, void* out,
+                        uint64_t cap_bytes, uint64_t* nbits, void* stream) {
+  if (!c || !nbits) return RD_ERR_INVALID_ARG;
+  if (out && ((uintptr_t)out & 7u)) return RD_ERR_INVALID_ARG;
+  // the ZFP truth: status checks, eb_abs and its exponent, the bit count
+  rd_result r;
+  rd_truth t;
+  int rc = run(c, fld, prm, P_ZFP_GT, DELTA_FROM_MSE, 0.0, &r, &t, stream);
+  if (rc) return rc;
+  if (r.flags & RD_F_CONSTANT) return RD_ERR_INVALID_ARG;  // no bound to code at
+  *nbits = t.zfp_bits_gt;
+  if (!out) return RD_OK;
+  const unsigned long long words = (t.zfp_bits_gt + 63ull) / 64ull;
+  if (cap_bytes < words * 8ull) return RD_ERR_RANGE;
+  CallGuard guard(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  Geometry g;
+  if ((rc = make_geometry(c, fld, nullptr, prm->r_sp, s, &g))) return rc;
+  // device scratch: per-block bits, per-chunk sums, the total
+  const int nch = zfp_stream_chunks(g.f.nblocks);
+  const size_t off_cs = ((size_t)g.f.nblocks * sizeof(uint32_t) + 15) / 16 * 16;
+  const size_t off_tot = off_cs + sizeof(unsigned long long) * (size_t)nch;
+  const size_t bytes = off_tot + 2 * sizeof(unsigned long long);
+  if (bytes > c->enc_bytes) {
+    if (c->budget && c->held + (bytes - c->enc_bytes) > c->budget) return RD_ERR_BUDGET;
+    if (c->enc) cudaFree(c->enc);
+    c->held -= c->enc_bytes;
+    c->enc = nullptr;
+    c->enc_bytes = 0;
+    if (cudaMalloc(&c->enc, bytes) != cudaSuccess) return RD_ERR_OOM;
+    c->enc_bytes = bytes;
+    c->held += bytes;
+  }
+  unsigned char* base = static_cast<unsigned char*>(c->enc);
+  uint32_t* dbits = reinterpret_cast<uint32_t*>(base);
+  unsigned long long* dcs = reinterpret_cast<unsigned long long*>(base + off_cs);
+  unsigned long long* dtot = reinterpret_cast<unsigned long long*>(base + off_tot);
+  cudaError_t e = cudaMemsetAsync(out, 0, words * 8ull, s);
+  if (e == cudaSuccess)
+    e = launch_zfp_stream(g.f, r.minexp, dbits, dcs, dtot, static_cast<unsigned long long*>(out), s);
+  unsigned long long* ht = reinterpret_cast<unsigned long long*>(&c->out->truth.zfp_bits_gt);  // pinned
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ht, dtot, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  c->launches += 3;
+  if (e != cudaSuccess) return cuda_status(e);
+  return *ht == t.zfp_bits_gt ? RD_OK : RD_ERR_CUDA;  // the blocks' bits add up to the truth's
+}
+
+int32_t rd_compress(rd_context* c, const rd_field* fld, const rd_params* prm, void* out,
+                    uint64_t cap_bytes, uint64_t* nbits, int32_t* selection, rd_result* est,
+                    void* stream) {
+  if (!c || !nbits || !selection) return RD_ERR_INVALID_ARG;
+  rd_result r;
+  int rc = rd_select(c, fld, prm, &r, stream);
+  if (rc) return rc;
+  if (est) *est = r;
+  if (r.flags & RD_F_CONSTANT) return RD_ERR_INVALID_ARG;
+  *selection = r.selection;
+  if (r.selection == 0) return rd_sz_compress(c, fld, prm, r.delta / 2.0, out, cap_bytes, nbits, stream);
+  return rd_zfp_compress(c, fld, prm, out, cap_bytes, nbits, stream);
 }
 
 int32_t rd_evaluate(rd_context* c, const rd_field* f, const rd_params* p, rd_result* est,

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "rd_internal.cuh"
+
 namespace rdk {
 
 // Points per CTA of the counting and packing passes.
@@ -29,5 +31,14 @@ cudaError_t launch_stream_pack(const int32_t* sym, const float* x, long long n, 
                                const unsigned* cta_esc, const unsigned long long* totals,
                                unsigned long long payload_base, unsigned long long* out,
                                cudaStream_t s);
+
+// ZFP fixed-accuracy stream (rd_zfp_stream.cu): every block's bits into
+// bits[nblocks], per-chunk sums into csum[zfp_stream_chunks(nblocks)] (then
+// scanned in place; total[0] = the stream's length); with out, every block
+// written at its offset by 64-bit ORs into out (zeroed, 8-byte aligned).
+int zfp_stream_chunks(long long nblocks);
+cudaError_t launch_zfp_stream(const FieldDev& f, int minexp, uint32_t* bits,
+                              unsigned long long* csum, unsigned long long* total,
+                              unsigned long long* out, cudaStream_t s);
 
 }  // namespace rdk

@@ -130,6 +130,10 @@ _SIGNATURES = {
                                             _P(rd_truth), C.c_void_p, C.c_void_p]),
     "rd_sz_compress": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), C.c_double, C.c_void_p,
                                    C.c_uint64, _P(C.c_uint64), C.c_void_p]),
+    "rd_zfp_compress": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), C.c_void_p, C.c_uint64,
+                                    _P(C.c_uint64), C.c_void_p]),
+    "rd_compress": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), C.c_void_p, C.c_uint64,
+                                _P(C.c_uint64), _P(C.c_int32), _P(rd_result), C.c_void_p]),
     "rd_rd_curve": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), _P(C.c_double), C.c_int32,
                                 _P(rd_rd_point), C.c_void_p]),
     "rd_evaluate": (C.c_int32, [C.c_void_p, _P(rd_field), _P(rd_params), _P(rd_result),
@@ -355,6 +359,43 @@ def rd_sz_compress(ctx, field, prm: rd_params, eb_sz: float, out=None, stream=No
     _check(lib().rd_sz_compress(ctx, C.byref(f), C.byref(prm), float(eb_sz), ptr, cap,
                                 C.byref(nbits), _stream(stream)), "rd_sz_compress")
     return nbits.value
+
+
+def _stream_out(out):
+    if out is None:
+        return None, 0
+    import torch
+    if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.uint8
+            and out.is_contiguous()):
+        raise ValueError("out must be a contiguous uint8 CUDA tensor")
+    return C.c_void_p(out.data_ptr()), out.numel()
+
+
+def rd_zfp_compress(ctx, field, prm: rd_params, out=None, stream=None) -> int:
+    """The ZFP fixed-accuracy stream at eb_abs (layout in
+    include/rdsel_stream.h) into out, a uint8 CUDA tensor of at least
+    8 * ceil(nbits / 64) bytes; out=None only sizes it.  Returns the
+    stream's length in bits."""
+    f, keep = make_field(field)
+    nbits = C.c_uint64(0)
+    ptr, cap = _stream_out(out)
+    _check(lib().rd_zfp_compress(ctx, C.byref(f), C.byref(prm), ptr, cap, C.byref(nbits),
+                                 _stream(stream)), "rd_zfp_compress")
+    return nbits.value
+
+
+def rd_compress(ctx, field, prm: rd_params, out=None, stream=None) -> dict:
+    """Algorithm 1 to the end: the selection s_i and the selected
+    compressor's stream C_i (into out when given).  Returns selection,
+    nbits and the selection's record (est)."""
+    f, keep = make_field(field)
+    nbits = C.c_uint64(0)
+    sel = C.c_int32(-1)
+    est = rd_result()
+    ptr, cap = _stream_out(out)
+    _check(lib().rd_compress(ctx, C.byref(f), C.byref(prm), ptr, cap, C.byref(nbits), C.byref(sel),
+                             C.byref(est), _stream(stream)), "rd_compress")
+    return {"selection": sel.value, "nbits": nbits.value, "est": _todict(est)}
 
 
 def rd_rd_curve(ctx, field, prm: rd_params, ebs, stream=None) -> list:
@@ -626,6 +667,12 @@ class Context:
 
     def ground_truth(self, x, p, eb_sz=0.0, stream=None):
         return rd_ground_truth(self.h, x, p, eb_sz, stream)
+
+    def zfp_compress(self, x, p, out=None, stream=None):
+        return rd_zfp_compress(self.h, x, p, out, stream)
+
+    def compress(self, x, p, out=None, stream=None):
+        return rd_compress(self.h, x, p, out, stream)
 
     def sz_compress(self, x, p, eb_sz, out=None, stream=None):
         return rd_sz_compress(self.h, x, p, eb_sz, out, stream)
