@@ -62,9 +62,11 @@ def parse():
                     help="skip the four 512^3 fields at eb_rel 1e-3 and 1e-5")
     ap.add_argument("--no-classic", action="store_true",
                     help="skip the classic SZ truth beside the prequantised one")
-    ap.add_argument("--serve-population", type=int, default=64)
-    ap.add_argument("--serve-requests", type=int, default=400)
-    ap.add_argument("--serve-rates", default="100,500,2000")
+    ap.add_argument("--serve-population", type=int, default=256)
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="longest span of arrivals per rate")
+    ap.add_argument("--serve-rates", default="50,100,200,500,1000,2000")
     return ap.parse_args()
 
 
@@ -462,15 +464,54 @@ def bench_sz_stream(R, ctx, x, stream, reps: int = 5):
             "GB_s": x.numel() * 4 / (statistics.median(ms) / 1e3) / 1e9}
 
 
-def bench_serving(R, population: int, n_req: int, rates, budget: int = 120 << 30):
+def _serve_rate(R, srv, fields, prm, rate, n_req, seed, max_s, population):
+    """Poisson arrivals at `rate` for at most n_req requests or max_s seconds
+    of arrivals; returns throughput, latency percentiles and residency."""
+    import time
+
+    import synth
+
+    reqs = [r for r in synth.serving_requests(rate, n_req, seed=seed, population=population)
+            if r["t"] <= max_s]
+    srv.reset_stats()
+    st0 = srv.stats()
+    done = 0
+    nbytes = 0
+    t0 = time.perf_counter()
+    for i, r in enumerate(reqs):
+        while True:
+            now = time.perf_counter() - t0
+            if now >= r["t"]:
+                break
+            if r["t"] - now > 2e-3:
+                time.sleep(r["t"] - now - 1e-3)
+        eb = min(prm, key=lambda e: abs(e - r["eb_rel"]))
+        srv.submit(fields[r["field"]], prm[eb], key=1 + r["field"], tag=i)
+        nbytes += 4 * fields[r["field"]].numel()
+        done += len(srv.poll(256, wait_ms=0))
+    while done < len(reqs):
+        done += len(srv.poll(256, wait_ms=5000))
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    hits = st["resident_hits"] - st0["resident_hits"]
+    return {"rate_req_s": rate, "requests": len(reqs), "wall_s": wall,
+            "throughput_req_s": len(reqs) / wall, "throughput_GB_s": nbytes / wall / 1e9,
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+            "max_ms": st["max_ms"], "resident_hits": hits, "hit_rate": hits / max(1, len(reqs)),
+            "evictions": st["evictions"] - st0["evictions"],
+            "resident_bytes": st["resident_bytes"]}
+
+
+def bench_serving(R, population: int, n_req: int, rates, budget: int = 120 << 30,
+                  max_s: float = 10.0, evict_rate: float = 200.0):
     """The serving loop under Poisson arrivals: requests name fields of a
     population held in pinned host memory (2D ny ~ logU[512, 1800], nx ~
     logU[512, 3600], or 3D cubes with side ~ logU[64, 512]; spectra k^a, a ~
-    U[-4, -2]) and an error bound from {1e-2 .. 1e-6}; each field stays
-    resident on the device after its first request (120 GB budget).  Every
-    field is requested once before the timed rates."""
-    import time
-
+    U[-4, -2]) and an error bound from {1e-2 .. 1e-6}; each rate runs for
+    n_req requests or max_s seconds of arrivals.  Under the 120 GB budget
+    every field stays resident (each is requested once first); a second run
+    starts cold under a budget of a quarter of the population, so requests
+    miss, copy their field in and evict others."""
     import torch
 
     import synth
@@ -486,8 +527,14 @@ def bench_serving(R, population: int, n_req: int, rates, budget: int = 120 << 30
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     prm = {eb: R.params(eb=eb, r_sp=R_SP) for eb in (1e-2, 1e-3, 1e-4, 1e-5, 1e-6)}
+    pop_bytes = sum(4 * f.numel() for f in fields)
     out = {"workload": SERVE_WORKLOAD, "population": population, "hbm_budget_bytes": budget,
-           "population_bytes": sum(4 * f.numel() for f in fields), "slots": 4, "rates": []}
+           "population_bytes": pop_bytes, "slots": 4, "window": 16,
+           "requests_per_rate": f"{n_req} or {max_s:g} s of arrivals",
+           "slots_are": "host threads, each running one request's launch chain on its own "
+                        "stream; concurrent requests overlap on the device, they are not "
+                        "merged into one launch",
+           "rates": []}
     with R.Server(0, slots=4, window=16, hbm_budget=budget) as srv:
         for i, f in enumerate(fields):  # first touch: copy in
             srv.submit(f, prm[1e-4], key=1 + i, tag=i)
@@ -495,33 +542,14 @@ def bench_serving(R, population: int, n_req: int, rates, budget: int = 120 << 30
         while got < len(fields):
             got += len(srv.poll(256, wait_ms=5000))
         for k, rate in enumerate(rates):
-            reqs = synth.serving_requests(rate, n_req, seed=synth.seed_for(5, 100 + k),
-                                          population=population)
-            srv.reset_stats()
-            done = 0
-            nbytes = 0
-            t0 = time.perf_counter()
-            for i, r in enumerate(reqs):
-                while True:
-                    now = time.perf_counter() - t0
-                    if now >= r["t"]:
-                        break
-                    if r["t"] - now > 2e-3:
-                        time.sleep(r["t"] - now - 1e-3)
-                eb = min(prm, key=lambda e: abs(e - r["eb_rel"]))
-                srv.submit(fields[r["field"]], prm[eb], key=1 + r["field"], tag=i)
-                nbytes += 4 * fields[r["field"]].numel()
-                done += len(srv.poll(256, wait_ms=0))
-            while done < len(reqs):
-                done += len(srv.poll(256, wait_ms=5000))
-            wall = time.perf_counter() - t0
-            st = srv.stats()
-            out["rates"].append({
-                "rate_req_s": rate, "requests": len(reqs), "wall_s": wall,
-                "throughput_req_s": len(reqs) / wall, "throughput_GB_s": nbytes / wall / 1e9,
-                "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
-                "max_ms": st["max_ms"], "resident_hits": st["resident_hits"],
-                "evictions": st["evictions"]})
+            out["rates"].append(_serve_rate(R, srv, fields, prm, rate, n_req,
+                                            synth.seed_for(5, 100 + k), max_s, population))
+    small = pop_bytes // 4
+    with R.Server(0, slots=4, window=16, hbm_budget=small) as srv:
+        ev = _serve_rate(R, srv, fields, prm, evict_rate, n_req, synth.seed_for(5, 200), max_s,
+                         population)
+    ev["hbm_budget_bytes"] = small
+    out["evicting"] = ev
     del fields
     return out
 
@@ -786,7 +814,8 @@ def main():
                                          args.batch_subset)
     if not args.no_serve and world == 1:
         rates = [float(v) for v in args.serve_rates.split(",") if v]
-        line["serving"] = bench_serving(R, args.serve_population, args.serve_requests, rates)
+        line["serving"] = bench_serving(R, args.serve_population, args.serve_requests, rates,
+                                        max_s=args.serve_seconds)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(x.cpu().numpy(), args.cpu_planes, 1, all_cores=True)
     if rank == 0:

@@ -1,12 +1,16 @@
 """The serving loop (rd_server_*) through the C ABI: requests served
 concurrently, with resident fields admitted and evicted under an HBM
-budget, give each the same record as rd_select on the field alone; errors
-stay with their request; the counters and latency percentiles add up."""
+budget, give each the same record as rd_select on the field alone and as
+the oracle (integers and singly rounded doubles exact, PSNR within 1e-6,
+entropy within 1e-10 relative); errors stay with their request; the
+counters and latency percentiles add up."""
 import numpy as np
 import pytest
 
 import synth
+from test_gpu_parity import check_result
 
+O = pytest.importorskip("oracle")
 torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
@@ -66,10 +70,15 @@ def test_mixed_requests_match_alone(R):
             got += srv.poll(64, wait_ms=2000)
         st = srv.stats()
     assert len(got) == len(want)
+    oracle = {}
     for c in got:
         assert c["status"] == 0, c
         i, j = want[c["request_id"]]
         assert c["result"] == alone[(i, j)], (i, j)
+        if (i, j) not in oracle:
+            eb, r_sp = SETTINGS[j]
+            oracle[(i, j)] = O.select(POP[i], O.params(eb=eb, r_sp=r_sp))
+        check_result(c["result"], oracle[(i, j)], POP[i].ndim)
         assert c["latency_ms"] >= c["service_ms"] >= 0.0 and c["queue_ms"] >= 0.0
     assert st["submitted"] == st["completed"] == len(want)
     assert st["evictions"] > 0 and st["resident_hits"] > 0
