@@ -5,151 +5,21 @@
 // One thread holding a whole 4^3 block needs its 64 values and 64
 // coefficients in registers (about 250 of them), which leaves one SM eight
 // resident warps and nothing to hide the latency of the integer chains.
-// Here the four lanes q = 0..3 of a quad share a block:
-//   slice layout  lane q holds the plane z = q (16 values, x fastest): the
-//                 lifting along x and y runs in its registers;
-//   line layout   lane q holds the row y = q of every plane (z, q, 0..3):
-//                 the lifting along z runs in its registers.  A transpose in
-//                 shared memory (four 16-byte stores and loads per lane)
-//                 turns one layout into the other;
-//   rank layout   the embedded-coding cost and the estimator's interpolated
-//                 sum walk the coefficients in sequency order: each lane
-//                 writes the leading-one position of its 16 coefficients as
-//                 bytes at their sequency ranks, and lane q reads ranks
-//                 16q .. 16q+15 back in one 16-byte load.  The suffix maximum
-//                 over ranks is the lane's own running maximum seeded with
-//                 the maxima of the lanes above it (two shuffles).
-// A warp takes eight consecutive blocks (eight quads) per step, so each of
-// its 16-byte loads reads four whole 128-byte rows.  Every integer result
-// (exponents, coefficients, bits, the estimator's sums) is the one thread-
-// per-block computation's, term for term; only the float32 sum of squared
-// errors is added in another order.
+// Here the four lanes of a quad share a block, in the slice, line and rank
+// layouts of rd_zfp3_dev.cuh.  A warp takes eight consecutive blocks (eight
+// quads) per step, so each of its 16-byte loads reads four whole 128-byte
+// rows.  Every integer result (exponents, coefficients, bits, the
+// estimator's sums) is the one thread-per-block computation's, term for
+// term; only the float32 sum of squared errors is added in another order.
 #include <stdint.h>
 
 #include "rd_delta.cuh"
-#include "rd_zfp_dev.cuh"
+#include "rd_zfp3_dev.cuh"
 
 namespace rdk {
 
 constexpr int kZ3Threads = 256;
 constexpr int kZ3Warps = kZ3Threads / 32;
-constexpr int kZ3SliceWords = 20;  // a 4x4 slice plus 4 words of padding (no bank conflicts)
-constexpr int kZ3BlockWords = 4 * kZ3SliceWords;
-// a block's 64 rank bytes plus 16 bytes of padding: the eight blocks of a
-// warp start 20 words apart, so byte stores of one rank by the eight quads
-// fall in different banks
-constexpr int kZ3RankBytes = 80;
-constexpr unsigned kFull = 0xffffffffu;
-
-// Per-lane constants of the layouts, built at compile time from the
-// sequency order and the EC sample positions of a 3D block.
-struct Z3Tables {
-  uint32_t rank[4][4];    // [q][z]: byte x = sequency rank of block index 16z + 4q + x
-  uint32_t wpaper[4][4];  // [q][k]: byte b = weight of rank 16q + 4k + b in the doubled S2 sum
-  uint32_t ecmask[4];     // [q]: bit 4z + x set when block index 16z + 4q + x is EC-sampled
-  constexpr Z3Tables() : rank(), wpaper(), ecmask() {
-    const Sequency<3> S{};
-    const EcPositions<3> EC{};
-    int rk[64] = {};
-    for (int p = 0; p < 64; p++) rk[S.perm[p]] = p;
-    int w[64] = {};
-    bool isec[64] = {};
-    // S2 = sum_j [(L_j + 1) n(p_j) + (L_j - 1) n(p_{j+1})] + 2 n(p_last):
-    // each EC position's weight is its share of the interpolated sum
-    for (int j = 0; j < EcPositions<3>::M; j++) {
-      int wt = j + 1 < EcPositions<3>::M ? EC.pos[j + 1] - EC.pos[j] + 1 : 2;
-      if (j > 0) wt += EC.pos[j] - EC.pos[j - 1] - 1;
-      w[EC.pos[j]] = wt;
-      isec[EC.pos[j]] = true;
-    }
-    for (int q = 0; q < 4; q++) {
-      uint32_t m = 0u;
-      for (int z = 0; z < 4; z++) {
-        uint32_t word = 0u;
-        for (int x = 0; x < 4; x++) {
-          const int r = rk[16 * z + 4 * q + x];
-          word |= (uint32_t)r << (8 * x);
-          if (isec[r]) m |= 1u << (4 * z + x);
-        }
-        rank[q][z] = word;
-      }
-      ecmask[q] = m;
-      for (int k = 0; k < 4; k++) {
-        uint32_t word = 0u;
-        for (int b = 0; b < 4; b++) word |= (uint32_t)w[16 * q + 4 * k + b] << (8 * b);
-        wpaper[q][k] = word;
-      }
-    }
-  }
-};
-
-__device__ __forceinline__ uint32_t pick_q(int q, uint32_t a0, uint32_t a1, uint32_t a2,
-                                           uint32_t a3) {
-  return q == 0 ? a0 : q == 1 ? a1 : q == 2 ? a2 : a3;
-}
-
-// A position in a 3-axis mixed radix (slowest first), advanced by a fixed
-// stride without divisions.
-struct Radix3 {
-  int a0, a1, a2;
-  __device__ __forceinline__ void set(long long u, const int* R) {
-    a2 = (int)(u % R[2]);
-    u /= R[2];
-    a1 = (int)(u % R[1]);
-    a0 = (int)(u / R[1]);
-  }
-  // add a stride given as digits (each below its radix)
-  __device__ __forceinline__ void add(const Radix3& s, const int* R) {
-    a2 += s.a2;
-    int c = a2 >= R[2];
-    a2 -= c ? R[2] : 0;
-    a1 += s.a1 + c;
-    c = a1 >= R[1];
-    a1 -= c ? R[1] : 0;
-    a0 += s.a0 + c;
-  }
-};
-
-// Load plane z = 4 b0 + q of a block (clamped to the last plane, rows and
-// columns clamped likewise: partial blocks replicate their last sample).
-__device__ __forceinline__ void load_slice(const FieldDev& f, int b0, int b1, int b2, int q,
-                                           bool act, bool interior, float* v) {
-  if (!act) {
-#pragma unroll
-    for (int i = 0; i < 16; i++) v[i] = 0.0f;
-    return;
-  }
-  const float* __restrict__ x = f.x;
-  const int z = min(4 * b0 + q, f.n[0] - 1);
-  const int y0 = 4 * b1, x0 = 4 * b2;
-  if (interior && f.vec_ok) {
-    // point indices stay below 2^31
-    const float* p0 = x + ((z * f.n[1] + y0) * f.n[2] + x0);
-#pragma unroll
-    for (int r = 0; r < 4; r++) {
-      const float4 t = __ldg(reinterpret_cast<const float4*>(p0 + r * f.n[2]));
-      v[4 * r + 0] = t.x;
-      v[4 * r + 1] = t.y;
-      v[4 * r + 2] = t.z;
-      v[4 * r + 3] = t.w;
-    }
-  } else {
-#pragma unroll
-    for (int r = 0; r < 4; r++) {
-      const int y = min(y0 + r, f.n[1] - 1);
-      const long long row = ((long long)z * f.n[1] + y) * f.n[2];
-#pragma unroll
-      for (int j = 0; j < 4; j++) v[4 * r + j] = __ldg(x + row + min(x0 + j, f.n[2] - 1));
-    }
-  }
-}
-
-// Block coordinate b is on axis k's sampling lattice (a multiple of s[k]).
-__device__ __forceinline__ bool on_stride(const FieldDev& f, int k, int b) {
-  if (f.ssh[k] < 0) return true;
-  const unsigned qt = __umulhi((unsigned)b, f.smag[k]) >> f.ssh[k];
-  return (int)qt * f.s[k] == b;
-}
 
 template <bool GT, bool EST>
 __global__ void __launch_bounds__(kZ3Threads) k_zfp3(FieldDev f, ParamsDev p, DeltaArgs da,
@@ -177,22 +47,7 @@ __global__ void __launch_bounds__(kZ3Threads) k_zfp3(FieldDev f, ParamsDev p, De
   // the layouts' per-lane constants, by q: ranks (4 words), S2 weights (4
   // words) and the EC mask, read from shared memory where used
   __shared__ uint32_t s_tab[4][12];
-  if (threadIdx.x < 48) {
-    constexpr Z3Tables T{};
-    const int tq = threadIdx.x / 12, k = threadIdx.x % 12;
-    const bool ec_all = p.ec_mode == RD_EC_ALL;
-    uint32_t v = 0u;
-#pragma unroll
-    for (int a = 0; a < 4; a++) {
-#pragma unroll
-      for (int z = 0; z < 4; z++) {
-        if (a == tq && z == k) v = T.rank[a][z];
-        if (a == tq && z + 4 == k) v = ec_all ? 0x02020202u : T.wpaper[a][z];
-      }
-      if (a == tq && k == 8) v = ec_all ? 0xffffu : T.ecmask[a];
-    }
-    s_tab[tq][k] = v;
-  }
+  quad_fill_tables(s_tab, p.ec_mode == RD_EC_ALL);
   __syncthreads();
   const uint32_t* tab = s_tab[q];
 
@@ -243,120 +98,30 @@ __global__ void __launch_bounds__(kZ3Threads) k_zfp3(FieldDev f, ParamsDev p, De
     {
       float v[16];
       load_slice(f, b0, b1, b2, q, act, interior, v);
-      // block exponent (zfp fixed-accuracy rule): the largest magnitude's
-      // exponent field over the quad
-      float am = 0.0f;
-#pragma unroll
-      for (int i = 0; i < 16; i++) am = fmaxf(am, fabsf(v[i]));
-      am = fmaxf(am, __shfl_xor_sync(kFull, am, 1));
-      am = fmaxf(am, __shfl_xor_sync(kFull, am, 2));
-      const unsigned m = __float_as_uint(am);
-      const unsigned E = m >> 23;
-      emax = m == 0u ? -127 : (E == 0u ? -126 : (int)E - 126);
-      // block-floating-point cast trunc(x 2^sh) (values are read again for
-      // the errors); 2^sh as one factor, or two when sh > 127
-      const int sh = 30 - emax;
-      if (m == 0u) {
-#pragma unroll
-        for (int i = 0; i < 16; i++) c[i] = 0;
-      } else if (sh <= 127) {
-        const float scl = pow2f(sh);
-#pragma unroll
-        for (int i = 0; i < 16; i++) c[i] = __float2int_rz(__fmul_rn(v[i], scl));
-      } else {
-        const float scl = pow2f(sh - 127);
-#pragma unroll
-        for (int i = 0; i < 16; i++) c[i] = __float2int_rz(__fmul_rn(__fmul_rn(v[i], pow2f(127)), scl));
-      }
+      emax = quad_emax(v);
+      quad_cast(v, emax, c);
     }
     const bool all_zero = emax == -127;
     const int prec = all_zero ? 0 : min(32, max(0, emax - minexp + 8));
     const int kmin = 32 - prec;
-
-    // lifting along x and y (slice layout)
-#pragma unroll
-    for (int y = 0; y < 4; y++) fwd_lift(c[4 * y], c[4 * y + 1], c[4 * y + 2], c[4 * y + 3]);
-#pragma unroll
-    for (int x = 0; x < 4; x++) fwd_lift(c[x], c[4 + x], c[8 + x], c[12 + x]);
-
-    // slice -> line layout
-#pragma unroll
-    for (int y = 0; y < 4; y++)
-      *reinterpret_cast<int4*>(tr + q * kZ3SliceWords + 4 * y) =
-          make_int4(c[4 * y], c[4 * y + 1], c[4 * y + 2], c[4 * y + 3]);
-    __syncwarp();
-#pragma unroll
-    for (int z = 0; z < 4; z++) {
-      const int4 t = *reinterpret_cast<const int4*>(tr + z * kZ3SliceWords + 4 * q);
-      c[4 * z] = t.x;
-      c[4 * z + 1] = t.y;
-      c[4 * z + 2] = t.z;
-      c[4 * z + 3] = t.w;
-    }
-    __syncwarp();
-    // lifting along z, then negabinary (c[4z + x] is block index 16z + 4q + x)
-#pragma unroll
-    for (int x = 0; x < 4; x++) fwd_lift(c[x], c[4 + x], c[8 + x], c[12 + x]);
     unsigned uu[16];
-#pragma unroll
-    for (int i = 0; i < 16; i++) uu[i] = to_negabinary(c[i]);
+    quad_transform(c, q, tr, uu);
 
     // estimator: exact squared truncation errors of the EC-sampled
     // coefficients, binned by the block exponent
     bool est_has = false;
     unsigned long long lo = 0ull, hi = 0ull;
     if (EST && sampled) {
-      const uint32_t ecm = tab[8];
-#pragma unroll
-      for (int i = 0; i < 16; i++)
-        if ((ecm >> i) & 1u) zfp_add_err(uu[i], kmin, lo, hi);
+      quad_est_err(uu, kmin, tab[8], lo, hi);
       est_has = !all_zero && (lo | hi);
     }
     if (EST) mse_add_warp(est_has, mse_bin<3>(emax), lo, hi, s_lo, s_hi);
 
-    // truncation to the coded planes; a coefficient whose leading one is
-    // below them counts as zero in every sum that follows
-    const unsigned keep = kmin >= 32 ? 0u : (0xffffffffu << kmin);
-#pragma unroll
-    for (int i = 0; i < 16; i++) uu[i] &= keep;
-
-    // rank layout: leading-one position + 1 (0 for a zero coefficient)
-#pragma unroll
-    for (int z = 0; z < 4; z++) {
-      const uint32_t rz = tab[z];
-#pragma unroll
-      for (int x = 0; x < 4; x++)
-        rb[(rz >> (8 * x)) & 0xffu] = (unsigned char)(32 - __clz((int)uu[4 * z + x]));
-    }
-    __syncwarp();
-    const uint4 cw = *reinterpret_cast<const uint4*>(rb + 16 * q);
-    __syncwarp();
-    const uint32_t cws[4] = {cw.x, cw.y, cw.z, cw.w};
+    // truncation to the coded planes, then the rank layout
     int cr[16];
-#pragma unroll
-    for (int j = 0; j < 16; j++) cr[j] = (int)((cws[j >> 2] >> (8 * (j & 3))) & 0xffu);
-    int lmax = 0;
-#pragma unroll
-    for (int j = 0; j < 16; j += 2) lmax = max(lmax, max(cr[j], cr[j + 1]));
-    // maximum over the ranks above this lane's (lanes q+1 .. 3 of the quad)
-    int s1 = __shfl_down_sync(kFull, lmax, 1);
-    s1 = q < 3 ? s1 : 0;
-    int s2 = __shfl_down_sync(kFull, max(lmax, s1), 2);
-    s2 = q < 2 ? s2 : 0;
-    const int seed = max(s1, s2);
+    const int seed = quad_rank(uu, kmin, q, tab, rb, cr);
 
-    if (EST && sampled) {
-      // doubled interpolated n_sb sum: every rank's weight times its n_sb
-      unsigned s2sum = 0u;
-#pragma unroll
-      for (int k = 0; k < 4; k++) {
-        const uint32_t wk = tab[4 + k];
-#pragma unroll
-        for (int b = 0; b < 4; b++)
-          s2sum += ((wk >> (8 * b)) & 0xffu) * (unsigned)max(0, cr[4 * k + b] - kmin);
-      }
-      my_s2 += s2sum;
-    }
+    if (EST && sampled) my_s2 += quad_s2(cr, kmin, tab);
 
     if (GT) {
       // exact group-test embedded-coding cost (the suffix-maximum closed
