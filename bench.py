@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="longest span of arrivals per rate")
     ap.add_argument("--serve-rates", default="50,100,200,500,1000,2000")
+    ap.add_argument("--source-hashes", action="store_true",
+                    help="print the source hash of each profiled kernel and exit")
     return ap.parse_args()
 
 
@@ -79,19 +81,26 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-# Translation units of the kernels that profiles/ and traffic.json describe
-# (range, ZFP, SZ, Huffman and batched passes, classic truth tiles).
-PROFILED_UNITS = ("rd_reduce.cu", "rd_zfp.cu", "rd_sz.cu", "rd_sz_tma.cu", "rd_batch.cu",
-                  "rd_sz_classic.cu")
+# Translation units of each kernel that profiles/ and traffic.json describe;
+# a kernel's recorded DRAM traffic holds only while the hash of its units
+# (and the package headers they include) is the one recorded beside it.
+KERNEL_UNITS = {
+    "range": ("rd_reduce.cu",),
+    "huffman": ("rd_reduce.cu",),
+    "zfp_pass": ("rd_zfp.cu", "rd_zfp3.cu"),
+    "sz_pass": ("rd_sz.cu", "rd_sz_tma.cu"),
+    "batch": ("rd_batch.cu",),
+    "classic": ("rd_sz_classic.cu",),
+}
 
 
-def kernel_source_hash() -> str:
-    """Hash of the sources the profiled kernels are compiled from: their
+def kernel_source_hash(kernel: str) -> str:
+    """Hash of the sources one profiled kernel is compiled from: its
     translation units and every header they include, followed through the
     package's own headers (the public header included)."""
     csrc = os.path.join(ROOT, "paper_1806_08901_gb300", "csrc")
     inc = os.path.join(ROOT, "include")
-    seen, todo = [], list(PROFILED_UNITS)
+    seen, todo = [], list(KERNEL_UNITS[kernel])
     while todo:
         fn = todo.pop(0)
         if fn in seen:
@@ -121,7 +130,7 @@ def recorded_traffic(kernel: str):
     with open(path) as f:
         d = json.load(f)
     rec = d.get(WORKLOAD, {}).get(kernel)
-    if not rec or rec.get("source_hash") != kernel_source_hash():
+    if not rec or kernel not in KERNEL_UNITS or rec.get("source_hash") != kernel_source_hash(kernel):
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -673,6 +682,9 @@ def weak_scaling_value(nbytes_per_rank: int, steps: int, world: int, max_ms: flo
 
 def main():
     args = parse()
+    if args.source_hashes:
+        print(json.dumps({k: kernel_source_hash(k) for k in KERNEL_UNITS}))
+        return
     if args.impl == "reference":
         run_reference(args)
         return
