@@ -32,9 +32,13 @@ struct MarchGeom {
   long long ntiles;
 };
 
-constexpr int kGtWin = 8192;   // shared histogram window of the ground truth
+// Shared histogram windows of the ground truth and of the estimator; codes
+// outside a window go to the global histogram.  Their sizes and the stages
+// fit four CTAs per SM: the ground truth codes every point, the estimator
+// only the sampled ones, so the estimator's window is the small one.
+constexpr int kGtWin = 8192;
 constexpr int kGtWinLo = kCenter - kGtWin / 2;
-constexpr int kEstWin = 2048;  // and of the estimator
+constexpr int kEstWin = 1024;
 constexpr int kEstWinLo = kCenter - kEstWin / 2;
 constexpr long long kWaitLimit = 1ll << 24;  // bounded mbarrier polling
 
@@ -415,11 +419,12 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 3D fields: 64 x 16 tiles, 4 rows per thread, two planes per step, three
-// steps in flight (one barrier per step).
+// 3D fields: 64 x 16 tiles, 4 rows per thread, two planes per step, two
+// steps in flight (one barrier per step); 55 KB of shared memory per CTA,
+// four CTAs per SM.
 // 2D fields (walked as rows x 1 x cols): 128-column tiles, 16 rows per step
 // (a tensor box spans at most 256 elements per axis).
-constexpr int k3TX = 64, k3TY = 16, k3R = 4, k3PZ = 2, k3NST = 3;
+constexpr int k3TX = 64, k3TY = 16, k3R = 4, k3PZ = 2, k3NST = 2;
 using Cfg3 = MarchCfg<k3TX, k3TY, k3R, k3PZ, k3NST>;
 using Cfg2 = MarchCfg<128, 1, 1, 16, 4>;
 
