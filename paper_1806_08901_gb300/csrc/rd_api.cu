@@ -355,8 +355,8 @@ int issue(rd_context* c, const CallKey& k, const Geometry& g, cudaStream_t s) {
   int hist_mask = ((passes & P_SZ_EST) ? 1 : 0) | ((passes & (P_SZ_GT | P_SZ_CLASSIC)) ? 2 : 0);
   const int fin_passes = classic ? (passes | P_SZ_GT) : passes;
   if (hist_mask) {
-    if ((rc = launch(c, K_CODE_PREP, s, [&] { return launch_code_prep(ws, hist_mask, s); }))) return rc;
-    if ((rc = launch(c, K_HUFFMAN, s, [&] { return launch_huffman(ws, hist_mask, c->xlogx, s); }))) return rc;
+    if ((rc = launch(c, K_CODE_PREP, s, [&] { return launch_code_prep(ws, hist_mask, c->xlogx, s); }))) return rc;
+    if ((rc = launch(c, K_HUFFMAN, s, [&] { return launch_huffman(ws, hist_mask, s); }))) return rc;
   }
   if ((rc = launch(c, K_FINISH, s, [&] {
          return launch_finish(p, ws, fin_passes, zfp_parts, sz_parts, f.N, g.npoints_sampled, s);
@@ -688,9 +688,9 @@ int issue_batch_estimate(rd_context* c, BatchPlan* b, cudaStream_t s, cudaEvent_
        })))
     return rc;
   if (ev) cudaEventRecord(ev[1], s);
-  if ((rc = launch(c, K_B_PREP, s, [&] { return launch_batch_code_prep(b->dbf, n, s); }))) return rc;
+  if ((rc = launch(c, K_B_PREP, s, [&] { return launch_batch_code_prep(b->dbf, n, c->xlogx, s); }))) return rc;
   return launch(c, K_B_FINAL, s, [&] {
-    return launch_batch_final(b->dbf, n, c->xlogx, c->d_bres, c->d_bstatus, s);
+    return launch_batch_final(b->dbf, n, c->d_bres, c->d_bstatus, s);
   });
 }
 
@@ -717,8 +717,8 @@ int issue_batch(rd_context* c, BatchPlan* b, cudaStream_t s) {
              return launch_sz_gt(f, p, 0, ws, c->sz_ctas[d], s, &sparts);
            })))
         return rc;
-      if ((rc = launch(c, K_CODE_PREP, s, [&] { return launch_code_prep(ws, 2, s); }))) return rc;
-      if ((rc = launch(c, K_HUFFMAN, s, [&] { return launch_huffman(ws, 2, c->xlogx, s); }))) return rc;
+      if ((rc = launch(c, K_CODE_PREP, s, [&] { return launch_code_prep(ws, 2, c->xlogx, s); }))) return rc;
+      if ((rc = launch(c, K_HUFFMAN, s, [&] { return launch_huffman(ws, 2, s); }))) return rc;
       if ((rc = launch(c, K_FINISH, s, [&] {
              return launch_finish(p, ws, P_ZFP_GT | P_SZ_GT, zparts, sparts, f.N, npts, s);
            })))
@@ -1043,8 +1043,8 @@ int estimate_sz_log(rd_context* c, const rd_field* fld, const rd_params* prm, rd
   if (e != cudaSuccess) return cuda_status(e);
   if ((rc = launch(c, K_SZ_LOG, s, [&] { return launch_sz_log_hist(f, n, c->log_f, ws, ctas, s); })))
     return rc;
-  if ((rc = launch(c, K_CODE_PREP, s, [&] { return launch_code_prep(ws, 1, s); }))) return rc;
-  if ((rc = launch(c, K_HUFFMAN, s, [&] { return launch_huffman(ws, 1, c->xlogx, s); }))) return rc;
+  if ((rc = launch(c, K_CODE_PREP, s, [&] { return launch_code_prep(ws, 1, c->xlogx, s); }))) return rc;
+  if ((rc = launch(c, K_HUFFMAN, s, [&] { return launch_huffman(ws, 1, s); }))) return rc;
   if ((rc = launch(c, K_FINISH, s,
                    [&] { return launch_sz_log_finish(p, c->log_a, ws, c->log_dev, s); })))
     return rc;

@@ -61,6 +61,7 @@ struct Workspace {
   Scalars sc;
   alignas(16) uint32_t hist[2][kNsym];          // 0 = SZ estimate, 1 = SZ ground truth
   double ent_part[2][kEntropyCtas];             // partial sums of h log2 h
+  unsigned long long ns_part[2][kEntropyCtas];  // partial sums of h
   HuffOut huff[2];
   double zfp_sse[kMaxGrid];                     // per-CTA partial sums (fixed order)
   double sz_sse[kMaxGrid];
@@ -213,8 +214,8 @@ cudaError_t launch_sz_gt(const FieldDev& f, const ParamsDev& p, int with_est,
 // cost (launch_huffman), of the histograms in which_mask (bit 0 = estimate,
 // bit 1 = ground truth); launch_code_stats issues both.  prepare_code_stats()
 // once per device first.
-cudaError_t launch_code_prep(Workspace* ws, int which_mask, cudaStream_t s);
-cudaError_t launch_huffman(Workspace* ws, int which_mask, const double* xlogx, cudaStream_t s);
+cudaError_t launch_code_prep(Workspace* ws, int which_mask, const double* xlogx, cudaStream_t s);
+cudaError_t launch_huffman(Workspace* ws, int which_mask, cudaStream_t s);
 cudaError_t launch_code_stats(Workspace* ws, int which_mask, const double* xlogx, cudaStream_t s);
 cudaError_t prepare_code_stats();
 cudaError_t launch_finish(const ParamsDev& p, Workspace* ws, int passes,
@@ -260,11 +261,11 @@ cudaError_t launch_batch_sz_hist(const BatchField* bf, const BatchItem* items, i
 // resident CTAs of the item-based passes
 // (blocks_ctas: one count per dimensionality 1..3)
 void batch_occupancy(int num_sms, int* range_ctas, int* blocks_ctas, int* sz_ctas);
-cudaError_t launch_batch_code_prep(const BatchField* bf, int n, cudaStream_t s);
+cudaError_t launch_batch_code_prep(const BatchField* bf, int n, const double* xlogx, cudaStream_t s);
 // Huffman cost, entropy and finish of every field; result records and
 // statuses gathered into res[n] and status[n]
-cudaError_t launch_batch_final(const BatchField* bf, int n, const double* xlogx, rd_result* res,
-                               int32_t* status, cudaStream_t s);
+cudaError_t launch_batch_final(const BatchField* bf, int n, rd_result* res, int32_t* status,
+                               cudaStream_t s);
 // ground-truth records and final statuses of a batch, gathered
 cudaError_t launch_batch_truth(const BatchField* bf, int n, rd_truth* truth, int32_t* status,
                                cudaStream_t s);

@@ -324,17 +324,20 @@ cudaError_t launch_init_tables(double* xlogx, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// Prep (kEntropyCtas CTAs per histogram, 1024 bins each, integer work only):
-// the multiplicity of every count value below 2^16 (a counting sort of the
-// counts; lanes holding equal counts merge into one atomic), a bitmap of the
-// count values present, and the counts of 2^16 or more (at most N / 2^16 of
-// them) appended to a list, with their share c log2 c of the entropy sum.
+// Prep (kEntropyCtas CTAs per histogram, 1024 bins each): the multiplicity
+// of every count value below 2^16 (a counting sort of the counts; lanes
+// holding equal counts merge into one atomic), a bitmap of the count values
+// present, the counts of 2^16 or more (at most N / 2^16 of them) appended
+// to a list, and the slice's shares of N_s = sum c and of the entropy sum
+// sum c log2 c (from the table below 2^16), each summed in a fixed order.
 // ---------------------------------------------------------------------------
 // With kClear, every nonzero bin read is set back to zero, except bin 0 (the
 // escape count, read by the finish step).
 template <bool kClear>
-__device__ __forceinline__ void code_prep_slice(Workspace* ws, int which, int slice) {
+__device__ __forceinline__ void code_prep_slice(Workspace* ws, int which, int slice,
+                                                const double* __restrict__ xlogx) {
   __shared__ double part[kPrepThreads / 32];
+  __shared__ unsigned long long npart[kPrepThreads / 32];
   if (ws->sc.status != RD_OK || ws->sc.constant) return;
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -342,13 +345,24 @@ __device__ __forceinline__ void code_prep_slice(Workspace* ws, int which, int sl
   uint32_t* present = ws->present[which];
   uint32_t* big = ws->node_scratch[which];
   double v = 0.0;
+  unsigned long long nsum = 0ull;
+  constexpr int kPer = 1024 / kPrepThreads;
+  // the bins and their table entries loaded together, ahead of the atomics
+  uint32_t cs[kPer];
+  double xs[kPer];
 #pragma unroll
-  for (int k = 0; k < 1024 / kPrepThreads; k++) {
+  for (int k = 0; k < kPer; k++) cs[k] = ws->hist[which][slice * 1024 + k * kPrepThreads + threadIdx.x];
+#pragma unroll
+  for (int k = 0; k < kPer; k++) xs[k] = (cs[k] != 0u && cs[k] < (uint32_t)kNsym) ? xlogx[cs[k]] : 0.0;
+#pragma unroll
+  for (int k = 0; k < kPer; k++) {
     const int bin = slice * 1024 + k * kPrepThreads + threadIdx.x;
-    const uint32_t c = ws->hist[which][bin];
+    const uint32_t c = cs[k];
     if (kClear && c != 0u && bin != 0) ws->hist[which][bin] = 0u;
     const bool small = c != 0u && c < (uint32_t)kNsym;
     const bool large = c >= (uint32_t)kNsym;
+    nsum += c;
+    v += xs[k];
     const unsigned ms = __ballot_sync(0xffffffffu, small);
     const unsigned mb = __ballot_sync(0xffffffffu, large);
     if (small) {
@@ -369,17 +383,27 @@ __device__ __forceinline__ void code_prep_slice(Workspace* ws, int which, int sl
     }
   }
   v = warp_sum(v);
-  if (lane == 0) part[threadIdx.x >> 5] = v;
+  nsum = warp_sum(nsum);
+  if (lane == 0) {
+    part[threadIdx.x >> 5] = v;
+    npart[threadIdx.x >> 5] = nsum;
+  }
   __syncthreads();
   if (threadIdx.x < 32) {
-    const double t = warp_sum(threadIdx.x < kPrepThreads / 32 ? part[threadIdx.x] : 0.0);
-    if (threadIdx.x == 0) ws->ent_part[which][slice] = t;
+    const bool in = threadIdx.x < kPrepThreads / 32;
+    const double t = warp_sum(in ? part[threadIdx.x] : 0.0);
+    const unsigned long long nt = warp_sum(in ? npart[threadIdx.x] : 0ull);
+    if (threadIdx.x == 0) {
+      ws->ent_part[which][slice] = t;
+      ws->ns_part[which][slice] = nt;
+    }
   }
 }
 
-__global__ void __launch_bounds__(kPrepThreads) k_code_prep(Workspace* ws, int which_mask) {
+__global__ void __launch_bounds__(kPrepThreads) k_code_prep(Workspace* ws, int which_mask,
+                                                            const double* __restrict__ xlogx) {
   const int first = (which_mask & 1) ? 0 : 1;
-  code_prep_slice<false>(ws, first + blockIdx.x / kEntropyCtas, blockIdx.x % kEntropyCtas);
+  code_prep_slice<false>(ws, first + blockIdx.x / kEntropyCtas, blockIdx.x % kEntropyCtas, xlogx);
 }
 
 // Block-wide scans and sums for kHuffThreads threads (32 warps); s_w holds
@@ -444,15 +468,6 @@ __device__ unsigned long long block_sum_u64(unsigned long long v, unsigned long 
   if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
   __syncthreads();
   const unsigned long long t = warp_sum(s_w[threadIdx.x & 31]);
-  __syncthreads();
-  return t;
-}
-
-__device__ double block_sum_f64(double v, double* s_w) {
-  v = warp_sum(v);
-  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
-  __syncthreads();
-  const double t = warp_sum(s_w[threadIdx.x & 31]);
   __syncthreads();
   return t;
 }
@@ -586,8 +601,8 @@ __device__ unsigned long long huffman_runs(const uint32_t* dv, uint32_t D, const
 // Huffman cost and entropy sum (one CTA per histogram).
 //  1. The bitmap of present count values gives each its rank d in ascending
 //     order; the D distinct values and their multiplicities (packed as
-//     v << 16 | (m - 1)) are gathered in that order.  The entropy sum is
-//     sum m v log2 v over them, from the table, plus the large counts' share.
+//     v << 16 | (m - 1)) are gathered in that order.  N_s and the entropy
+//     sum are the code prep's per-slice shares added in a fixed order.
 //  2. The ascending leaf array: the first position of every distinct value
 //     is marked with the value and a running maximum over positions fills
 //     each run; the large counts follow, sorted by a bitonic network.
@@ -600,7 +615,7 @@ __device__ unsigned long long huffman_runs(const uint32_t* dv, uint32_t D, const
 // a ring, in shared memory (huffman_runs), when the runs fit; otherwise the
 // linear queues live in the workspace in global memory.
 // ---------------------------------------------------------------------------
-__device__ void huffman_cta(Workspace* ws, int which, const double* __restrict__ xlogx) {
+__device__ void huffman_cta(Workspace* ws, int which) {
   extern __shared__ uint32_t s_dyn[];
   __shared__ uint32_t s_w[32];
   __shared__ unsigned long long s_w64[32];
@@ -612,7 +627,8 @@ __device__ void huffman_cta(Workspace* ws, int which, const double* __restrict__
   // 1. distinct values in ascending order
   const uint2 pw = reinterpret_cast<const uint2*>(ws->present[which])[tid];
   const uint32_t nbig = ws->nbig[which];
-  double ent = tid < kEntropyCtas ? ws->ent_part[which][tid] : 0.0;
+  const double ent = tid < kEntropyCtas ? ws->ent_part[which][tid] : 0.0;
+  const unsigned long long nsum = tid < kEntropyCtas ? ws->ns_part[which][tid] : 0ull;
   uint32_t D;
   const uint32_t dbase = block_excl_sum(__popc(pw.x) + __popc(pw.y), s_w, &D);
   uint32_t* dv = (D <= (uint32_t)kHuffSmemKeys) ? s_dyn + kHuffSmemKeys : ws->distinct[which];
@@ -623,10 +639,8 @@ __device__ void huffman_cta(Workspace* ws, int which, const double* __restrict__
   }
   __syncthreads();
   uint32_t msum = 0u;
-  unsigned long long nsum = 0ull;
   for (uint32_t d0 = tid; d0 < D; d0 += 4u * kHuffThreads) {
     uint32_t vv[4], mm[4];
-    double xl[4];
 #pragma unroll
     for (int u = 0; u < 4; u++) {
       const uint32_t d = d0 + (uint32_t)u * kHuffThreads;
@@ -636,7 +650,6 @@ __device__ void huffman_cta(Workspace* ws, int which, const double* __restrict__
     for (int u = 0; u < 4; u++) {
       const uint32_t d = d0 + (uint32_t)u * kHuffThreads;
       mm[u] = d < D ? cc[vv[u]] : 0u;
-      xl[u] = d < D ? xlogx[vv[u]] : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < 4; u++) {
@@ -644,17 +657,30 @@ __device__ void huffman_cta(Workspace* ws, int which, const double* __restrict__
       if (d < D) {
         dv[d] = (vv[u] << 16) | (mm[u] - 1u);
         msum += mm[u];
-        nsum += (unsigned long long)mm[u] * vv[u];
-        ent += (double)mm[u] * xl[u];
       }
     }
   }
   const uint32_t* big = ws->node_scratch[which];
-  for (uint32_t i = tid; i < nbig; i += kHuffThreads) nsum += big[i];
+  // the number of small symbols, N_s and the entropy sum: one fixed-order
+  // block reduction of the three
   uint32_t nsmall;
-  (void)block_excl_sum(msum, s_w, &nsmall);
-  const unsigned long long ns = block_sum_u64(nsum, s_w64);
-  const double plogp = block_sum_f64(ent, s_wd);
+  unsigned long long ns;
+  double plogp;
+  {
+    const uint32_t a = warp_sum(msum);
+    const unsigned long long b = warp_sum(nsum);
+    const double c = warp_sum(ent);
+    if ((tid & 31) == 0) {
+      s_w[tid >> 5] = a;
+      s_w64[tid >> 5] = b;
+      s_wd[tid >> 5] = c;
+    }
+    __syncthreads();
+    nsmall = warp_sum(s_w[tid & 31]);
+    ns = warp_sum(s_w64[tid & 31]);
+    plogp = warp_sum(s_wd[tid & 31]);
+    __syncthreads();
+  }
   const uint32_t K = nsmall + nbig;
 
   unsigned long long cost = 0ull;
@@ -773,32 +799,30 @@ __device__ void huffman_cta(Workspace* ws, int which, const double* __restrict__
   }
 }
 
-__global__ void __launch_bounds__(kHuffThreads) k_huffman(Workspace* ws, int which0,
-                                                          const double* xlogx) {
-  huffman_cta(ws, which0 + blockIdx.x, xlogx);
+__global__ void __launch_bounds__(kHuffThreads) k_huffman(Workspace* ws, int which0) {
+  huffman_cta(ws, which0 + blockIdx.x);
 }
 
-cudaError_t launch_code_prep(Workspace* ws, int which_mask, cudaStream_t s) {
+cudaError_t launch_code_prep(Workspace* ws, int which_mask, const double* xlogx, cudaStream_t s) {
   const int nh = (which_mask == 3) ? 2 : 1;
-  k_code_prep<<<nh * kEntropyCtas, kPrepThreads, 0, s>>>(ws, which_mask);
+  k_code_prep<<<nh * kEntropyCtas, kPrepThreads, 0, s>>>(ws, which_mask, xlogx);
   return cudaGetLastError();
 }
 
-cudaError_t launch_huffman(Workspace* ws, int which_mask, const double* xlogx, cudaStream_t s) {
+cudaError_t launch_huffman(Workspace* ws, int which_mask, cudaStream_t s) {
   const int smem = 2 * kHuffSmemKeys * (int)sizeof(uint32_t);
   const int nh = (which_mask == 3) ? 2 : 1;
-  k_huffman<<<nh, kHuffThreads, smem, s>>>(ws, (which_mask & 1) ? 0 : 1, xlogx);
+  k_huffman<<<nh, kHuffThreads, smem, s>>>(ws, (which_mask & 1) ? 0 : 1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_code_stats(Workspace* ws, int which_mask, const double* xlogx, cudaStream_t s) {
-  cudaError_t e = launch_code_prep(ws, which_mask, s);
-  if (e == cudaSuccess) e = launch_huffman(ws, which_mask, xlogx, s);
+  cudaError_t e = launch_code_prep(ws, which_mask, xlogx, s);
+  if (e == cudaSuccess) e = launch_huffman(ws, which_mask, s);
   return e;
 }
 
 __global__ void __launch_bounds__(kHuffThreads) k_batch_final(const BatchField* __restrict__ bf,
-                                                              const double* __restrict__ xlogx,
                                                               rd_result* res, int32_t* status);
 
 cudaError_t prepare_code_stats() {
@@ -964,21 +988,21 @@ cudaError_t launch_batch_reset(const BatchField* bf, int n, int need_gt, cudaStr
   return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(kPrepThreads) k_batch_code_prep(const BatchField* __restrict__ bf) {
-  code_prep_slice<true>(bf[blockIdx.x / kEntropyCtas].ws, 0, blockIdx.x % kEntropyCtas);
+__global__ void __launch_bounds__(kPrepThreads) k_batch_code_prep(const BatchField* __restrict__ bf,
+                                                                  const double* __restrict__ xlogx) {
+  code_prep_slice<true>(bf[blockIdx.x / kEntropyCtas].ws, 0, blockIdx.x % kEntropyCtas, xlogx);
 }
 
-cudaError_t launch_batch_code_prep(const BatchField* bf, int n, cudaStream_t s) {
-  k_batch_code_prep<<<n * kEntropyCtas, kPrepThreads, 0, s>>>(bf);
+cudaError_t launch_batch_code_prep(const BatchField* bf, int n, const double* xlogx, cudaStream_t s) {
+  k_batch_code_prep<<<n * kEntropyCtas, kPrepThreads, 0, s>>>(bf, xlogx);
   return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(kHuffThreads) k_batch_final(const BatchField* __restrict__ bf,
-                                                              const double* __restrict__ xlogx,
                                                               rd_result* res, int32_t* status) {
   const BatchField& F = bf[blockIdx.x];
   Workspace* ws = F.ws;
-  huffman_cta(ws, 0, xlogx);
+  huffman_cta(ws, 0);
   __syncthreads();
   finish_cta(F.p, ws, P_ZFP_EST | P_SZ_EST, 0, 0, F.f.N, F.npoints);
   __syncthreads();
@@ -1007,10 +1031,10 @@ __global__ void __launch_bounds__(kHuffThreads) k_batch_final(const BatchField* 
   if (threadIdx.x == 0) ws->sc.clean = used ? kCleanTables : 0u;
 }
 
-cudaError_t launch_batch_final(const BatchField* bf, int n, const double* xlogx, rd_result* res,
-                               int32_t* status, cudaStream_t s) {
+cudaError_t launch_batch_final(const BatchField* bf, int n, rd_result* res, int32_t* status,
+                               cudaStream_t s) {
   const int smem = 2 * kHuffSmemKeys * (int)sizeof(uint32_t);
-  k_batch_final<<<n, kHuffThreads, smem, s>>>(bf, xlogx, res, status);
+  k_batch_final<<<n, kHuffThreads, smem, s>>>(bf, res, status);
   return cudaGetLastError();
 }
 
