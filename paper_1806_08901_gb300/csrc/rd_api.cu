@@ -38,11 +38,7 @@ struct Pending {
   cudaEvent_t a, b;
 };
 
-struct HostOut {
-  rd_result res;
-  rd_truth truth;
-  int32_t status;
-};
+using HostOut = OutRecords;
 
 // What the log-scale estimate reads back: the range pass's scalars, the
 // largest residual, and at the end the record.
@@ -118,7 +114,8 @@ struct rd_context {
   size_t held = 0;
   Workspace* ws = nullptr;
   double* xlogx = nullptr;  // v log2 v table of the entropy sums
-  HostOut* out = nullptr;  // pinned
+  HostOut* out = nullptr;      // pinned
+  HostOut* out_dev = nullptr;  // the same memory as the device addresses it
   float* staging = nullptr;
   size_t staging_bytes = 0;
   float* xhat = nullptr;  // reconstruction of the classic SZ truth
@@ -359,16 +356,13 @@ int issue(rd_context* c, const CallKey& k, const Geometry& g, cudaStream_t s) {
     if ((rc = launch(c, K_HUFFMAN, s, [&] { return launch_huffman(ws, hist_mask, s); }))) return rc;
   }
   if ((rc = launch(c, K_FINISH, s, [&] {
-         return launch_finish(p, ws, fin_passes, zfp_parts, sz_parts, f.N, g.npoints_sampled, s);
+         // the finish step writes the records and the status into the
+         // pinned host block itself: no copy nodes after it
+         return launch_finish(p, ws, fin_passes, zfp_parts, sz_parts, f.N, g.npoints_sampled,
+                              c->out_dev, s);
        })))
     return rc;
-  // one copy of the result records and the device status
-  cudaError_t e = cudaMemcpyAsync(&c->out->res, &ws->res, sizeof(rd_result), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(&c->out->truth, &ws->truth, sizeof(rd_truth), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(&c->out->status, &ws->sc.status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-  return cuda_status(e);
+  return RD_OK;
 }
 
 GraphEntry* find_graph(rd_context* c, const CallKey& k) {
@@ -720,7 +714,7 @@ int issue_batch(rd_context* c, BatchPlan* b, cudaStream_t s) {
       if ((rc = launch(c, K_CODE_PREP, s, [&] { return launch_code_prep(ws, 2, c->xlogx, s); }))) return rc;
       if ((rc = launch(c, K_HUFFMAN, s, [&] { return launch_huffman(ws, 2, s); }))) return rc;
       if ((rc = launch(c, K_FINISH, s, [&] {
-             return launch_finish(p, ws, P_ZFP_GT | P_SZ_GT, zparts, sparts, f.N, npts, s);
+             return launch_finish(p, ws, P_ZFP_GT | P_SZ_GT, zparts, sparts, f.N, npts, nullptr, s);
            })))
         return rc;
     }
@@ -1096,9 +1090,18 @@ int32_t rd_context_create(int32_t device, size_t hbm_budget, rd_context** out) {
   }
   c->held = sizeof(Workspace) + kNsym * sizeof(double);
   if (cudaMallocHost(&c->out, sizeof(HostOut)) != cudaSuccess) {
+    cudaFree(c->xlogx);
     cudaFree(c->ws);
     delete c;
     return RD_ERR_OOM;
+  }
+  memset(c->out, 0, sizeof(HostOut));
+  if (cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->out_dev), c->out, 0) != cudaSuccess) {
+    cudaFreeHost(c->out);
+    cudaFree(c->xlogx);
+    cudaFree(c->ws);
+    delete c;
+    return RD_ERR_CUDA;
   }
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
   if (prepare_code_stats() != cudaSuccess || prepare_sz_march() != cudaSuccess ||

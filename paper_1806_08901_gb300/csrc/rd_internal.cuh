@@ -218,9 +218,17 @@ cudaError_t launch_code_prep(Workspace* ws, int which_mask, const double* xlogx,
 cudaError_t launch_huffman(Workspace* ws, int which_mask, cudaStream_t s);
 cudaError_t launch_code_stats(Workspace* ws, int which_mask, const double* xlogx, cudaStream_t s);
 cudaError_t prepare_code_stats();
+// The result records and the status of one call, where the host reads them.
+struct OutRecords {
+  rd_result res;
+  rd_truth truth;
+  int32_t status;
+};
+// The finish step; with out (device-visible pinned host memory, or NULL)
+// it also writes the records and the status there.
 cudaError_t launch_finish(const ParamsDev& p, Workspace* ws, int passes,
                           int zfp_parts, int sz_parts, long long npoints_all,
-                          unsigned long long zfp_npoints, cudaStream_t s);
+                          unsigned long long zfp_npoints, OutRecords* out, cudaStream_t s);
 cudaError_t launch_zfp_inspect(const FieldDev& f, double eb_abs, int32_t* emax,
                                int32_t* prec, uint64_t* bits, uint32_t* coeffs,
                                cudaStream_t s);

@@ -954,14 +954,26 @@ __device__ void finish_cta(const ParamsDev& p, Workspace* ws, int passes, int zf
 __global__ void __launch_bounds__(kFinishThreads) k_finish(ParamsDev p, Workspace* ws, int passes,
                                                            int zfp_parts, int sz_parts,
                                                            long long npoints_all,
-                                                           unsigned long long zfp_npoints) {
+                                                           unsigned long long zfp_npoints,
+                                                           OutRecords* out) {
   finish_cta(p, ws, passes, zfp_parts, sz_parts, npoints_all, zfp_npoints);
+  if (!out) return;
+  // the records and the status, word by word, straight into host memory
+  __syncthreads();
+  const uint32_t* rs = reinterpret_cast<const uint32_t*>(&ws->res);
+  const uint32_t* ts = reinterpret_cast<const uint32_t*>(&ws->truth);
+  uint32_t* rd = reinterpret_cast<uint32_t*>(&out->res);
+  uint32_t* td = reinterpret_cast<uint32_t*>(&out->truth);
+  for (int i = threadIdx.x; i < (int)(sizeof(rd_result) / 4); i += blockDim.x) rd[i] = rs[i];
+  for (int i = threadIdx.x; i < (int)(sizeof(rd_truth) / 4); i += blockDim.x) td[i] = ts[i];
+  if (threadIdx.x == 0) out->status = ws->sc.status;
 }
 
 cudaError_t launch_finish(const ParamsDev& p, Workspace* ws, int passes, int zfp_parts,
                           int sz_parts, long long npoints_all, unsigned long long zfp_npoints,
-                          cudaStream_t s) {
-  k_finish<<<1, kFinishThreads, 0, s>>>(p, ws, passes, zfp_parts, sz_parts, npoints_all, zfp_npoints);
+                          OutRecords* out, cudaStream_t s) {
+  k_finish<<<1, kFinishThreads, 0, s>>>(p, ws, passes, zfp_parts, sz_parts, npoints_all, zfp_npoints,
+                                        out);
   return cudaGetLastError();
 }
 

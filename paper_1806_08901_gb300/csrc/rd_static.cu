@@ -156,7 +156,7 @@ extern "C" int32_t rd_select_static(const rd_field* fld, const rd_params* prm, r
   if (e == cudaSuccess) e = launch_zfp(f, p, P_ZFP_EST, da, ws, slot->zfp_ctas[d], s, &zparts);
   if (e == cudaSuccess) e = launch_sz_est(f, p, ws, slot->sz_est_ctas[d], s);
   if (e == cudaSuccess) e = launch_code_stats(ws, 1, slot->xlogx, s);
-  if (e == cudaSuccess) e = launch_finish(p, ws, passes, zparts, 0, f.N, g.npoints_sampled, s);
+  if (e == cudaSuccess) e = launch_finish(p, ws, passes, zparts, 0, f.N, g.npoints_sampled, nullptr, s);
   rd_result r;
   int32_t status = RD_OK;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&r, &ws->res, sizeof(rd_result), cudaMemcpyDeviceToHost, s);
