@@ -11,7 +11,11 @@
  *    caller owns the field memory; the library never writes or frees it.
  *    rd_field.location says whether `data` is a DEVICE pointer (the normal
  *    case) or a HOST pointer, which the library then copies into a staging
- *    buffer it owns inside the context.
+ *    buffer it owns inside the context.  For rd_select, rd_ground_truth,
+ *    rd_ground_truth_classic, rd_evaluate and rd_rd_curve, a host field in
+ *    page-locked (pinned) memory whose address is 16-byte aligned is not
+ *    copied separately: the value-range pass reads it from host memory and
+ *    stores it into the staging buffer as it goes.
  *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
  *    stream).  Work is stream-ordered; every entry point synchronises that
  *    stream before it returns and writes its result structs to caller-owned

@@ -60,6 +60,7 @@ struct CallKey {
   int profiling;
   int pad;
   const void* aux;  // the reconstruction buffer of a classic SZ truth, else NULL
+  const float* host_src;  // a pinned host field the range pass stages, else NULL
 };
 
 struct GraphEntry {
@@ -262,8 +263,12 @@ struct CallGuard {
   }
 };
 
+// A host field is staged into the context's buffer: by a copy, or, with
+// stage_src given and the field in pinned host memory (16-byte aligned), by
+// the range pass itself (*stage_src = the device's address of the field).
 int make_geometry(rd_context* c, const rd_field* fld, const int* strides_or_null, double r_sp,
-                  cudaStream_t s, Geometry* g) {
+                  cudaStream_t s, Geometry* g, const float** stage_src = nullptr) {
+  if (stage_src) *stage_src = nullptr;
   if (!fld || !fld->data) return RD_ERR_INVALID_ARG;
   if (fld->location != RD_LOC_DEVICE && fld->location != RD_LOC_HOST) return RD_ERR_INVALID_ARG;
   int rc = field_geometry(fld, fld->data, strides_or_null, r_sp, g);
@@ -281,8 +286,17 @@ int make_geometry(rd_context* c, const rd_field* fld, const int* strides_or_null
       c->staging_bytes = bytes;
       c->held += bytes;
     }
-    cudaError_t e = cudaMemcpyAsync(c->staging, fld->data, bytes, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return RD_ERR_CUDA;
+    cudaPointerAttributes at;
+    const bool pinned = cudaPointerGetAttributes(&at, fld->data) == cudaSuccess &&
+                        at.type == cudaMemoryTypeHost && at.devicePointer != nullptr &&
+                        ((uintptr_t)at.devicePointer & 15u) == 0;
+    cudaGetLastError();
+    if (stage_src && pinned) {
+      *stage_src = static_cast<const float*>(at.devicePointer);
+    } else {
+      cudaError_t e = cudaMemcpyAsync(c->staging, fld->data, bytes, cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) return RD_ERR_CUDA;
+    }
     // the device copy: the same geometry at the staging buffer's address
     rc = field_geometry(fld, c->staging, strides_or_null, r_sp, g);
     if (rc) return rc;
@@ -308,7 +322,8 @@ int issue(rd_context* c, const CallKey& k, const Geometry& g, cudaStream_t s) {
   int rc;
 
   if ((rc = launch(c, K_RESET, s, [&] { return launch_reset(ws, s); }))) return rc;
-  if ((rc = launch(c, K_RANGE, s, [&] { return launch_range(f, p, ws, c->range_ctas, s); }))) return rc;
+  if ((rc = launch(c, K_RANGE, s, [&] { return launch_range(f, p, ws, c->range_ctas, s, k.host_src); })))
+    return rc;
   // delta: by the last CTA of the ZFP pass when there is one, else its own launch
   const bool need_delta = need_quant || (passes & P_ZFP_EST);
   const DeltaArgs da{need_delta ? 1 : 0, delta_mode, delta_arg, need_quant ? 1 : 0, need_gt ? 1 : 0,
@@ -422,11 +437,13 @@ int run(rd_context* c, const rd_field* fld, const rd_params* prm, int passes, in
   CallGuard guard(c->device);
   cudaStream_t s = (cudaStream_t)stream;
   Geometry g;
-  rc = make_geometry(c, fld, nullptr, prm->r_sp, s, &g);
+  const float* stage_src = nullptr;
+  rc = make_geometry(c, fld, nullptr, prm->r_sp, s, &g, &stage_src);
   if (rc) return rc;
   CallKey k;
   memset(&k, 0, sizeof(k));
   k.f = g.f;
+  k.host_src = stage_src;
   k.p = params_dev(prm);
   k.passes = passes;
   k.delta_mode = delta_mode;

@@ -185,9 +185,11 @@ struct DeltaArgs {
 // the table v log2 v (v < 2^16) of the entropy sums, kNsym doubles (once)
 cudaError_t launch_init_tables(double* xlogx, cudaStream_t s);
 cudaError_t launch_reset(Workspace* ws, cudaStream_t s);
-// value range; the CTA that ends last derives VR, eb_abs and minexp
+// value range; the CTA that ends last derives VR, eb_abs and minexp.  With
+// host_src (pinned host memory holding the field) the pass reads the field
+// there and stores it at f.x as it goes.
 cudaError_t launch_range(const FieldDev& f, const ParamsDev& p, Workspace* ws, int ctas,
-                         cudaStream_t s);
+                         cudaStream_t s, const float* host_src = nullptr);
 // ZFP pass; with da.on, its last CTA derives delta
 cudaError_t launch_zfp(const FieldDev& f, const ParamsDev& p, int passes, const DeltaArgs& da,
                        Workspace* ws, int ctas, cudaStream_t s, int* grid_used);

@@ -22,18 +22,27 @@ struct RangeAcc {
 };
 
 // Values [begin, end) of x, thread tid of nth: a scalar head up to a 16-byte
-// boundary, float4 loads, a scalar tail.
+// boundary, float4 loads, a scalar tail.  With kCopy every value is also
+// stored at the same index of copy (whose address has x's alignment modulo
+// 16), through L2, where the next pass finds it.
+template <bool kCopy = false>
 __device__ __forceinline__ void range_span(const float* __restrict__ x, long long begin,
                                            long long end, long long tid, long long nth,
-                                           RangeAcc& acc) {
+                                           RangeAcc& acc, float* __restrict__ copy = nullptr) {
   const float* xb = x + begin;
+  float* cb = kCopy ? copy + begin : nullptr;
   const long long n = end - begin;
   long long head = (long long)((16u - ((uintptr_t)xb & 15u)) & 15u) / 4;
   if (head > n) head = n;
   if (((uintptr_t)xb & 3u) != 0) head = n;  // not even 4-byte aligned: all scalar
-  for (long long i = tid; i < head; i += nth) acc.add(xb[i]);
+  for (long long i = tid; i < head; i += nth) {
+    const float v = xb[i];
+    if (kCopy) __stcg(cb + i, v);
+    acc.add(v);
+  }
   const long long nvec = (n - head) / 4;
   const float4* x4 = reinterpret_cast<const float4*>(xb + head);
+  float4* c4 = kCopy ? reinterpret_cast<float4*>(cb + head) : nullptr;
   long long i = tid;
   // four independent 16-byte loads in flight per thread
   for (; i + 3 * nth < nvec; i += 4 * nth) {
@@ -42,6 +51,7 @@ __device__ __forceinline__ void range_span(const float* __restrict__ x, long lon
     for (int u = 0; u < 4; u++) q[u] = __ldg(x4 + i + u * nth);
 #pragma unroll
     for (int u = 0; u < 4; u++) {
+      if (kCopy) __stcg(c4 + i + u * nth, q[u]);
       acc.add(q[u].x);
       acc.add(q[u].y);
       acc.add(q[u].z);
@@ -50,12 +60,17 @@ __device__ __forceinline__ void range_span(const float* __restrict__ x, long lon
   }
   for (; i < nvec; i += nth) {
     const float4 q = __ldg(x4 + i);
+    if (kCopy) __stcg(c4 + i, q);
     acc.add(q.x);
     acc.add(q.y);
     acc.add(q.z);
     acc.add(q.w);
   }
-  for (long long i = head + nvec * 4 + tid; i < n; i += nth) acc.add(xb[i]);
+  for (long long i = head + nvec * 4 + tid; i < n; i += nth) {
+    const float v = xb[i];
+    if (kCopy) __stcg(cb + i, v);
+    acc.add(v);
+  }
 }
 
 // Warp, then CTA, then one update per CTA of the field's shared keys.  All

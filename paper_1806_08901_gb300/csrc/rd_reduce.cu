@@ -81,12 +81,16 @@ cudaError_t launch_reset(Workspace* ws, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // The CTA that ends last (a counter, fenced on both sides) derives VR,
 // eb_abs and minexp (Algorithm 1 line 2).
+// With kCopy, x is the field in host memory the device can address (pinned)
+// and every value is also stored at copy (the device staging buffer): the
+// host-to-device transfer is the range pass's own read.
+template <bool kCopy>
 __global__ void __launch_bounds__(512) k_range(const float* __restrict__ x, long long n,
-                                               ParamsDev p, Workspace* ws) {
+                                               ParamsDev p, Workspace* ws, float* __restrict__ copy) {
   __shared__ int s_last;
   RangeAcc acc;
-  range_span(x, 0, n, (long long)blockIdx.x * blockDim.x + threadIdx.x,
-             (long long)gridDim.x * blockDim.x, acc);
+  range_span<kCopy>(x, 0, n, (long long)blockIdx.x * blockDim.x + threadIdx.x,
+                    (long long)gridDim.x * blockDim.x, acc, copy);
   range_commit(acc, ws);
   if (threadIdx.x == 0) {
     __threadfence();
@@ -100,10 +104,13 @@ __global__ void __launch_bounds__(512) k_range(const float* __restrict__ x, long
 }
 
 cudaError_t launch_range(const FieldDev& f, const ParamsDev& p, Workspace* ws, int ctas,
-                         cudaStream_t s) {
+                         cudaStream_t s, const float* host_src) {
   long long want = (f.N / 4 + 511) / 512;
   int g = (int)(want < ctas ? (want < 1 ? 1 : want) : ctas);
-  k_range<<<g, 512, 0, s>>>(f.x, f.N, p, ws);
+  if (host_src)
+    k_range<true><<<g, 512, 0, s>>>(host_src, f.N, p, ws, const_cast<float*>(f.x));
+  else
+    k_range<false><<<g, 512, 0, s>>>(f.x, f.N, p, ws, nullptr);
   return cudaGetLastError();
 }
 

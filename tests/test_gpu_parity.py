@@ -265,6 +265,35 @@ def test_host_field_location(R, ctx):
     check_truth(gt, O.ground_truth(x, op))
 
 
+def test_pinned_host_field_staged_by_the_range_pass(R, ctx):
+    """A field in pinned host memory is read by the range pass itself, which
+    stores it into the staging buffer: the records equal those of the
+    device copy and the oracle, on the direct launch, the graph capture and
+    the replays (the buffer rewritten between calls), and for a pinned view
+    that is not 16-byte aligned (staged by a copy)."""
+    x = FIELDS["3d_tiles"]
+    op = O.params(eb=1e-4, r_sp=0.2)
+    gp = _gp(R, op)
+    want = ctx.evaluate(torch.from_numpy(x).cuda(), gp)
+    check_result(want[0], O.select(x, op), 3)
+    check_truth(want[1], O.ground_truth(x, op))
+    h = torch.empty(x.shape, dtype=torch.float32, pin_memory=True)
+    other = FIELDS["3d_ragged"]
+    for i in range(4):
+        h.copy_(torch.from_numpy(x))
+        assert ctx.evaluate(h, gp) == want
+    # the same pinned buffer, other contents: the replay reads them afresh
+    h2 = torch.empty(other.shape, dtype=torch.float32, pin_memory=True)
+    for i in range(3):
+        h2.copy_(torch.from_numpy(other))
+        got = ctx.evaluate(h2, gp)
+        check_result(got[0], O.select(other, op), 3)
+        check_truth(got[1], O.ground_truth(other, op))
+    buf = torch.empty(x.size + 1, dtype=torch.float32, pin_memory=True)
+    buf[1:].copy_(torch.from_numpy(x.ravel()))
+    assert ctx.evaluate(buf[1:].view(x.shape), gp) == want
+
+
 def test_unaligned_device_pointer(R, ctx):
     """A view starting one float into an allocation: rows are not 16-byte
     aligned, so the scalar load path runs."""
