@@ -366,17 +366,20 @@ int issue(rd_context* c, const CallKey& k, const Geometry& g, cudaStream_t s) {
   }
   int hist_mask = ((passes & P_SZ_EST) ? 1 : 0) | ((passes & (P_SZ_GT | P_SZ_CLASSIC)) ? 2 : 0);
   const int fin_passes = classic ? (passes | P_SZ_GT) : passes;
+  // the finish step writes the records and the status into the pinned host
+  // block itself (no copy nodes after it); with histograms it is fused into
+  // the Huffman launch, run by the CTA that ends last
+  const FinishArgs fa{p, fin_passes, zfp_parts, sz_parts, f.N, g.npoints_sampled, c->out_dev};
   if (hist_mask) {
     if ((rc = launch(c, K_CODE_PREP, s, [&] { return launch_code_prep(ws, hist_mask, c->xlogx, s); }))) return rc;
-    if ((rc = launch(c, K_HUFFMAN, s, [&] { return launch_huffman(ws, hist_mask, s); }))) return rc;
-  }
-  if ((rc = launch(c, K_FINISH, s, [&] {
-         // the finish step writes the records and the status into the
-         // pinned host block itself: no copy nodes after it
-         return launch_finish(p, ws, fin_passes, zfp_parts, sz_parts, f.N, g.npoints_sampled,
-                              c->out_dev, s);
-       })))
+    if ((rc = launch(c, K_HUFFMAN, s, [&] { return launch_huffman_finish(ws, hist_mask, fa, s); })))
+      return rc;
+  } else if ((rc = launch(c, K_FINISH, s, [&] {
+                return launch_finish(p, ws, fin_passes, zfp_parts, sz_parts, f.N, g.npoints_sampled,
+                                     c->out_dev, s);
+              }))) {
     return rc;
+  }
   return RD_OK;
 }
 

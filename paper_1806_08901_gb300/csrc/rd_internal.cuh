@@ -42,6 +42,7 @@ struct Scalars {
   unsigned int zfp_maxerr;       // float bits of max |x - xhat|
   unsigned int sz_maxerr;
   unsigned int log_maxabs;       // float bits of max |residual| (log-scale estimate)
+  uint32_t huff_done;            // Huffman CTAs finished (the last one runs the finish step)
   unsigned long long mse_lo[kMseBins];  // 128-bit sums of d^2 per exponent
   unsigned long long mse_hi[kMseBins];
 };
@@ -231,6 +232,19 @@ struct OutRecords {
 cudaError_t launch_finish(const ParamsDev& p, Workspace* ws, int passes,
                           int zfp_parts, int sz_parts, long long npoints_all,
                           unsigned long long zfp_npoints, OutRecords* out, cudaStream_t s);
+// The arguments of the finish step, for the launch that fuses it.
+struct FinishArgs {
+  ParamsDev p;
+  int passes, zfp_parts, sz_parts;
+  long long npoints_all;
+  unsigned long long zfp_npoints;
+  OutRecords* out;
+};
+// Huffman cost and entropy of the histograms in which_mask, then the finish
+// step by the CTA that ends last (one launch fewer than launch_huffman and
+// launch_finish).
+cudaError_t launch_huffman_finish(Workspace* ws, int which_mask, const FinishArgs& fa,
+                                  cudaStream_t s);
 cudaError_t launch_zfp_inspect(const FieldDev& f, double eb_abs, int32_t* emax,
                                int32_t* prec, uint64_t* bits, uint32_t* coeffs,
                                cudaStream_t s);

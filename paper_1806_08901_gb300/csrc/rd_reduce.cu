@@ -52,6 +52,7 @@ __device__ void reset_ws(Workspace* ws, int tid, int nth, int which_mask) {
     s.zfp_maxerr = 0u;
     s.sz_maxerr = 0u;
     s.log_maxabs = 0u;
+    s.huff_done = 0u;
     for (int w = 0; w < 2; w++) {
       ws->nbig[w] = 0u;
       ws->huff[w].ns = 0ull;
@@ -674,18 +675,29 @@ __device__ void huffman_cta(Workspace* ws, int which) {
   unsigned long long ns;
   double plogp;
   {
+    static_assert(kEntropyCtas % 32 == 0 && kEntropyCtas <= 32 * 32, "whole warps of slices");
+    constexpr int kSliceWarps = kEntropyCtas / 32;
     const uint32_t a = warp_sum(msum);
-    const unsigned long long b = warp_sum(nsum);
-    const double c = warp_sum(ent);
-    if ((tid & 31) == 0) {
-      s_w[tid >> 5] = a;
-      s_w64[tid >> 5] = b;
-      s_wd[tid >> 5] = c;
+    // the slices' shares are held by the first warps alone (float64 is
+    // a narrow pipe: the other warps skip it)
+    if (tid < kEntropyCtas) {
+      const unsigned long long b = warp_sum(nsum);
+      const double c = warp_sum(ent);
+      if ((tid & 31) == 0) {
+        s_w64[tid >> 5] = b;
+        s_wd[tid >> 5] = c;
+      }
     }
+    if ((tid & 31) == 0) s_w[tid >> 5] = a;
     __syncthreads();
     nsmall = warp_sum(s_w[tid & 31]);
-    ns = warp_sum(s_w64[tid & 31]);
-    plogp = warp_sum(s_wd[tid & 31]);
+    ns = 0ull;
+    plogp = 0.0;
+#pragma unroll
+    for (int i = 0; i < kSliceWarps; i++) {
+      ns += s_w64[i];
+      plogp += s_wd[i];
+    }
     __syncthreads();
   }
   const uint32_t K = nsmall + nbig;
@@ -832,9 +844,14 @@ cudaError_t launch_code_stats(Workspace* ws, int which_mask, const double* xlogx
 __global__ void __launch_bounds__(kHuffThreads) k_batch_final(const BatchField* __restrict__ bf,
                                                               rd_result* res, int32_t* status);
 
+__global__ void __launch_bounds__(kHuffThreads) k_huffman_finish(Workspace* ws, int which0,
+                                                                 FinishArgs fa);
+
 cudaError_t prepare_code_stats() {
   const int smem = 2 * kHuffSmemKeys * (int)sizeof(uint32_t);
   cudaError_t e = cudaFuncSetAttribute(k_huffman, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_huffman_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_batch_final, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   return e;
@@ -847,15 +864,20 @@ constexpr int kFinishThreads = 256;
 
 // Fixed-order block sum (strided per-thread sums, then a fixed tree); the
 // result is valid in thread 0.
+// Fixed-order sum of a[0..n) by the first kFinishThreads threads of the CTA
+// (every thread calls it): the same order whatever the CTA's size, and few
+// warps on the SM's narrow float64 pipe.
 __device__ double block_sum_parts(const double* a, int n, double* red) {
-  double v = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) v += a[i];
-  v = warp_sum(v);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  if (threadIdx.x < kFinishThreads) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += kFinishThreads) v += a[i];
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  }
   __syncthreads();
   double t = 0.0;
   if (threadIdx.x < 32) {
-    t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    t = threadIdx.x < kFinishThreads / 32 ? red[threadIdx.x] : 0.0;
     t = warp_sum(t);
   }
   __syncthreads();
@@ -958,14 +980,9 @@ __device__ void finish_cta(const ParamsDev& p, Workspace* ws, int passes, int zf
   t.flags = s.flags & (RD_F_DELTA_CLAMPED | RD_F_MSE_ZERO | RD_F_CONSTANT);
 }
 
-__global__ void __launch_bounds__(kFinishThreads) k_finish(ParamsDev p, Workspace* ws, int passes,
-                                                           int zfp_parts, int sz_parts,
-                                                           long long npoints_all,
-                                                           unsigned long long zfp_npoints,
-                                                           OutRecords* out) {
-  finish_cta(p, ws, passes, zfp_parts, sz_parts, npoints_all, zfp_npoints);
-  if (!out) return;
-  // the records and the status, word by word, straight into host memory
+// The records and the status, word by word, straight into host memory (all
+// threads of the CTA, after the finish step).
+__device__ void write_out(const Workspace* ws, OutRecords* out) {
   __syncthreads();
   const uint32_t* rs = reinterpret_cast<const uint32_t*>(&ws->res);
   const uint32_t* ts = reinterpret_cast<const uint32_t*>(&ws->truth);
@@ -974,6 +991,41 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(ParamsDev p, Workspac
   for (int i = threadIdx.x; i < (int)(sizeof(rd_result) / 4); i += blockDim.x) rd[i] = rs[i];
   for (int i = threadIdx.x; i < (int)(sizeof(rd_truth) / 4); i += blockDim.x) td[i] = ts[i];
   if (threadIdx.x == 0) out->status = ws->sc.status;
+}
+
+__global__ void __launch_bounds__(kFinishThreads) k_finish(ParamsDev p, Workspace* ws, int passes,
+                                                           int zfp_parts, int sz_parts,
+                                                           long long npoints_all,
+                                                           unsigned long long zfp_npoints,
+                                                           OutRecords* out) {
+  finish_cta(p, ws, passes, zfp_parts, sz_parts, npoints_all, zfp_npoints);
+  if (out) write_out(ws, out);
+}
+
+// One CTA per histogram; the CTA that ends last (a counter, fenced on both
+// sides) runs the finish step.
+__global__ void __launch_bounds__(kHuffThreads) k_huffman_finish(Workspace* ws, int which0,
+                                                                 FinishArgs fa) {
+  __shared__ int s_last;
+  huffman_cta(ws, which0 + blockIdx.x);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&ws->sc.huff_done, 1u) == gridDim.x - 1u;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  finish_cta(fa.p, ws, fa.passes, fa.zfp_parts, fa.sz_parts, fa.npoints_all, fa.zfp_npoints);
+  if (fa.out) write_out(ws, fa.out);
+}
+
+cudaError_t launch_huffman_finish(Workspace* ws, int which_mask, const FinishArgs& fa,
+                                  cudaStream_t s) {
+  const int smem = 2 * kHuffSmemKeys * (int)sizeof(uint32_t);
+  const int nh = (which_mask == 3) ? 2 : 1;
+  k_huffman_finish<<<nh, kHuffThreads, smem, s>>>(ws, (which_mask & 1) ? 0 : 1, fa);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_finish(const ParamsDev& p, Workspace* ws, int passes, int zfp_parts,
