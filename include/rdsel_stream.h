@@ -38,16 +38,17 @@ extern "C" {
  *    zero.  out = NULL: only *nbits is computed (the ground truth's bit
  *    count), nothing is written.
  *  - *nbits: the stream's length in bits.
- *  - Device work: the ground truth (histogram, quantiser, status), the
- *    per-point symbols, per-CTA sums of code lengths and escapes, one scan
- *    over the CTAs, then each CTA writes its points' codes and escaped values
- *    at their offsets (64-bit ORs).  The code lengths (a Huffman tree over
- *    at most 65536 symbols) and the header are built on the host from the
- *    device histogram.  The context keeps a scratch of 4 N bytes + 0.6 MB,
- *    counted against its memory budget.
- *  - Equal-weight ties in the Huffman tree may be broken either way: the
- *    code lengths are those of one optimal code, and the payload length is
- *    the same for every optimal code.
+ *  - Device work: the ground truth (histogram, quantiser, status); the
+ *    code table (the symbols sorted by count, stably, a Huffman tree over at
+ *    most 65536 symbols, the code lengths, canonical codes, the header and
+ *    table written into out); the per-point symbols, per-CTA sums of code
+ *    lengths and escapes, one scan over the CTAs, then each CTA writes its
+ *    points' codes and escaped values at their offsets (64-bit ORs).  The
+ *    context keeps a scratch of 4 N bytes + 2.9 MB, counted against its
+ *    memory budget.
+ *  - Equal counts keep symbol order in the tree's leaves, so the same
+ *    histogram gives the same code on every call; the code is one optimal
+ *    code (its payload length is the same for every optimal code).
  *  - Returns once the work on `stream` has finished. */
 int32_t rd_sz_compress(rd_context* ctx, const rd_field* field, const rd_params* params,
                        double eb_sz, void* out, uint64_t cap_bytes, uint64_t* nbits,

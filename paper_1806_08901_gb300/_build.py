@@ -19,7 +19,7 @@ LIB = os.path.join(PKG, "librdsel.so")
 
 SOURCES = ["rd_api.cu", "rd_reduce.cu", "rd_zfp.cu", "rd_zfp3.cu", "rd_sz.cu", "rd_sz_tma.cu", "rd_static.cu", "rd_batch.cu", "rd_server.cu",
            "rd_sz_classic.cu", "rd_sz_stream.cu", "rd_sz_log.cu",
-           "rd_zfp_stream.cu"]
+           "rd_zfp_stream.cu", "rd_sz_codes.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

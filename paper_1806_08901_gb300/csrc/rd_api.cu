@@ -10,7 +10,6 @@
 #include <algorithm>
 #include <functional>
 #include <new>
-#include <queue>
 #include <utility>
 #include <vector>
 
@@ -1125,6 +1124,7 @@ int32_t rd_context_create(int32_t device, size_t hbm_budget, rd_context** out) {
   }
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
   if (prepare_code_stats() != cudaSuccess || prepare_sz_march() != cudaSuccess ||
+      prepare_sz_code_table() != cudaSuccess ||
       prepare_sz_est() != cudaSuccess ||
       launch_init_tables(c->xlogx, 0) != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess) {
     cudaFreeHost(c->out);
@@ -1219,56 +1219,6 @@ int32_t rd_ground_truth_classic(rd_context* c, const rd_field* f, const rd_param
   return cuda_status(e);
 }
 
-namespace {
-
-// Code lengths of an optimal prefix code for the histogram h (the leaf
-// depths of a Huffman tree merged from a min-heap of (weight, node)); one
-// symbol alone gets length 1.  Returns the number of symbols, or -1 when a
-// length would exceed 63 (the table's 6-bit field).
-long long stream_code_lengths(const std::vector<uint32_t>& h, std::vector<uint8_t>& len) {
-  len.assign(kNsym, 0);
-  std::vector<int> sym;
-  for (int s = 0; s < kNsym; s++)
-    if (h[s]) sym.push_back(s);
-  const long long K = (long long)sym.size();
-  if (K == 1) len[sym[0]] = 1;
-  if (K <= 1) return K;
-  typedef std::pair<unsigned long long, int> Item;
-  std::priority_queue<Item, std::vector<Item>, std::greater<Item>> pq;
-  std::vector<int> up((size_t)(2 * K), -1);
-  for (long long i = 0; i < K; i++) pq.push(Item(h[sym[i]], (int)i));
-  int next = (int)K;
-  while (pq.size() > 1) {
-    const Item a = pq.top();
-    pq.pop();
-    const Item b = pq.top();
-    pq.pop();
-    up[a.second] = next;
-    up[b.second] = next;
-    pq.push(Item(a.first + b.first, next++));
-  }
-  for (long long i = 0; i < K; i++) {
-    int d = 0;
-    for (int v = (int)i; up[v] >= 0; v = up[v]) d++;
-    if (d > 63) return -1;
-    len[sym[i]] = (uint8_t)d;
-  }
-  return K;
-}
-
-struct StreamBits {
-  std::vector<uint8_t> b;
-  unsigned long long pos = 0;
-  void put(unsigned long long v, int nb) {
-    for (int i = nb - 1; i >= 0; i--, pos++) {
-      if ((pos >> 3) >= b.size()) b.push_back(0);
-      b[pos >> 3] |= (uint8_t)(((v >> i) & 1ull) << (7 - (pos & 7)));
-    }
-  }
-};
-
-}  // namespace
-
 int32_t rd_sz_compress(rd_context* c, const rd_field* fld, const rd_params* prm, double eb_sz, void* out,
                        uint64_t cap_bytes, uint64_t* nbits, void* stream) {
   if (!c || !nbits || !(eb_sz > 0.0) || !isfinite(eb_sz)) return RD_ERR_INVALID_ARG;
@@ -1287,55 +1237,18 @@ int32_t rd_sz_compress(rd_context* c, const rd_field* fld, const rd_params* prm,
   Geometry g;
   if ((rc = make_geometry(c, fld, nullptr, prm->r_sp, s, &g))) return rc;
   const long long n = g.f.N;
-  std::vector<uint32_t> h(kNsym);
-  float q[3];
-  cudaError_t e = cudaMemcpy(h.data(), c->ws->hist[1], sizeof(uint32_t) * kNsym, cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess) e = cudaMemcpy(q, &c->ws->sc.w, sizeof(q), cudaMemcpyDeviceToHost);  // w, inv, tau
-  if (e != cudaSuccess) return cuda_status(e);
-  std::vector<uint8_t> len;
-  const long long K = stream_code_lengths(h, len);
-  if (K < 0) return RD_ERR_RANGE;
-  unsigned long long payload = 0ull, nesc = h[0];
-  for (int v = 0; v < kNsym; v++) payload += (unsigned long long)h[v] * len[v];
-  // an optimal code's payload is the Huffman cost the truth reported
-  if ((unsigned long long)K != t.sz_nsym_gt || payload != t.sz_huff_gt || nesc != t.sz_nesc_gt)
-    return RD_ERR_CUDA;
-  // canonical codes: ascending (length, symbol) take consecutive values;
-  // the first code of each length from the count of shorter codes
-  std::vector<unsigned long long> code(kNsym, 0ull);
-  {
-    unsigned long long nlen[65] = {0ull}, next[65] = {0ull};
-    for (int v = 0; v < kNsym; v++) nlen[len[v]]++;
-    nlen[0] = 0ull;
-    unsigned long long cv = 0ull;
-    int prev = 0;
-    for (int L = 1; L <= 63; L++) {
-      if (!nlen[L]) continue;
-      cv = prev ? (cv + nlen[prev]) << (L - prev) : 0ull;
-      next[L] = cv;
-      prev = L;
-    }
-    for (int v = 0; v < kNsym; v++)
-      if (len[v]) code[v] = next[len[v]]++;
-  }
-  // header and table, written here; the payload starts right after them
-  StreamBits hb;
-  hb.put((unsigned long long)K, 32);
-  hb.put(nesc, 32);
-  for (int v = 0; v < kNsym; v++)
-    if (h[v]) {
-      hb.put((unsigned long long)v, 16);
-      hb.put(len[v], 6);
-    }
-  const unsigned long long payload_base = hb.pos;
-  // device scratch: symbols, lengths, codes, per-CTA bit and escape offsets
+  // the code table, the symbols, the offsets and the stream, all on the
+  // device: the truth's histogram and quantiser are still in the workspace
+  const unsigned long long payload_base = 64ull + 22ull * t.sz_nsym_gt;
   const int nctas = stream_ctas(n);
   const size_t off_len = (size_t)n * sizeof(int32_t);
   const size_t off_code = (off_len + kNsym + 15) / 16 * 16;
   const size_t off_cb = off_code + sizeof(unsigned long long) * kNsym;
   const size_t off_ce = off_cb + sizeof(unsigned long long) * (size_t)nctas;
   const size_t off_tot = (off_ce + sizeof(unsigned) * (size_t)nctas + 15) / 16 * 16;
-  const size_t bytes = off_tot + 2 * sizeof(unsigned long long);
+  const size_t off_cs = off_tot + 2 * sizeof(unsigned long long);
+  const size_t off_st = off_cs + sizeof(uint32_t) * (size_t)kCodeScratchWords;
+  const size_t bytes = off_st + 16;
   if (bytes > c->enc_bytes) {
     if (c->budget && c->held + (bytes - c->enc_bytes) > c->budget) return RD_ERR_BUDGET;
     if (c->enc) cudaFree(c->enc);
@@ -1353,25 +1266,33 @@ int32_t rd_sz_compress(rd_context* c, const rd_field* fld, const rd_params* prm,
   unsigned long long* dcb = reinterpret_cast<unsigned long long*>(base + off_cb);
   unsigned* dce = reinterpret_cast<unsigned*>(base + off_ce);
   unsigned long long* dtot = reinterpret_cast<unsigned long long*>(base + off_tot);
-  e = cudaMemcpyAsync(dlen, len.data(), kNsym, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dcode, code.data(), sizeof(unsigned long long) * kNsym, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(out, 0, words * 8ull, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(out, hb.b.data(), hb.b.size(), cudaMemcpyHostToDevice, s);
-  // the symbols of the truth's quantiser, then the offsets
-  if (e == cudaSuccess) e = launch_sz_inspect_q(g.f, q[0], q[1], q[2], prm->quant_radius, nullptr, dsym, nullptr, 0, s);
+  uint32_t* cw = reinterpret_cast<uint32_t*>(base + off_cs);
+  const CodeScratch cs{cw, cw + kNsym, cw + 2 * kNsym, cw + 3 * kNsym, cw + 4 * kNsym,
+                       cw + 5 * kNsym, cw + 6 * kNsym, cw + 7 * kNsym, cw + 8 * kNsym};
+  int32_t* dst = reinterpret_cast<int32_t*>(base + off_st);
+  unsigned long long* dout = static_cast<unsigned long long*>(out);
+  cudaError_t e = cudaMemsetAsync(out, 0, words * 8ull, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dst, 0, sizeof(int32_t), s);
+  if (e == cudaSuccess) e = launch_sz_code_table(c->ws->hist[1], cs, dlen, dcode, dout, dst, s);
+  if (e == cudaSuccess)
+    e = launch_sz_inspect_q(g.f, 0.0f, 0.0f, 0.0f, prm->quant_radius, nullptr, dsym, nullptr, 0, s, c->ws);
   if (e == cudaSuccess) e = launch_stream_count(dsym, n, dlen, dcb, dce, s);
   if (e == cudaSuccess) e = launch_stream_scan(dcb, dce, nctas, dtot, s);
+  if (e == cudaSuccess)
+    e = launch_stream_pack(dsym, g.f.x, n, dlen, dcode, dcb, dce, dtot, payload_base, dout, s);
+  // one read-back, after the last kernel: the totals and the table status
   unsigned long long tot[2] = {0ull, 0ull};
+  int32_t st = RD_OK;
   if (e == cudaSuccess) e = cudaMemcpyAsync(tot, dtot, sizeof(tot), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&st, dst, sizeof(st), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_status(e);
-  c->launches += 3;
-  if (tot[0] != payload || tot[1] != nesc) return RD_ERR_CUDA;  // symbols differ from the histogram
-  e = launch_stream_pack(dsym, g.f.x, n, dlen, dcode, dcb, dce, dtot, payload_base,
-                         static_cast<unsigned long long*>(out), s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  c->launches += 1;
-  return cuda_status(e);
+  c->launches += 5;
+  if (st != RD_OK) return st;
+  // an optimal code's payload is the Huffman cost the truth reported, and
+  // the symbols are the truth's
+  if (tot[0] != t.sz_huff_gt || tot[1] != t.sz_nesc_gt) return RD_ERR_CUDA;
+  return RD_OK;
 }
 
 int32_t rd_zfp_compress(rd_context* c, const rd_field* fld, const rd_params* prm, void* out,

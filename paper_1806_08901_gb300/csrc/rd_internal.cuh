@@ -250,7 +250,7 @@ cudaError_t launch_zfp_inspect(const FieldDev& f, double eb_abs, int32_t* emax,
                                cudaStream_t s);
 cudaError_t launch_sz_inspect_q(const FieldDev& f, float w, float inv, float tau, int R,
                                 int32_t* est_sym, int32_t* gt_sym, float* recon,
-                                int use_strides, cudaStream_t s);
+                                int use_strides, cudaStream_t s, const Workspace* qws = nullptr);
 // SZ pass as a TMA-fed march (2D/3D fields with 16-byte aligned rows);
 // prepare_sz_march() once per device first.
 bool sz_march_supported(const FieldDev& f);

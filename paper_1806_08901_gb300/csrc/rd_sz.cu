@@ -210,9 +210,15 @@ int sz_occupancy(int d, int num_sms) {
 // ---------------------------------------------------------------------------
 // Inspector: per-point symbols and reconstruction through the same helpers.
 // ---------------------------------------------------------------------------
+// With qws, the quantiser (w, 1/w, tau) is the one that workspace holds.
 template <int D>
 __global__ void k_sz_inspect(FieldDev f, float w, float inv, float tau, int R, int use_strides,
-                             int32_t* est_sym, int32_t* gt_sym, float* recon) {
+                             int32_t* est_sym, int32_t* gt_sym, float* recon, const Workspace* qws) {
+  if (qws) {
+    w = qws->sc.w;
+    inv = qws->sc.inv;
+    tau = qws->sc.tau;
+  }
   for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < f.N;
        u += (long long)gridDim.x * blockDim.x) {
     int g[3] = {0, 0, 0};
@@ -233,14 +239,14 @@ __global__ void k_sz_inspect(FieldDev f, float w, float inv, float tau, int R, i
 
 cudaError_t launch_sz_inspect_q(const FieldDev& f, float w, float inv, float tau, int R,
                                 int32_t* est_sym, int32_t* gt_sym, float* recon, int use_strides,
-                                cudaStream_t s) {
+                                cudaStream_t s, const Workspace* qws) {
   long long g = (f.N + 255) / 256;
   if (g > 65535) g = 65535;
   if (g < 1) g = 1;
   switch (f.d) {
-    case 1: k_sz_inspect<1><<<(int)g, 256, 0, s>>>(f, w, inv, tau, R, use_strides, est_sym, gt_sym, recon); break;
-    case 2: k_sz_inspect<2><<<(int)g, 256, 0, s>>>(f, w, inv, tau, R, use_strides, est_sym, gt_sym, recon); break;
-    default: k_sz_inspect<3><<<(int)g, 256, 0, s>>>(f, w, inv, tau, R, use_strides, est_sym, gt_sym, recon); break;
+    case 1: k_sz_inspect<1><<<(int)g, 256, 0, s>>>(f, w, inv, tau, R, use_strides, est_sym, gt_sym, recon, qws); break;
+    case 2: k_sz_inspect<2><<<(int)g, 256, 0, s>>>(f, w, inv, tau, R, use_strides, est_sym, gt_sym, recon, qws); break;
+    default: k_sz_inspect<3><<<(int)g, 256, 0, s>>>(f, w, inv, tau, R, use_strides, est_sym, gt_sym, recon, qws); break;
   }
   return cudaGetLastError();
 }

@@ -5,7 +5,7 @@
 // its bit offset.  Offsets are exclusive scans of the code lengths and
 // escape flags in storage order: per-CTA totals, one scan over the CTAs,
 // then each CTA re-scans its chunk and writes.  The header and code table
-// are written by the host.
+// are written by the code-table kernel (rd_sz_codes.cu).
 #include <stdint.h>
 
 #include "rd_sz_stream.cuh"
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_pack(
     const int s = s_loc[k];
     if (s < 0) continue;
     const int L = len[s];
-    if (L == 0) continue;  // not in the table: the host's length check refuses the stream
+    if (L == 0) continue;  // not in the table: the length check refuses the stream
     put_bits(out, p, code[s], L);
     p += (unsigned long long)L;
     if (s == 0) {

@@ -32,6 +32,32 @@ cudaError_t launch_stream_pack(const int32_t* sym, const float* x, long long n, 
                                unsigned long long payload_base, unsigned long long* out,
                                cudaStream_t s);
 
+// Device scratch of the code table (rd_sz_codes.cu): kNsym words each.
+struct CodeScratch {
+  uint32_t* sym0;     // present symbols in symbol order
+  uint32_t* keyA;     // radix sort: counts and symbols, two buffers
+  uint32_t* symA;
+  uint32_t* keyB;
+  uint32_t* symB;
+  uint32_t* nodes;    // Huffman nodes' weights (above kHuffSmemKeys symbols)
+  uint32_t* leafpar;  // parent node of every leaf (sorted order)
+  uint32_t* nodepar;  // parent node of every node
+  uint32_t* ndepth;   // depth of every node
+};
+constexpr int kCodeScratchWords = 9 * kNsym;
+
+// From the histogram h (kNsym bins): the code length len[s] and canonical
+// code code[s] of every symbol (length 0: absent) of an optimal prefix
+// code, with the stream's header (present symbols K, h[0] escapes; 32 bits
+// each) and table (per present symbol in symbol order: symbol 16 bits,
+// length 6 bits) ORed into out (zeroed) from bit 0, so that the payload
+// starts at bit 64 + 22 K.  *status (RD_OK on entry) gets RD_ERR_RANGE when
+// a length would exceed 63.  One CTA.
+cudaError_t prepare_sz_code_table();
+cudaError_t launch_sz_code_table(const uint32_t* h, const CodeScratch& sc, uint8_t* len,
+                                 unsigned long long* code, unsigned long long* out, int32_t* status,
+                                 cudaStream_t s);
+
 // ZFP fixed-accuracy stream (rd_zfp_stream.cu): every block's bits into
 // bits[nblocks], per-chunk sums into csum[zfp_stream_chunks(nblocks)] (then
 // scanned in place; total[0] = the stream's length); with out, every block

@@ -122,3 +122,46 @@ def test_stream_of_a_host_field_and_repeats(R, ctx):
     assert n2 == nbits and np.array_equal(out_h.cpu().numpy(), buf)
     n3, buf3 = compress(R, ctx, x, op, 0.005)
     assert n3 == nbits and np.array_equal(buf3, buf)
+
+
+def _table(buf, nbits):
+    """The header and code table of a stream: K, escapes, and per present
+    symbol (ascending) its code length."""
+    bits = np.unpackbits(np.frombuffer(buf, dtype=np.uint8))
+    def field(p, n):
+        return int("".join(map(str, bits[p:p + n])), 2) if n else 0
+    K, nesc = field(0, 32), field(32, 32)
+    lens = {}
+    for r in range(K):
+        lens[field(64 + 22 * r, 16)] = field(64 + 22 * r + 16, 6)
+    return K, nesc, lens
+
+
+@pytest.mark.parametrize("shape,rel_eb", [((64, 128, 256), 1e-6), ((40, 100, 100), 1e-4),
+                                          ((4096,), 1e-2)])
+def test_code_table_built_on_the_device(R, ctx, shape, rel_eb):
+    """The code table is built on the device: the same bytes on every call,
+    an optimal code (the lengths' weighted sum is the Huffman cost, the
+    Kraft sum is at most one), the table in ascending symbol order with the
+    histogram's symbols; the widest case has more symbols than the shared-
+    memory queues hold (the queues go to global memory), the last a handful
+    of symbols."""
+    x = (synth.grf_np(shape, -1.5, 91) * 7).astype(np.float32)
+    vr = float(x.max()) - float(x.min())
+    eb_sz = rel_eb * vr
+    op = O.params(eb=1e-3)
+    nbits, buf = compress(R, ctx, x, op, eb_sz)
+    nbits2, buf2 = compress(R, ctx, x, op, eb_sz)
+    assert nbits2 == nbits and np.array_equal(buf, buf2)
+    t = O.ground_truth(x, op, eb_sz, want_hist=True)
+    h = np.asarray(t["hist"], dtype=np.int64)
+    K, nesc, lens = _table(buf[: (nbits + 7) // 8].tobytes(), nbits)
+    assert K == t["sz_nsym_gt"] == int((h > 0).sum()) and nesc == t["sz_nesc_gt"]
+    assert sorted(lens) == list(np.nonzero(h)[0])
+    assert sum(int(h[s]) * L for s, L in lens.items()) == t["sz_huff_gt"]
+    if K > 1:
+        assert sum(2.0 ** -L for L in lens.values()) <= 1.0
+    if shape == (64, 128, 256):
+        assert K > 28672
+    sym, _ = O.sz_stream_decode(buf[: (nbits + 7) // 8].tobytes(), nbits, x.size)
+    assert np.array_equal(sym, O.sz_symbols(x, 2 * eb_sz)["gt"].ravel())
