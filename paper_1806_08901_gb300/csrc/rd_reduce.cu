@@ -884,32 +884,56 @@ __device__ double block_sum_parts(const double* a, int n, double* red) {
   return t;
 }
 
-__device__ void finish_cta(const ParamsDev& p, Workspace* ws, int passes, int zfp_parts,
-                           int sz_parts, long long npoints_all, unsigned long long zfp_npoints) {
+// The finish step in two parts.  finish_pre (every thread of the CTA): the
+// fields that need no Huffman cost — the truth's squared-error sums (fixed
+// order), MSEs and PSNRs, the ZFP truth's rates.  finish_post (warp 0):
+// the entropy, rates and selection from the Huffman costs, the SZ truth's
+// sizes, the flags.  finish_cta runs both; the fused Huffman launch runs
+// the first part in its first CTA before that CTA's own Huffman work.
+__device__ void finish_pre(Workspace* ws, int passes, int zfp_parts, int sz_parts,
+                           long long npoints_all) {
   __shared__ double red[32];
   Scalars& s = ws->sc;
-  if (s.status != RD_OK) return;
-  rd_result& r = ws->res;
+  if (s.status != RD_OK || s.constant) return;
   rd_truth& t = ws->truth;
   double zsse = 0.0, ssse = 0.0;
-  if (!s.constant) {
-    if (passes & P_ZFP_GT) zsse = block_sum_parts(ws->zfp_sse, zfp_parts, red);
-    if (passes & P_SZ_GT) ssse = block_sum_parts(ws->sz_sse, sz_parts, red);
-  }
+  if (passes & P_ZFP_GT) zsse = block_sum_parts(ws->zfp_sse, zfp_parts, red);
+  if (passes & P_SZ_GT) ssse = block_sum_parts(ws->sz_sse, sz_parts, red);
   if (threadIdx.x >= 32) return;
   const int lane = threadIdx.x;
-  // the logarithms in separate lanes: 0 VR, 1 N_s, 2 ZFP truth MSE, 3 SZ truth MSE
-  const double ns_d = (double)ws->huff[0].ns;
+  // the logarithms in separate lanes: 0 VR, 2 ZFP truth MSE, 3 SZ truth MSE
   const double mse_z = zsse / (double)npoints_all;
   const double mse_s = ssse / (double)npoints_all;
-  const double larg = lane == 0 ? s.vr : lane == 1 ? ns_d : lane == 2 ? mse_z : mse_s;
+  const double larg = lane == 0 ? s.vr : lane == 2 ? mse_z : mse_s;
   const double lg2 = log2(larg);
   const double kLog10of2 = 0.30102999566398119521;
   const double l_vr = __shfl_sync(0xffffffffu, lg2, 0) * kLog10of2;
-  const double l_ns = __shfl_sync(0xffffffffu, lg2, 1);
   const double l_mz = __shfl_sync(0xffffffffu, lg2, 2) * kLog10of2;
   const double l_ms = __shfl_sync(0xffffffffu, lg2, 3) * kLog10of2;
   if (lane != 0) return;
+  const double lvr = 20.0 * l_vr;
+  if (passes & P_ZFP_GT) {
+    t.zfp_bits_gt = s.zfp_bits;
+    t.br_zfp_gt = (double)s.zfp_bits / (double)npoints_all;
+    t.sse_zfp = zsse;
+    t.maxerr_zfp = (double)__uint_as_float(s.zfp_maxerr);
+    t.psnr_zfp_gt = mse_z > 0.0 ? lvr - 10.0 * l_mz : INFINITY;
+  }
+  if (passes & P_SZ_GT) {
+    t.delta = s.delta;
+    t.eb_sz = s.delta / 2.0;
+    t.sse_sz = ssse;
+    t.maxerr_sz = (double)__uint_as_float(s.sz_maxerr);
+    t.psnr_sz_gt = mse_s > 0.0 ? lvr - 10.0 * l_ms : INFINITY;
+  }
+}
+
+__device__ void finish_post(const ParamsDev& p, Workspace* ws, int passes, long long npoints_all,
+                            unsigned long long zfp_npoints) {
+  Scalars& s = ws->sc;
+  if (s.status != RD_OK || threadIdx.x != 0) return;
+  rd_result& r = ws->res;
+  rd_truth& t = ws->truth;
   if (s.constant) {
     r.flags = s.flags;
     r.psnr_zfp = INFINITY;
@@ -921,11 +945,10 @@ __device__ void finish_cta(const ParamsDev& p, Workspace* ws, int passes, int zf
     t.best_gt = 1;
     return;
   }
-  const double lvr = 20.0 * l_vr;
   if (passes & P_SZ_EST) {
     const HuffOut& hh = ws->huff[0];
     double ns = (double)hh.ns;
-    double H = l_ns - hh.plogp / ns;
+    double H = log2(ns) - hh.plogp / ns;
     if (H < 0.0) H = 0.0;
     uint32_t h0 = ws->hist[0][0];
     r.entropy = H;
@@ -955,29 +978,24 @@ __device__ void finish_cta(const ParamsDev& p, Workspace* ws, int passes, int zf
     }
   }
   r.flags = s.flags;
-  if (passes & P_ZFP_GT) {
-    t.zfp_bits_gt = s.zfp_bits;
-    t.br_zfp_gt = (double)s.zfp_bits / (double)npoints_all;
-    t.sse_zfp = zsse;
-    t.maxerr_zfp = (double)__uint_as_float(s.zfp_maxerr);
-    t.psnr_zfp_gt = mse_z > 0.0 ? lvr - 10.0 * l_mz : INFINITY;
-  }
   if (passes & P_SZ_GT) {
     const HuffOut& hg = ws->huff[1];
     uint32_t h0 = ws->hist[1][0];
-    t.delta = s.delta;
-    t.eb_sz = s.delta / 2.0;
     t.sz_huff_gt = hg.cost;
     t.sz_nsym_gt = hg.nsym;
     t.sz_nesc_gt = h0;
     t.sz_bits_gt = hg.cost + 32ull * h0 + 22ull * hg.nsym + 64ull;
     t.br_sz_gt = (double)t.sz_bits_gt / (double)npoints_all;
-    t.sse_sz = ssse;
-    t.maxerr_sz = (double)__uint_as_float(s.sz_maxerr);
-    t.psnr_sz_gt = mse_s > 0.0 ? lvr - 10.0 * l_ms : INFINITY;
     if (passes & P_ZFP_GT) t.best_gt = t.br_sz_gt < t.br_zfp_gt ? 0 : 1;
   }
   t.flags = s.flags & (RD_F_DELTA_CLAMPED | RD_F_MSE_ZERO | RD_F_CONSTANT);
+}
+
+__device__ void finish_cta(const ParamsDev& p, Workspace* ws, int passes, int zfp_parts,
+                           int sz_parts, long long npoints_all, unsigned long long zfp_npoints) {
+  finish_pre(ws, passes, zfp_parts, sz_parts, npoints_all);
+  __syncthreads();
+  finish_post(p, ws, passes, npoints_all, zfp_npoints);
 }
 
 // The records and the status, word by word, straight into host memory (all
@@ -1007,6 +1025,12 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(ParamsDev p, Workspac
 __global__ void __launch_bounds__(kHuffThreads) k_huffman_finish(Workspace* ws, int which0,
                                                                  FinishArgs fa) {
   __shared__ int s_last;
+  // the finish step's first part needs no Huffman cost: the first CTA does
+  // it before its own histogram
+  if (blockIdx.x == 0) {
+    finish_pre(ws, fa.passes, fa.zfp_parts, fa.sz_parts, fa.npoints_all);
+    __syncthreads();
+  }
   huffman_cta(ws, which0 + blockIdx.x);
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1016,7 +1040,7 @@ __global__ void __launch_bounds__(kHuffThreads) k_huffman_finish(Workspace* ws, 
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  finish_cta(fa.p, ws, fa.passes, fa.zfp_parts, fa.sz_parts, fa.npoints_all, fa.zfp_npoints);
+  finish_post(fa.p, ws, fa.passes, fa.npoints_all, fa.zfp_npoints);
   if (fa.out) write_out(ws, fa.out);
 }
 
