@@ -173,49 +173,16 @@ __device__ void bitonic_sort(uint32_t* a, int n) {
   }
 }
 
-// Number of A elements among the first d of merge(A, B), ties from A first:
-// the predicate A[i] <= B[d-1-i] holds for a prefix of i in [lo, hi].  A
-// 4-way search (three probes per step, loaded together) shortens the chain
-// of dependent loads, then binary steps finish.
-template <class VA, class VB>
-__device__ __forceinline__ uint32_t merge_split(const VA& A, uint32_t na, const VB& B, uint32_t nb,
-                                                uint32_t d) {
-  uint32_t lo = d > nb ? d - nb : 0u, hi = d < na ? d : na;
-  while (hi - lo > 3u) {
-    const uint32_t q = (hi - lo) >> 2;
-    const uint32_t m1 = lo + q, m2 = lo + 2u * q, m3 = lo + 3u * q;
-    const bool p1 = A[m1] <= B[d - 1 - m1];
-    const bool p2 = A[m2] <= B[d - 1 - m2];
-    const bool p3 = A[m3] <= B[d - 1 - m3];
-    if (!p1) {
-      hi = m1;
-    } else if (!p2) {
-      lo = m1 + 1u;
-      hi = m2;
-    } else if (!p3) {
-      lo = m2 + 1u;
-      hi = m3;
-    } else {
-      lo = m3 + 1u;
-    }
-  }
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if (A[mid] <= B[d - 1 - mid]) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
-
-
 constexpr int kPrepThreads = 256;   // code-statistics prep CTAs (1024 bins each)
 constexpr int kHuffThreads = 1024;  // Huffman CTA
 constexpr uint32_t kMinPairs = 1;   // fewest pairs per thread in a Huffman phase
 
 // Numbers of elements below T of the sorted a[0..na) and b[0..nb), found
-// together by one warp: each round tests 32 evenly spaced elements of every
-// range still wider than 32 and keeps the gap holding the answer; a range of
-// at most 32 is answered by one ballot.  T < 2^33; a T of 2^32 or more
-// exceeds every 32-bit element.
+// together by one warp: each round tests 128 evenly spaced elements of every
+// range still wider than 128 (four per lane, loaded together) and keeps the
+// gap holding the answer; a range of at most 128 is answered by one round
+// of four ballots.  T < 2^33; a T of 2^32 or more exceeds every 32-bit
+// element.
 template <class VA, class VB>
 __device__ __forceinline__ void warp_count_below2(const VA& a, uint32_t na, const VB& b, uint32_t nb,
                                                   unsigned long long T, uint32_t& ra,
@@ -228,18 +195,28 @@ __device__ __forceinline__ void warp_count_below2(const VA& a, uint32_t na, cons
   const uint32_t t = (uint32_t)T;
   const uint32_t lane = threadIdx.x & 31u;
   constexpr uint32_t kOpen = 0xffffffffu;
+  constexpr uint32_t kProbes = 128u;
   uint32_t alo = 0u, ahi = na, blo = 0u, bhi = nb;
   ra = kOpen;
   rb = kOpen;
   while (ra == kOpen || rb == kOpen) {
-    const bool wa = ahi - alo > 32u, wb = bhi - blo > 32u;
-    const uint32_t sa = wa ? (ahi - alo + 31u) >> 5 : 1u;
-    const uint32_t sb = wb ? (bhi - blo + 31u) >> 5 : 1u;
-    const uint32_t ia = alo + lane * sa, ib = blo + lane * sb;
-    const bool pa = ra == kOpen && ia < ahi && a[ia] < t;
-    const bool pb = rb == kOpen && ib < bhi && b[ib] < t;
-    const uint32_t ca = (uint32_t)__popc(__ballot_sync(0xffffffffu, pa));
-    const uint32_t cb = (uint32_t)__popc(__ballot_sync(0xffffffffu, pb));
+    const bool wa = ahi - alo > kProbes, wb = bhi - blo > kProbes;
+    const uint32_t sa = wa ? (ahi - alo + kProbes - 1u) / kProbes : 1u;
+    const uint32_t sb = wb ? (bhi - blo + kProbes - 1u) / kProbes : 1u;
+    bool pa[4], pb[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const uint32_t q = (uint32_t)u * 32u + lane;
+      const uint32_t ia = alo + q * sa, ib = blo + q * sb;
+      pa[u] = ra == kOpen && ia < ahi && a[ia] < t;
+      pb[u] = rb == kOpen && ib < bhi && b[ib] < t;
+    }
+    uint32_t ca = 0u, cb = 0u;
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      ca += (uint32_t)__popc(__ballot_sync(0xffffffffu, pa[u]));
+      cb += (uint32_t)__popc(__ballot_sync(0xffffffffu, pb[u]));
+    }
     if (ra == kOpen) {
       if (!wa) {
         ra = alo + ca;
@@ -286,7 +263,9 @@ __device__ __forceinline__ uint32_t run_of(const uint32_t* rs, uint32_t R, uint3
   return lo;
 }
 
-// merge_split with the leaves in run-length form: A[i] is leaf lh + i, run r
+// The merge split (the number of leaves among the first d items of the
+// merged order, ties from the leaves first) with the leaves in run-length
+// form: A[i] is leaf lh + i, run r
 // holding leaves rs[r] .. rs[r+1]-1, all of weight rv[r].  The predicate
 // A[i] <= B[d-1-i] is tested first at the starts of runs, then inside the
 // one run where it turns false.  Returns the split and, in run, the run of
@@ -480,6 +459,45 @@ __device__ unsigned long long block_sum_u64(unsigned long long v, unsigned long 
   return t;
 }
 
+// The Huffman phases once every remaining item lies below the threshold
+// (the sum of the two smallest).  Then every later phase pairs all of its
+// items in order: for a sorted list Q with Q[L-1] < Q[0] + Q[1] the next
+// list (the last item when L is odd, then the pair sums) is sorted again, and
+// again all below its threshold, since Q[L-3] + Q[L-2] < (Q[0] + Q[1]) +
+// Q[L-1] and Q[L-2] + Q[L-1] < 2 (Q[0] + Q[1]).  So a phase needs neither
+// the threshold search nor a merge.  The list is the front item f (when fv),
+// then n queue words from position base; new nodes go from position it on.
+// at(p, k) is the queue word k places after position p, nxt(p, k) its
+// position.  One barrier per phase: a phase reads the words the one before
+// wrote and writes past them.  Returns this thread's share of the cost.
+template <class At, class Nxt>
+__device__ __forceinline__ unsigned long long huffman_tail(At at, Nxt nxt, bool fv, uint32_t f,
+                                                           uint32_t base, uint32_t n, uint32_t it) {
+  unsigned long long cost = 0ull;
+  const uint32_t tid = threadIdx.x;
+  for (;;) {
+    const uint32_t L = n + (fv ? 1u : 0u);
+    if (L <= 1u) break;
+    const uint32_t np = L >> 1;
+    for (uint32_t j = tid; j < np; j += kHuffThreads) {
+      const uint32_t v0 = fv ? (j == 0u ? f : at(base, 2u * j - 1u)) : at(base, 2u * j);
+      const uint32_t v1 = fv ? at(base, 2u * j) : at(base, 2u * j + 1u);
+      const uint32_t sum = v0 + v1;
+      at(it, j) = sum;
+      cost += sum;
+    }
+    const bool odd = (L & 1u) != 0u;
+    const uint32_t last = odd ? at(base, n - 1u) : 0u;  // the list's last item
+    __syncthreads();
+    fv = odd;
+    f = last;
+    base = it;
+    n = np;
+    it = nxt(it, np);
+  }
+  return cost;
+}
+
 // Phases of the two-queue merge with the leaves in run-length form, for
 // alphabets past the linear shared-memory form: the ascending leaves are
 // runs of equal weight (rv[r], first leaf rs[r]; the D distinct small
@@ -491,7 +509,10 @@ __device__ unsigned long long block_sum_u64(unsigned long long v, unsigned long 
 // cost.
 __device__ unsigned long long huffman_runs(const uint32_t* dv, uint32_t D, const uint32_t* big,
                                            uint32_t nbig, uint32_t nsmall, uint32_t K,
-                                           uint32_t* s_dyn, uint32_t* s_w) {
+                                           uint32_t* s_w) {
+  // the runs and the ring in shared memory, addressed as such (every phase
+  // is a chain of dependent loads)
+  extern __shared__ uint32_t s_dyn[];
   const uint32_t tid = threadIdx.x;
   const uint32_t R = D + nbig;
   const uint32_t C = (3u * K + 3u) / 4u + 1u;
@@ -555,6 +576,7 @@ __device__ unsigned long long huffman_runs(const uint32_t* dv, uint32_t D, const
     __syncthreads();
     const uint32_t ml = s_w[0], mi = s_w[1], cl = s_w[2];
     const uint32_t np = (ml + mi) >> 1;
+    const bool all_below = ml + mi == (K - lh) + (it - ih);
     const uint32_t per_t = max(kMinPairs, (np + kHuffThreads - 1) / kHuffThreads);
     const uint32_t j0 = tid * per_t;
     const uint32_t j1 = min(np, j0 + per_t);
@@ -601,6 +623,246 @@ __device__ unsigned long long huffman_runs(const uint32_t* dv, uint32_t D, const
     it += np;
     itr += np;
     if (itr >= C) itr -= C;
+    if (all_below) {
+      // what is left: a leaf (odd count), then the nodes from ring position ihr
+      const bool fv = lh < K;
+      const uint32_t f = fv ? rv[run_of(rs, R, lh)] : 0u;
+      auto at = [&](uint32_t p, uint32_t k) -> uint32_t& {
+        uint32_t q = p + k;  // p < C, k < C
+        if (q >= C) q -= C;
+        return ring[q];
+      };
+      auto nxt = [&](uint32_t p, uint32_t k) {
+        uint32_t q = p + k;
+        return q >= C ? q - C : q;
+      };
+      cost += huffman_tail(at, nxt, fv, f, ihr, it - ih, itr);
+      break;
+    }
+  }
+  return cost;
+}
+
+// Keys of queue items for the windowed merge: the weight doubled, plus one
+// for an internal node, so that key order is weight order with leaves first
+// among equal weights (weights are below 2^31: fields hold fewer points).
+__device__ __forceinline__ uint32_t hkey_leaf(uint32_t v) { return v << 1; }
+__device__ __forceinline__ uint32_t hkey_node(uint32_t v) { return (v << 1) | 1u; }
+
+// Number of A items among the first d of merge(A, B) (ties from A first),
+// found by one warp: the predicate A[i] <= B[d-1-i] holds for a prefix of i
+// in [lo, hi); each round tests 128 evenly spaced i (four per lane) and
+// keeps the gap holding the first failure.
+template <class VA, class VB>
+__device__ __forceinline__ uint32_t warp_merge_split(const VA& A, uint32_t na, const VB& B, uint32_t nb,
+                                                     uint32_t d) {
+  const uint32_t lane = threadIdx.x & 31u;
+  uint32_t lo = d > nb ? d - nb : 0u, hi = d < na ? d : na;
+  while (lo < hi) {
+    const uint32_t n = hi - lo;
+    const uint32_t st = n > 128u ? (n + 127u) / 128u : 1u;
+    bool pr[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const uint32_t i = lo + ((uint32_t)u * 32u + lane) * st;
+      pr[u] = i < hi && A[i] <= B[d - 1u - i];
+    }
+    uint32_t c = 0u;
+#pragma unroll
+    for (int u = 0; u < 4; u++) c += (uint32_t)__popc(__ballot_sync(0xffffffffu, pr[u]));
+    if (st == 1u) return lo + c;  // every i of the range tested
+    if (c == 0u) return lo;
+    const uint32_t nh = lo + c * st;
+    lo += (c - 1u) * st + 1u;
+    hi = nh < hi ? nh : hi;
+  }
+  return lo;
+}
+
+// The 64 smallest of 64 rising keys a (a0 at lane l is item l, a1 item
+// 32 + l) and 64 rising keys b (the same layout), in rising order as r0
+// (item l) and r1 (item 32 + l): a half-cleaner on a followed by b reversed
+// (a bitonic sequence) keeps the lower half, then a bitonic sort of it.
+__device__ __forceinline__ void window_merge64(uint32_t a0, uint32_t a1, uint32_t b0, uint32_t b1,
+                                               uint32_t& r0, uint32_t& r1) {
+  const uint32_t lane = threadIdx.x & 31u;
+  // item e of the lower half: min(a[e], b[63 - e])
+  uint32_t u0 = min(a0, __shfl_sync(0xffffffffu, b1, 31u - lane));
+  uint32_t u1 = min(a1, __shfl_sync(0xffffffffu, b0, 31u - lane));
+  r0 = min(u0, u1);
+  r1 = max(u0, u1);
+#pragma unroll
+  for (uint32_t dist = 16u; dist >= 1u; dist >>= 1) {
+    const uint32_t p0 = __shfl_xor_sync(0xffffffffu, r0, dist);
+    const uint32_t p1 = __shfl_xor_sync(0xffffffffu, r1, dist);
+    const bool upper = (lane & dist) != 0u;
+    r0 = upper ? max(r0, p0) : min(r0, p0);
+    r1 = upper ? max(r1, p1) : min(r1, p1);
+  }
+}
+
+// Steps 2 and 3 of the Huffman cost with both queues linear: the leaves
+// (the small counts expanded from the distinct list, then the large ones
+// sorted), then the phases.  kSmem: K <= kHuffSmemKeys, both queues in shared
+// memory (addressed as such: every phase is a chain of dependent loads),
+// else in the workspace.  Returns this thread's share of the cost.
+template <bool kSmem>
+__device__ __forceinline__ unsigned long long huffman_linear(Workspace* ws, int which,
+                                                             const uint32_t* dv_ws, uint32_t D,
+                                                             const uint32_t* big, uint32_t nbig,
+                                                             uint32_t nsmall, uint32_t K,
+                                                             unsigned long long ns, uint32_t* s_w) {
+  extern __shared__ uint32_t s_dyn[];
+  const int tid = threadIdx.x;
+  unsigned long long cost = 0ull;
+  // with the queues in shared memory the distinct list (D <= K) is there too
+  const uint32_t* dv = kSmem ? s_dyn + kHuffSmemKeys : dv_ws;
+  uint32_t* leaves = kSmem ? s_dyn : ws->sort_scratch[which];
+  // the nodes overwrite the distinct list, or the large counts once copied
+  uint32_t* nodes = kSmem ? s_dyn + kHuffSmemKeys : ws->node_scratch[which];
+  const uint32_t Cd = (D + kHuffThreads - 1) / kHuffThreads;
+  const uint32_t e0 = min(D, (uint32_t)tid * Cd), e1 = min(D, e0 + Cd);
+  uint32_t mloc = 0u;
+  for (uint32_t d = e0; d < e1; d++) mloc += (dv[d] & 0xffffu) + 1u;
+  uint32_t tot;
+  uint32_t start = block_excl_sum(mloc, s_w, &tot);
+  for (uint32_t o = tid; o < nsmall; o += kHuffThreads) leaves[o] = 0u;
+  __syncthreads();
+  for (uint32_t d = e0; d < e1; d++) {
+    const uint32_t q = dv[d];
+    leaves[start] = q >> 16;
+    start += (q & 0xffffu) + 1u;
+  }
+  for (uint32_t i = tid; i < nbig; i += kHuffThreads) leaves[nsmall + i] = big[i];
+  __syncthreads();
+  {
+    const uint32_t C = (nsmall + kHuffThreads - 1) / kHuffThreads;
+    const uint32_t o0 = min(nsmall, (uint32_t)tid * C), o1 = min(nsmall, o0 + C);
+    uint32_t run = 0u;
+    for (uint32_t o = o0; o < o1; o++) run = max(run, leaves[o]);
+    uint32_t carry = block_excl_max(run, s_w);
+    for (uint32_t o = o0; o < o1; o++) {
+      carry = max(carry, leaves[o]);
+      leaves[o] = carry;
+    }
+  }
+  __syncthreads();
+  bitonic_sort(leaves + nsmall, (int)nbig);
+
+  // 3. phases
+  if (K == 1) {
+    cost = (tid == 0) ? ns : 0ull;
+  } else if (K > 1) {
+    const uint32_t lane = (uint32_t)tid & 31u;
+    // the phase reports carry their phase number: a report not written in
+    // this phase is never read as one
+    if (tid == 0) s_w[2] = s_w[6] = 0xffffffffu;
+    __syncthreads();
+    uint32_t lh = 0u, ih = 0u, it = 0u;  // leaf head, node head, node tail
+    for (uint32_t ph = 0u;; ph++) {
+      const uint32_t na = K - lh, nb = it - ih, L = na + nb;
+      if (L <= 1u) break;
+      const uint32_t* A = leaves + lh;
+      const uint32_t* B = nodes + ih;
+      // T: the two smallest items (every thread reads the queue heads)
+      unsigned long long c4[4] = {~0ull, ~0ull, ~0ull, ~0ull};
+      if (na > 0u) c4[0] = A[0];
+      if (na > 1u) c4[1] = A[1];
+      if (nb > 0u) c4[2] = B[0];
+      if (nb > 1u) c4[3] = B[1];
+      const unsigned long long m01 = min(c4[0], c4[1]), x01 = max(c4[0], c4[1]);
+      const unsigned long long m23 = min(c4[2], c4[3]), x23 = max(c4[2], c4[3]);
+      const unsigned long long T = min(m01, m23) + (m01 < m23 ? min(x01, m23) : min(x23, m01));
+      // every item below T: this phase pairs them all, then the tail follows
+      const uint32_t topa = na > 0u ? A[na - 1u] : 0u, topb = nb > 0u ? B[nb - 1u] : 0u;
+      const bool all_below = (unsigned long long)max(topa, topb) < T;
+      // windows of 32 pairs: warp w takes windows w, w + 32, ... while they
+      // pair all 32; the window where pairing stops writes (np, cl)
+      uint32_t* s_res = s_w + 4u * (ph & 1u);
+      for (uint32_t win = (uint32_t)tid >> 5;; win += kHuffThreads / 32) {
+        const uint32_t d = 64u * win;  // merged position of the window's first item
+        if (d >= L) {
+          // all L items paired (L even): the phase ends exactly here
+          if (d == L && all_below && lane == 0u) {
+            s_res[0] = L / 2u;
+            s_res[1] = na;
+            s_res[2] = ph;
+          }
+          break;
+        }
+        {
+          // skip a window that provably holds no pair and does not end the
+          // phase: at most d - 1 items lie below T when A[a] >= T and
+          // B[b] >= T (or a queue is shorter) with a + b = d - 1
+          if (d > 0u) {
+            const uint32_t ia = (d - 1u) >> 1, ib = d - 1u - ia;
+            const bool fa = ia >= na || (unsigned long long)A[ia] >= T;
+            const bool fb = ib >= nb || (unsigned long long)B[ib] >= T;
+            if (fa && fb) break;
+          }
+        }
+        const uint32_t i0 = warp_merge_split(A, na, B, nb, d);
+        const uint32_t k0 = d - i0;
+        const uint32_t a0k = i0 + lane < na ? hkey_leaf(A[i0 + lane]) : ~0u;
+        const uint32_t a1k = i0 + 32u + lane < na ? hkey_leaf(A[i0 + 32u + lane]) : ~0u;
+        const uint32_t b0k = k0 + lane < nb ? hkey_node(B[k0 + lane]) : ~0u;
+        const uint32_t b1k = k0 + 32u + lane < nb ? hkey_node(B[k0 + 32u + lane]) : ~0u;
+        uint32_t r0, r1;
+        window_merge64(a0k, a1k, b0k, b1k, r0, r1);
+        // lane l's pair: merged items 2l and 2l + 1 of the window
+        const uint32_t src = (2u * lane) & 31u;
+        const uint32_t x0 = __shfl_sync(0xffffffffu, r0, src), x1 = __shfl_sync(0xffffffffu, r0, src + 1u);
+        const uint32_t y0 = __shfl_sync(0xffffffffu, r1, src), y1 = __shfl_sync(0xffffffffu, r1, src + 1u);
+        const uint32_t e0 = lane < 16u ? x0 : y0, e1 = lane < 16u ? x1 : y1;
+        // a pair forms when its larger item is below T (a prefix of the lanes)
+        const bool valid = d + 2u * lane + 1u < L && (unsigned long long)(e1 >> 1) < T;
+        if (valid) {
+          const uint32_t sum = (e0 >> 1) + (e1 >> 1);
+          nodes[it + d / 2u + lane] = sum;
+          cost += sum;
+        }
+        const unsigned vm = __ballot_sync(0xffffffffu, valid);
+        if (vm != 0xffffffffu) {
+          const uint32_t v = (uint32_t)__popc(vm);
+          // this window ends the phase when the item before it is below T
+          bool prev_ok = true;
+          if (d > 0u) {
+            const uint32_t pa = i0 > 0u ? A[i0 - 1u] : 0u, pb = k0 > 0u ? B[k0 - 1u] : 0u;
+            prev_ok = (unsigned long long)max(pa, pb) < T;
+          }
+          // leaves among the window's first 2v items
+          const unsigned la = __ballot_sync(0xffffffffu, lane < v && (e0 & 1u) == 0u);
+          const unsigned lb = __ballot_sync(0xffffffffu, lane < v && (e1 & 1u) == 0u);
+          if (prev_ok && lane == 0u) {
+            s_res[0] = d / 2u + v;
+            s_res[1] = i0 + (uint32_t)__popc(la) + (uint32_t)__popc(lb);
+            s_res[2] = ph;
+          }
+          break;
+        }
+      }
+      __syncthreads();
+      const uint32_t np = s_res[0], cl = s_res[1];
+      // exactly one window reports, with at least one pair (the two smallest
+      // items are below T); a missing or inconsistent report would stall the
+      // loop, so it ends the call instead
+      if (s_res[2] != ph || np == 0u || 2u * np > L || cl > na || 2u * np - cl > nb) {
+        if (tid == 0) atomicCAS((int*)&ws->sc.status, RD_OK, RD_ERR_TIMEOUT);
+        break;
+      }
+      lh += cl;
+      ih += 2u * np - cl;
+      it += np;
+      if (all_below) {
+        // what is left: a leaf (odd count), then the nodes from ih
+        const bool fv = lh < K;
+        const uint32_t f = fv ? leaves[lh] : 0u;
+        auto at = [&](uint32_t p, uint32_t k) -> uint32_t& { return nodes[p + k]; };
+        auto nxt = [](uint32_t p, uint32_t k) { return p + k; };
+        cost += huffman_tail(at, nxt, fv, f, ih, it - ih, it);
+        break;
+      }
+    }
   }
   return cost;
 }
@@ -614,10 +876,18 @@ __device__ unsigned long long huffman_runs(const uint32_t* dv, uint32_t D, const
 //  2. The ascending leaf array: the first position of every distinct value
 //     is marked with the value and a running maximum over positions fills
 //     each run; the large counts follow, sorted by a bitonic network.
-//  3. The phased two-queue merge: one warp finds the phase threshold and
-//     the numbers of leaves and nodes below it, then the threads pair
-//     contiguous runs of the merged order (nodes are written only above the
-//     queue tail, which no thread reads until the next barrier).
+//  3. The phased two-queue merge (nodes are written only above the queue
+//     tail, which no thread reads until the next barrier).  With both
+//     queues linear, every warp takes windows of 64 consecutive items of
+//     the merged order (the window's start by a 128-way search for the
+//     split, then the 64 smallest of the next 64 leaves and 64 nodes sorted
+//     by a bitonic network) and forms the window's pairs whose larger item
+//     lies below the phase threshold; the window where pairing stops
+//     reports the phase's numbers of pairs and of leaves consumed, so a
+//     phase has one barrier.  In run-length form one warp finds the numbers
+//     of leaves and nodes below the threshold first, then the threads pair
+//     contiguous runs of the merged order.  Once every remaining item lies
+//     below the threshold the phases need no search at all (huffman_tail).
 // Up to kHuffSmemKeys symbols both queues are linear in shared memory.
 // Larger alphabets keep the leaves as runs of equal weight and the nodes in
 // a ring, in shared memory (huffman_runs), when the runs fit; otherwise the
@@ -707,107 +977,11 @@ __device__ void huffman_cta(Workspace* ws, int which) {
   const bool runs = K > (uint32_t)kHuffSmemKeys && 2u * R + 1u <= (uint32_t)kHuffSmemKeys &&
                     2u * R + 1u + (3u * K + 3u) / 4u + 1u <= 2u * (uint32_t)kHuffSmemKeys;
   if (runs) {
-    cost = huffman_runs(dv, D, big, nbig, nsmall, K, s_dyn, s_w);
+    cost = huffman_runs(dv, D, big, nbig, nsmall, K, s_w);
+  } else if (K <= (uint32_t)kHuffSmemKeys) {
+    cost = huffman_linear<true>(ws, which, dv, D, big, nbig, nsmall, K, ns, s_w);
   } else {
-    // 2. leaves
-    uint32_t* leaves;
-    uint32_t* nodes;
-    if (K <= (uint32_t)kHuffSmemKeys) {
-      leaves = s_dyn;
-      nodes = s_dyn + kHuffSmemKeys;  // the distinct list lives here until the phases
-    } else {
-      leaves = ws->sort_scratch[which];
-      nodes = ws->node_scratch[which];  // free once the large counts are copied
-    }
-    const uint32_t Cd = (D + kHuffThreads - 1) / kHuffThreads;
-    const uint32_t e0 = min(D, (uint32_t)tid * Cd), e1 = min(D, e0 + Cd);
-    uint32_t mloc = 0u;
-    for (uint32_t d = e0; d < e1; d++) mloc += (dv[d] & 0xffffu) + 1u;
-    uint32_t tot;
-    uint32_t start = block_excl_sum(mloc, s_w, &tot);
-    for (uint32_t o = tid; o < nsmall; o += kHuffThreads) leaves[o] = 0u;
-    __syncthreads();
-    for (uint32_t d = e0; d < e1; d++) {
-      const uint32_t q = dv[d];
-      leaves[start] = q >> 16;
-      start += (q & 0xffffu) + 1u;
-    }
-    for (uint32_t i = tid; i < nbig; i += kHuffThreads) leaves[nsmall + i] = big[i];
-    __syncthreads();
-    {
-      const uint32_t C = (nsmall + kHuffThreads - 1) / kHuffThreads;
-      const uint32_t o0 = min(nsmall, (uint32_t)tid * C), o1 = min(nsmall, o0 + C);
-      uint32_t run = 0u;
-      for (uint32_t o = o0; o < o1; o++) run = max(run, leaves[o]);
-      uint32_t carry = block_excl_max(run, s_w);
-      for (uint32_t o = o0; o < o1; o++) {
-        carry = max(carry, leaves[o]);
-        leaves[o] = carry;
-      }
-    }
-    __syncthreads();
-    bitonic_sort(leaves + nsmall, (int)nbig);
-
-    // 3. phases
-    if (K == 1) {
-      cost = (tid == 0) ? ns : 0ull;
-    } else if (K > 1) {
-      uint32_t lh = 0u, ih = 0u, it = 0u;  // leaf head, node head, node tail
-      for (;;) {
-        if ((K - lh) + (it - ih) <= 1u) break;
-        if (tid < 32) {
-          unsigned long long c4[4] = {~0ull, ~0ull, ~0ull, ~0ull};
-          if (lh < K) c4[0] = leaves[lh];
-          if (lh + 1 < K) c4[1] = leaves[lh + 1];
-          if (ih < it) c4[2] = nodes[ih];
-          if (ih + 1 < it) c4[3] = nodes[ih + 1];
-          const unsigned long long m01 = min(c4[0], c4[1]), x01 = max(c4[0], c4[1]);
-          const unsigned long long m23 = min(c4[2], c4[3]), x23 = max(c4[2], c4[3]);
-          const unsigned long long a0 = min(m01, m23);
-          const unsigned long long a1 = m01 < m23 ? min(x01, m23) : min(x23, m01);
-          uint32_t ml, mi;
-          warp_count_below2(leaves + lh, K - lh, nodes + ih, it - ih, a0 + a1, ml, mi);
-          // leaves among the 2 np paired items: all ml, unless the count is
-          // odd and the last item below T in merged order (ties: leaves
-          // first) is a leaf; that item waits for the next phase
-          uint32_t cl = ml;
-          if ((ml + mi) & 1u) {
-            if (mi == 0u || (ml > 0u && leaves[lh + ml - 1] > nodes[ih + mi - 1])) cl = ml - 1u;
-          }
-          if (tid == 0) {
-            s_w[0] = ml;
-            s_w[1] = mi;
-            s_w[2] = cl;
-          }
-        }
-        __syncthreads();
-        const uint32_t ml = s_w[0], mi = s_w[1], cl = s_w[2];
-        const uint32_t np = (ml + mi) >> 1;
-        const uint32_t* A = leaves + lh;
-        const uint32_t* B = nodes + ih;
-        // each thread pairs a contiguous run of the merged order (at least
-        // kMinPairs, so that few warps search when the phase is small)
-        const uint32_t per_t = max(kMinPairs, (np + kHuffThreads - 1) / kHuffThreads);
-        const uint32_t j0 = (uint32_t)tid * per_t;
-        const uint32_t j1 = min(np, j0 + per_t);
-        if (j0 < j1) {
-          uint32_t i = merge_split(A, ml, B, mi, 2u * j0);
-          uint32_t k = 2u * j0 - i;
-          for (uint32_t j = j0; j < j1; j++) {
-            uint32_t e0v, e1v;
-            if (i < ml && (k >= mi || A[i] <= B[k])) e0v = A[i++]; else e0v = B[k++];
-            if (i < ml && (k >= mi || A[i] <= B[k])) e1v = A[i++]; else e1v = B[k++];
-            const uint32_t sum = e0v + e1v;
-            nodes[it + j] = sum;
-            cost += sum;
-          }
-        }
-        __syncthreads();
-        lh += cl;
-        ih += 2u * np - cl;
-        it += np;
-      }
-    }
+    cost = huffman_linear<false>(ws, which, dv, D, big, nbig, nsmall, K, ns, s_w);
   }
   cost = block_sum_u64(cost, s_w64);
   if (tid == 0) {
@@ -1027,7 +1201,7 @@ __global__ void __launch_bounds__(kHuffThreads) k_huffman_finish(Workspace* ws, 
   __shared__ int s_last;
   // the finish step's first part needs no Huffman cost: the first CTA does
   // it before its own histogram
-  if (blockIdx.x == 0) {
+  if (blockIdx.x == 0 && (fa.passes & (P_ZFP_GT | P_SZ_GT))) {  // nothing to do without a truth
     finish_pre(ws, fa.passes, fa.zfp_parts, fa.sz_parts, fa.npoints_all);
     __syncthreads();
   }
