@@ -15,16 +15,20 @@
 
 namespace rdk {
 
-// Estimator: one thread per sampled block (sz_est_block), grid-strided, one
-// CTA of up to 1024 threads per SM with the whole-alphabet 16-bit window
-// (codes of fine bounds spread over tens of thousands of bins); the 2H+1
-// codes around the centre are counted in registers.  A round is one plane
-// of the CTA's 3D blocks, or one of its 2D / 1D blocks: at most
-// kRoundPoints points.
+// Estimator: grid-strided, one CTA of up to 1024 threads per SM with the
+// whole-alphabet 16-bit window (codes of fine bounds spread over tens of
+// thousands of bins); the 2H+1 codes around the centre are counted in
+// registers.  Two work units: with few sampled blocks (their rows fill the
+// resident threads at most four times) one thread per row of four points
+// (sz_est_row: a row's residuals need only its own four row loads, so the
+// gather latency is paid once); otherwise one thread per block
+// (sz_est_block: five planes in turn, each row loaded once).  A round is
+// one pass of the CTA's threads over rows, or one plane of its 3D blocks,
+// or one of its 2D / 1D blocks: at most kRoundPoints points.
 constexpr int kSzEstThreads = 1024;
 static_assert(kSzEstThreads * 16 <= kRoundPoints, "a round adds at most kRoundPoints");
 
-template <int D>
+template <int D, bool ROWS>
 __global__ void __launch_bounds__(kSzEstThreads, 1) k_sz_est(FieldDev f, ParamsDev p, Workspace* ws) {
   extern __shared__ uint32_t s_win[];  // kPackWords words of two counters
   __shared__ int s_hot;
@@ -48,11 +52,22 @@ __global__ void __launch_bounds__(kSzEstThreads, 1) k_sz_est(FieldDev f, ParamsD
       __syncthreads();
     }
   };
-  for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < f.nsampled;
-       b0 += (long long)gridDim.x * blockDim.x) {  // uniform trip count over the CTA
-    const long long sb = b0 + threadIdx.x;
-    sz_est_block<D>(f, sb, sb < f.nsampled, inv, p.R, add, round_end);
-    if (D < 3) round_end();
+  if (ROWS) {
+    constexpr int kRows = est_rows<D>();
+    const long long nrows = f.nsampled * kRows;
+    for (long long q0 = (long long)blockIdx.x * blockDim.x; q0 < nrows;
+         q0 += (long long)gridDim.x * blockDim.x) {  // uniform trip count over the CTA
+      const long long q = q0 + threadIdx.x;
+      sz_est_row<D>(f, q / kRows, (int)(q % kRows), q < nrows, inv, p.R, add);
+      round_end();
+    }
+  } else {
+    for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < f.nsampled;
+         b0 += (long long)gridDim.x * blockDim.x) {  // uniform trip count over the CTA
+      const long long sb = b0 + threadIdx.x;
+      sz_est_block<D>(f, sb, sb < f.nsampled, inv, p.R, add, round_end);
+      if (D < 3) round_end();
+    }
   }
   hot.flush_global(g_hist);
   window_flush(s_win, g_hist);
@@ -132,14 +147,24 @@ __global__ void __launch_bounds__(kSzThreads) k_sz_gt(FieldDev f, ParamsDev p, W
 template <int D>
 static cudaError_t launch_est_d(const FieldDev& f, const ParamsDev& p, Workspace* ws, int ctas,
                                 cudaStream_t s) {
-  // one CTA per SM (ctas); fewer threads per CTA when the field has fewer
-  // sampled blocks than the CTAs' threads, so that every SM takes a share
-  long long per = (f.nsampled + ctas - 1) / ctas;
+  // one CTA per SM (ctas); rows as work units when they fill the resident
+  // threads at most four times (on a 100x500x500 field 2.1 rounds of rows
+  // took 26.5 us against 30.6 for blocks; on 512^3 fields 10.5 rounds of
+  // rows took 88 us against 66), else blocks; fewer threads per CTA when
+  // there are fewer units than the CTAs' threads, so that every SM takes a
+  // share
+  const long long nrows = f.nsampled * est_rows<D>();
+  const bool rows = nrows <= 4ll * ctas * kSzEstThreads;
+  const long long units = rows ? nrows : f.nsampled;
+  long long per = (units + ctas - 1) / ctas;
   per = (per + 31) / 32 * 32;
   const int threads = (int)(per < 128 ? 128 : per > kSzEstThreads ? kSzEstThreads : per);
-  long long want = (f.nsampled + threads - 1) / threads;
+  long long want = (units + threads - 1) / threads;
   int g = (int)(want < ctas ? (want < 1 ? 1 : want) : ctas);
-  k_sz_est<D><<<g, threads, kPackWords * sizeof(uint32_t), s>>>(f, p, ws);
+  if (rows)
+    k_sz_est<D, true><<<g, threads, kPackWords * sizeof(uint32_t), s>>>(f, p, ws);
+  else
+    k_sz_est<D, false><<<g, threads, kPackWords * sizeof(uint32_t), s>>>(f, p, ws);
   return cudaGetLastError();
 }
 
@@ -176,17 +201,19 @@ cudaError_t launch_sz_gt(const FieldDev& f, const ParamsDev& p, int with_est, Wo
 
 cudaError_t prepare_sz_est() {
   const int smem = kPackWords * (int)sizeof(uint32_t);
-  cudaError_t e = cudaFuncSetAttribute(k_sz_est<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_sz_est<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_sz_est<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const void* fns[6] = {(const void*)k_sz_est<1, false>, (const void*)k_sz_est<2, false>,
+                        (const void*)k_sz_est<3, false>, (const void*)k_sz_est<1, true>,
+                        (const void*)k_sz_est<2, true>,  (const void*)k_sz_est<3, true>};
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 6 && e == cudaSuccess; i++)
+    e = cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   return e;
 }
 
 int sz_est_occupancy(int d, int num_sms) {
   int per = 0;
-  const void* fn = d == 1 ? (const void*)k_sz_est<1> : d == 2 ? (const void*)k_sz_est<2> : (const void*)k_sz_est<3>;
+  const void* fn = d == 1 ? (const void*)k_sz_est<1, false>
+                 : d == 2 ? (const void*)k_sz_est<2, false> : (const void*)k_sz_est<3, false>;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kSzEstThreads,
                                                     kPackWords * sizeof(uint32_t)) != cudaSuccess ||
       per < 1) {

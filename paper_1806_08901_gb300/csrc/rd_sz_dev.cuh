@@ -101,8 +101,7 @@ __device__ __forceinline__ bool in_sampled_block(const FieldDev& f, const int* g
 // Row y of plane z, values x0-1 .. x0+3 (zero outside the domain; values past
 // the far edges feed no valid point and read as zero).
 __device__ __forceinline__ void load_halo_row(const FieldDev& f, long long row, bool row_ok, int x0,
-                                              float* v) {
-  const int nx = f.n[f.d - 1];
+                                              int nx, float* v) {
   if (!row_ok) {
 #pragma unroll
     for (int k = 0; k < 5; k++) v[k] = 0.0f;
@@ -144,7 +143,7 @@ __device__ __forceinline__ void sz_block_residuals(const FieldDev& f, long long 
   if (active) sampled_block_origin<D>(f, sb, o);
   if constexpr (D == 1) {
     float v[5];
-    load_halo_row(f, 0, active, o[0], v);
+    load_halo_row(f, 0, active, o[0], f.n[0], v);
 #pragma unroll
     for (int k = 0; k < 4; k++) {
       const bool ok = active && o[0] + k < f.n[0];
@@ -161,7 +160,7 @@ __device__ __forceinline__ void sz_block_residuals(const FieldDev& f, long long 
         const int y = y0 - 1 + r;
         const bool ok = z_ok && y >= 0 && y < ny;
         const long long row = (D == 3 ? (long long)z * ny : 0ll) + y;
-        load_halo_row(f, row, ok, x0, v[r]);
+        load_halo_row(f, row, ok, x0, nx, v[r]);
       }
 #pragma unroll
       for (int j = 0; j < 4; j++)
@@ -196,11 +195,70 @@ __device__ __forceinline__ void sz_block_residuals(const FieldDev& f, long long 
   }
 }
 
+// Rows of four points per sampled block: 16 in 3D (plane i = t >> 2, row
+// j = t & 3), 4 in 2D, 1 in 1D.
+template <int D>
+__host__ __device__ constexpr int est_rows() { return D == 3 ? 16 : D == 2 ? 4 : 1; }
+
+// res(r) receives the residual of every valid point of row t of sampled
+// block sb: the same nested first differences as sz_block_residuals, from
+// the row itself, the row before it (y - 1) and, in 3D, those two rows of
+// plane z - 1 (zero outside the domain), so one thread's loads are
+// independent of each other.
+template <int D, class Res>
+__device__ __forceinline__ void sz_row_residuals(const FieldDev& f, long long sb, int t, bool active,
+                                                 Res&& res) {
+  int o[3] = {0, 0, 0};
+  if (active) sampled_block_origin<D>(f, sb, o);
+  if constexpr (D == 1) {
+    float v[5];
+    load_halo_row(f, 0, active, o[0], f.n[0], v);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const bool ok = active && o[0] + k < f.n[0];
+      if (ok) res(__fsub_rn(v[k + 1], v[k]));
+    }
+  } else {
+    const int ny = f.n[D - 2], nx = f.n[D - 1];
+    const int j = t & 3;
+    const int y = o[D - 2] + j, x0 = o[D - 1];
+    const int nz = D == 3 ? f.n[0] : 1;
+    const int z = D == 3 ? o[0] + (t >> 2) : 0;
+    const bool z_ok = active && z < nz;
+    auto row_of = [&](int zz, int yy) { return (D == 3 ? (long long)zz * ny : 0ll) + yy; };
+    float v11[5], v10[5];
+    load_halo_row(f, row_of(z, y), z_ok && y < ny, x0, nx, v11);
+    load_halo_row(f, row_of(z, y - 1), z_ok && y >= 1 && y - 1 < ny, x0, nx, v10);
+    float v01[5], v00[5];
+    if (D == 3) {
+      const bool p_ok = active && z >= 1 && z - 1 < nz;
+      load_halo_row(f, row_of(z - 1, y), p_ok && y < ny, x0, nx, v01);
+      load_halo_row(f, row_of(z - 1, y - 1), p_ok && y >= 1 && y - 1 < ny, x0, nx, v00);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const bool ok = z_ok && y < ny && x0 + k < nx;
+      const float cur = __fsub_rn(__fsub_rn(v11[k + 1], v11[k]), __fsub_rn(v10[k + 1], v10[k]));
+      float r = cur;
+      if (D == 3)
+        r = __fsub_rn(cur, __fsub_rn(__fsub_rn(v01[k + 1], v01[k]), __fsub_rn(v00[k + 1], v00[k])));
+      if (ok) res(r);
+    }
+  }
+}
+
 // add(sym) counts the linear code of every valid point of the block.
 template <int D, class Add, class RoundEnd>
 __device__ __forceinline__ void sz_est_block(const FieldDev& f, long long sb, bool active, float inv,
                                              int R, Add&& add, RoundEnd&& round_end) {
   sz_block_residuals<D>(f, sb, active, [&](float r) { add(est_symbol(r, inv, R)); }, round_end);
+}
+
+// add(sym) counts the linear code of every valid point of row t of block sb.
+template <int D, class Add>
+__device__ __forceinline__ void sz_est_row(const FieldDev& f, long long sb, int t, bool active,
+                                           float inv, int R, Add&& add) {
+  sz_row_residuals<D>(f, sb, t, active, [&](float r) { add(est_symbol(r, inv, R)); });
 }
 
 }  // namespace rdk
