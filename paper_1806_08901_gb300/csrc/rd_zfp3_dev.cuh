@@ -1,7 +1,6 @@
 // rd_zfp3_dev.cuh -- the ZFP block code of a 4x4x4 block shared by the four
 // lanes q = 0..3 of a quad (Sections "Block Orthogonal Transformation" and
-// "Estimation Based on Dynamic Quantization"), used by the 3D ZFP pass and
-// the batched estimate's 3D sampled blocks:
+// "Estimation Based on Dynamic Quantization"), used by the 3D ZFP pass:
 //   slice layout  lane q holds the plane z = q (16 values, x fastest): the
 //                 lifting along x and y runs in its registers;
 //   line layout   lane q holds the row y = q of every plane (z, q, 0..3):
