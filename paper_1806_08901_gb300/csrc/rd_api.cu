@@ -25,7 +25,7 @@ const char* kKernelNames[K_COUNT] = {
     "reset", "range", "zfp_pass", "delta", "sz_est", "sz_pass",
     "code_prep", "huffman", "finish", "zfp_inspect", "sz_inspect",
     "batch_reset", "batch_range", "batch_blocks", "batch_sz_hist", "batch_code_prep",
-    "batch_final", "batch_truth", "sz_classic", "sz_classic_err", "sz_log"};
+    "batch_final", "batch_truth", "sz_classic", "sz_classic_err", "sz_log", "zfp_est"};
 
 struct KStat {
   double ms;
@@ -303,6 +303,43 @@ int make_geometry(rd_context* c, const rd_field* fld, const int* strides_or_null
   return RD_OK;
 }
 
+// The evaluate step of a 3D field (both estimates and both truths): the
+// truth's ZFP pass needs nothing the SZ side computes, so the ZFP estimate
+// runs first (for delta), then the SZ pass, the code prep and the Huffman
+// launch, and the truth's ZFP pass is launched as the Huffman launch's
+// programmatic dependent: it starts once the Huffman CTAs run (they take two
+// SMs; the pass is sized to the rest) and its last CTA, after the Huffman
+// launch has completed, finishes the ZFP truth and writes the records.
+int issue_overlapped(rd_context* c, const CallKey& k, const Geometry& g, cudaStream_t s) {
+  const FieldDev& f = k.f;
+  const ParamsDev& p = k.p;
+  const int passes = k.passes;
+  Workspace* ws = c->ws;
+  const int d = f.d;
+  const unsigned long long ncoeff = (unsigned long long)f.nsampled * ec_count(d, p.ec_mode);
+  int zfp_parts = 0, sz_parts = 0, est_parts = 0;
+  int rc;
+  if ((rc = launch(c, K_RESET, s, [&] { return launch_reset(ws, s); }))) return rc;
+  if ((rc = launch(c, K_RANGE, s, [&] { return launch_range(f, p, ws, c->range_ctas, s, k.host_src); })))
+    return rc;
+  const DeltaArgs da{1, k.delta_mode, k.delta_arg, 1, 1, ncoeff, g.npoints_sampled};
+  if ((rc = launch(c, K_ZFP_EST, s, [&] {
+         return launch_zfp(f, p, P_ZFP_EST, da, ws, c->zfp_ctas[d], s, &est_parts);
+       })))
+    return rc;
+  if ((rc = launch(c, K_SZ_GT, s, [&] {
+         if (sz_march_supported(f)) return launch_sz_march(f, p, 1, ws, c->num_sms, s, &sz_parts);
+         return launch_sz_gt(f, p, 1, ws, c->sz_ctas[d], s, &sz_parts);
+       })))
+    return rc;
+  if ((rc = launch(c, K_CODE_PREP, s, [&] { return launch_code_prep(ws, 3, c->xlogx, s); }))) return rc;
+  const FinishArgs fa{p, passes, 0, sz_parts, f.N, g.npoints_sampled, c->out_dev, 1};
+  if ((rc = launch(c, K_HUFFMAN, s, [&] { return launch_huffman_finish(ws, 3, fa, s); }))) return rc;
+  const int per = c->zfp_ctas[d] / (c->num_sms > 0 ? c->num_sms : 1);
+  const int zctas = per > 0 && c->num_sms > 4 ? per * (c->num_sms - 2) : c->zfp_ctas[d];
+  return launch(c, K_ZFP, s, [&] { return launch_zfp3_after_huffman(f, p, ws, zctas, fa, s, &zfp_parts); });
+}
+
 // Issue the launch sequence of one call and the copy of its result records
 // into pinned host memory, on stream s (which may be capturing).
 int issue(rd_context* c, const CallKey& k, const Geometry& g, cudaStream_t s) {
@@ -320,6 +357,10 @@ int issue(rd_context* c, const CallKey& k, const Geometry& g, cudaStream_t s) {
   int zfp_parts = 0, sz_parts = 0;
   int rc;
 
+  // the evaluate step of a 3D field: the truth's ZFP pass beside the Huffman launch
+  if (d == 3 && (passes & P_ZFP_EST) && (passes & P_ZFP_GT) && (passes & P_SZ_GT) && (passes & P_SZ_EST) &&
+      !classic)
+    return issue_overlapped(c, k, g, s);
   if ((rc = launch(c, K_RESET, s, [&] { return launch_reset(ws, s); }))) return rc;
   if ((rc = launch(c, K_RANGE, s, [&] { return launch_range(f, p, ws, c->range_ctas, s, k.host_src); })))
     return rc;

@@ -43,6 +43,8 @@ struct Scalars {
   unsigned int sz_maxerr;
   unsigned int log_maxabs;       // float bits of max |residual| (log-scale estimate)
   uint32_t huff_done;            // Huffman CTAs finished (the last one runs the finish step)
+  uint32_t zfp_done;             // CTAs of the truth's ZFP pass finished (the last one writes
+                                 // the evaluate step's records)
   unsigned long long mse_lo[kMseBins];  // 128-bit sums of d^2 per exponent
   unsigned long long mse_hi[kMseBins];
 };
@@ -159,6 +161,7 @@ enum KernelId {
   K_SZ_CLASSIC,
   K_SZ_CLASSIC_ERR,
   K_SZ_LOG,
+  K_ZFP_EST,
   K_COUNT
 };
 
@@ -239,6 +242,11 @@ struct FinishArgs {
   long long npoints_all;
   unsigned long long zfp_npoints;
   OutRecords* out;
+  // 1: the evaluate step with the truth's ZFP pass launched beside the
+  // Huffman launch (programmatic dependent launch): the Huffman launch
+  // finishes the estimates and the SZ truth only; the ZFP pass's last CTA
+  // waits for it, finishes the ZFP truth and writes the records
+  int join;
 };
 // Huffman cost and entropy of the histograms in which_mask, then the finish
 // step by the CTA that ends last (one launch fewer than launch_huffman and
@@ -260,7 +268,13 @@ cudaError_t launch_sz_march(const FieldDev& f, const ParamsDev& p, int with_est,
 int zfp_occupancy(int d, int num_sms);
 // the 3D ZFP pass, four lanes per block (launch_zfp dispatches to it)
 cudaError_t launch_zfp3(const FieldDev& f, const ParamsDev& p, int passes, const DeltaArgs& da,
-                        Workspace* ws, int ctas, cudaStream_t s, int* grid_used);
+                        Workspace* ws, int ctas, cudaStream_t s, int* grid_used,
+                        const FinishArgs* join = nullptr);
+// The truth's ZFP pass (3D) of the evaluate step, launched right after the
+// Huffman launch as its programmatic dependent (it starts once the Huffman
+// CTAs run and its last CTA waits for them to complete).
+cudaError_t launch_zfp3_after_huffman(const FieldDev& f, const ParamsDev& p, Workspace* ws, int ctas,
+                                      const FinishArgs& fa, cudaStream_t s, int* grid_used);
 int zfp3_occupancy(int num_sms);
 
 // ---- log-scale quantisation estimate (rd_sz_log.cu) ----

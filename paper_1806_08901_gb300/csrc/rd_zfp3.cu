@@ -12,18 +12,42 @@
 // estimator's sums) is the one thread-per-block computation's, term for
 // term; only the float32 sum of squared errors is added in another order.
 #include <stdint.h>
+#include <string.h>
 
 #include "rd_delta.cuh"
+#include "rd_finish.cuh"
 #include "rd_zfp3_dev.cuh"
 
 namespace rdk {
 
 constexpr int kZ3Threads = 256;
 constexpr int kZ3Warps = kZ3Threads / 32;
+static_assert(kZ3Threads >= kFinishThreads, "the last CTA runs the finish step's sums");
+
+// The evaluate step's truth pass beside the Huffman launch: the CTA that
+// ends last (its own counter, fenced on both sides) waits for the Huffman
+// launch to complete (the programmatic dependency's wait; so this pass also
+// completes after it), finishes the ZFP truth (squared-error sum over the
+// CTAs' partials in a fixed order, MSE, PSNR, rate), compares the truths and
+// writes the records.  Every thread of every CTA calls it.
+__device__ __forceinline__ void zfp_finish_last(Workspace* ws, const FinishArgs& fa) {
+  __shared__ int s_lastz;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_lastz = atomicAdd(&ws->sc.zfp_done, 1u) == gridDim.x - 1u;
+  }
+  __syncthreads();
+  if (!s_lastz) return;
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  __threadfence();
+  finish_pre(ws, fa.passes & ~P_SZ_GT, (int)gridDim.x, fa.sz_parts, fa.npoints_all);
+  finish_combine(ws, fa.passes, fa.out);
+}
 
 template <bool GT, bool EST>
 __global__ void __launch_bounds__(kZ3Threads) k_zfp3(FieldDev f, ParamsDev p, DeltaArgs da,
-                                                      Workspace* ws) {
+                                                      Workspace* ws, FinishArgs fa) {
   __shared__ unsigned long long s_lo[kMseBins], s_hi[kMseBins];
   __shared__ unsigned long long s_acc[2];
   __shared__ double s_sse[kZ3Warps];
@@ -31,7 +55,18 @@ __global__ void __launch_bounds__(kZ3Threads) k_zfp3(FieldDev f, ParamsDev p, De
   __shared__ __align__(16) int s_tr[kZ3Warps][8 * kZ3BlockWords];
   __shared__ __align__(16) unsigned char s_rk[kZ3Warps][8 * kZ3RankBytes];
   const Scalars& sc = ws->sc;
-  if (sc.status != RD_OK || sc.constant) return;
+  {
+    // one reading of the status for the whole CTA (with a join, the Huffman
+    // launch runs beside this pass and may change it)
+    __shared__ int s_skip;
+    if (threadIdx.x == 0) s_skip = (__ldcg(&sc.status) != RD_OK || __ldcg(&sc.constant)) ? 1 : 0;
+    __syncthreads();
+    if (s_skip) {
+      // the evaluate step's records still come from this pass's last CTA
+      if (GT && fa.join) zfp_finish_last(ws, fa);
+      return;
+    }
+  }
   const int minexp = sc.minexp;
   if (EST) {
     for (int i = threadIdx.x; i < kMseBins; i += blockDim.x) {
@@ -291,10 +326,14 @@ __global__ void __launch_bounds__(kZ3Threads) k_zfp3(FieldDev f, ParamsDev p, De
       delta_warp(p, ws, da.mode, da.arg, da.need_quant, da.need_gt, da.ncoeff, da.npoints);
     }
   }
+  if (GT && fa.join) zfp_finish_last(ws, fa);
 }
 
 cudaError_t launch_zfp3(const FieldDev& f, const ParamsDev& p, int passes, const DeltaArgs& da,
-                        Workspace* ws, int ctas, cudaStream_t s, int* grid_used) {
+                        Workspace* ws, int ctas, cudaStream_t s, int* grid_used, const FinishArgs* join) {
+  FinishArgs fa;
+  memset(&fa, 0, sizeof(fa));
+  if (join) fa = *join;
   const bool gt = passes & P_ZFP_GT, est = passes & P_ZFP_EST;
   const long long units = gt ? f.nblocks : f.nsampled;
   const long long per_cta = 8LL * kZ3Warps;
@@ -302,12 +341,31 @@ cudaError_t launch_zfp3(const FieldDev& f, const ParamsDev& p, int passes, const
   int g = (int)(want < ctas ? (want < 1 ? 1 : want) : ctas);
   if (grid_used) *grid_used = g;
   if (gt && est)
-    k_zfp3<true, true><<<g, kZ3Threads, 0, s>>>(f, p, da, ws);
+    k_zfp3<true, true><<<g, kZ3Threads, 0, s>>>(f, p, da, ws, fa);
   else if (gt)
-    k_zfp3<true, false><<<g, kZ3Threads, 0, s>>>(f, p, da, ws);
+    k_zfp3<true, false><<<g, kZ3Threads, 0, s>>>(f, p, da, ws, fa);
   else
-    k_zfp3<false, true><<<g, kZ3Threads, 0, s>>>(f, p, da, ws);
+    k_zfp3<false, true><<<g, kZ3Threads, 0, s>>>(f, p, da, ws, fa);
   return cudaGetLastError();
+}
+
+cudaError_t launch_zfp3_after_huffman(const FieldDev& f, const ParamsDev& p, Workspace* ws, int ctas,
+                                      const FinishArgs& fa, cudaStream_t s, int* grid_used) {
+  const long long per_cta = 8LL * kZ3Warps;
+  const long long want = (f.nblocks + per_cta - 1) / per_cta;
+  const int g = (int)(want < ctas ? (want < 1 ? 1 : want) : ctas);
+  if (grid_used) *grid_used = g;
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3(g, 1, 1);
+  cfg.blockDim = dim3(kZ3Threads, 1, 1);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_zfp3<true, false>, f, p, DeltaArgs{}, ws, fa);
 }
 
 int zfp3_occupancy(int num_sms) {
