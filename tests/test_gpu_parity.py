@@ -225,6 +225,35 @@ def test_nonfinite_rejected(R, ctx):
             O.select(y, O.params())
 
 
+def test_evaluate_3d_edge_cases_then_a_good_call(R, ctx):
+    """The 3D evaluate step writes its records from the last CTA of the
+    truth's ZFP pass after the Huffman launch it follows: a constant field,
+    a field with a non-finite value and a truth whose codes overflow must
+    each report as the oracle does, and the next call must be unaffected."""
+    op = O.params(eb=1e-3)
+    good = synth.config2_field(seed=21, shape=(20, 24, 28))
+    const = np.full((6, 7, 9), 1.5, np.float32)
+    ge, gt = ctx.evaluate(torch.from_numpy(const).cuda(), _gp(R, op))
+    assert ge["flags"] & R.RD_F_CONSTANT and ge["selection"] == 1
+    check_result(ge, O.select(const, op), 3)
+    check_truth(gt, O.ground_truth(const, op))
+    assert math.isinf(gt["psnr_sz_gt"]) and gt["best_gt"] == 1
+    bad = good.copy()
+    bad[3, 5, 7] = np.nan
+    with pytest.raises(R.RdselError) as e:
+        ctx.evaluate(torch.from_numpy(bad).cuda(), _gp(R, op))
+    assert e.value.code == R.RD_ERR_NONFINITE
+    rng = np.random.default_rng(9)
+    flat = (1000.0 + 1e-3 * rng.standard_normal((8, 16, 16))).astype(np.float32)
+    with pytest.raises(R.RdselError) as e:
+        ctx.evaluate(torch.from_numpy(flat).cuda(), _gp(R, O.params(eb=1e-9, r_sp=1.0)))
+    assert e.value.code == R.RD_ERR_RANGE
+    for _ in range(2):
+        ge, gt = ctx.evaluate(torch.from_numpy(good).cuda(), _gp(R, op))
+        check_result(ge, O.select(good, op), 3)
+        check_truth(gt, O.ground_truth(good, op))
+
+
 def test_range_error_when_codes_overflow(R, ctx):
     rng = np.random.default_rng(5)
     x = (1000.0 + 1e-3 * rng.standard_normal((16, 16))).astype(np.float32)
